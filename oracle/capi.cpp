@@ -1,0 +1,251 @@
+// C interface of the CPU oracle, loaded by the tests (ctypes) and by the
+// timed CPU baseline of the benchmark.  TEST INFRASTRUCTURE ONLY (see scalar.h).
+//
+// Single-environment arrays are plain [nq] / [nv] / [nq + nv] vectors;
+// batched arrays are environment-major ([B][...]).
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "integrator.h"
+
+using namespace orc;
+
+namespace {
+Model& M(void* h) { return *static_cast<Model*>(h); }
+
+template <class Fn> void parallel_for(int n, int nthreads, Fn fn) {
+  nthreads = std::max(1, std::min(nthreads, n));
+  if (nthreads == 1) { for (int i = 0; i < n; ++i) fn(i); return; }
+  std::atomic<int> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&] {
+      for (int i = next++; i < n; i = next++) fn(i);
+    });
+  for (auto& x : th) x.join();
+}
+Opts make_opts(double T, int NI, double rtol, double atol, double h0, int max_steps) {
+  Opts o;
+  o.T = T; o.NI = NI; o.rtol = rtol; o.atol = atol; o.h0 = h0; o.max_steps = max_steps;
+  return o;
+}
+void put_stats(const Result& r, int* s) { s[0] = r.status; s[1] = r.nsteps; s[2] = r.nrej; s[3] = r.nrhs; }
+}  // namespace
+
+extern "C" {
+
+void* orc_create(const double* body, int nbody, const double* geom, int ngeom, const double* pair, int npair,
+                 const double* act, int nact, const double* opt, const double* qpos0, char* err, int errlen) {
+  Model* m = new Model();
+  std::string e = build_model(*m, body, nbody, geom, ngeom, pair, npair, act, nact, opt, qpos0);
+  if (!e.empty()) {
+    if (err && errlen > 0) { std::strncpy(err, e.c_str(), errlen - 1); err[errlen - 1] = 0; }
+    delete m;
+    return nullptr;
+  }
+  return m;
+}
+void orc_free(void* h) { delete static_cast<Model*>(h); }
+
+void orc_dims(void* h, int* out) {
+  Model& m = M(h);
+  out[0] = m.nq; out[1] = m.nv; out[2] = m.nu; out[3] = m.nslot; out[4] = m.nrowmax; out[5] = (int)m.body.size();
+}
+double orc_body_invw(void* h, int b) { return M(h).body_invw[b]; }
+double orc_pair_invw(void* h, int p) { return M(h).pair[p].invw; }
+
+void orc_tableau(double* a, double* b, double* bhat, double* c) {
+  const Tableau& t = dopri5();
+  for (int i = 0; i < 7; ++i) {
+    for (int j = 0; j < 7; ++j) a[7 * i + j] = t.a[i][j];
+    b[i] = t.b[i]; bhat[i] = t.bhat[i]; c[i] = t.c[i];
+  }
+}
+
+int orc_kinematics(void* h, const double* q, double* R, double* p, double* com) {
+  Model& m = M(h);
+  Kin<double> k;
+  kinematics(m, q, k);
+  for (size_t b = 0; b < m.body.size(); ++b) {
+    for (int i = 0; i < 9; ++i) R[9 * b + i] = k.R[b][i];
+    for (int i = 0; i < 3; ++i) { p[3 * b + i] = k.p[b][i]; com[3 * b + i] = k.c[b][i]; }
+  }
+  return 0;
+}
+// Linear (3 x nv) and angular (3 x nv) Jacobians of a world point fixed to body b.
+int orc_point_jacobian(void* h, const double* q, int b, const double* x, double* Jlin, double* Jang) {
+  Model& m = M(h);
+  Kin<double> k;
+  kinematics(m, q, k);
+  V3<double> xp = {x[0], x[1], x[2]};
+  for (int i = 0; i < m.nv; ++i) {
+    V3<double> pv = dof_point_vel(m, k, i, b, xp);
+    const bool moves = m.anc[b][m.dof_body[i]];
+    for (int r = 0; r < 3; ++r) {
+      Jlin[r * m.nv + i] = pv[r];
+      Jang[r * m.nv + i] = moves ? k.s[i][r] : 0.0;
+    }
+  }
+  return 0;
+}
+int orc_mass(void* h, const double* q, double* Mout) {
+  Model& m = M(h);
+  Kin<double> k;
+  kinematics(m, q, k);
+  std::vector<double> Mm;
+  crba(m, k, Mm);
+  std::copy(Mm.begin(), Mm.end(), Mout);
+  return 0;
+}
+int orc_bias(void* h, const double* q, const double* v, double* c) {
+  Model& m = M(h);
+  Kin<double> k;
+  kinematics(m, q, k);
+  std::vector<double> cc;
+  rne(m, k, v, cc);
+  std::copy(cc.begin(), cc.end(), c);
+  return 0;
+}
+int orc_applied(void* h, const double* q, const double* v, const double* u, double* tau) {
+  std::vector<double> t;
+  applied(M(h), q, v, u, t);
+  std::copy(t.begin(), t.end(), tau);
+  return 0;
+}
+// out per slot (16): r, pos[3], n[3], t1[3], t2[3], bodyA, bodyB, pair
+int orc_contacts(void* h, const double* q, double* out) {
+  Model& m = M(h);
+  Kin<double> k;
+  kinematics(m, q, k);
+  std::vector<Contact<double>> ct;
+  contacts(m, k, ct);
+  for (int s = 0; s < m.nslot; ++s) {
+    double* o = out + 16 * s;
+    o[0] = ct[s].r;
+    for (int i = 0; i < 3; ++i) { o[1 + i] = ct[s].pos[i]; o[4 + i] = ct[s].n[i]; o[7 + i] = ct[s].t1[i]; o[10 + i] = ct[s].t2[i]; }
+    o[13] = ct[s].bodyA; o[14] = ct[s].bodyB; o[15] = ct[s].pair;
+  }
+  return 0;
+}
+double orc_impedance(void* h, double r, int cfd) { return impedance<double>(M(h), r, cfd != 0); }
+
+// Constraint rows of the included contacts; returns the number of rows.
+int orc_rows(void* h, const double* q, const double* v, int cfd, double* J, double* aref, double* D, int* slot) {
+  Model& m = M(h);
+  Kin<double> k;
+  kinematics(m, q, k);
+  std::vector<Contact<double>> ct;
+  contacts(m, k, ct);
+  Rows<double> R;
+  make_rows(m, k, ct, v, cfd != 0, R);
+  std::copy(R.J.begin(), R.J.end(), J);
+  std::copy(R.aref.begin(), R.aref.end(), aref);
+  std::copy(R.D.begin(), R.D.end(), D);
+  std::copy(R.slot.begin(), R.slot.end(), slot);
+  return R.nr;
+}
+// info: nr, newton iterations, noconv, spd_fail
+int orc_rhs(void* h, const double* q, const double* v, const double* u, int cfd, double* a, double* f, int* active, int* info) {
+  Model& m = M(h);
+  RhsDiag<double> dg;
+  bool ok = rhs<double>(m, q, v, u, cfd != 0, a, &dg);
+  if (f) std::copy(dg.f.begin(), dg.f.end(), f);
+  if (active) for (int r = 0; r < dg.rows.nr; ++r) active[r] = dg.info.active[r];
+  if (info) { info[0] = dg.rows.nr; info[1] = dg.info.iters; info[2] = dg.info.noconv; info[3] = dg.info.spd_fail; }
+  return ok ? 0 : 1;
+}
+// Jacobians of F (or F~) w.r.t. q (nv x nq), v (nv x nv), u (nv x nu).
+int orc_rhs_jacobian(void* h, const double* q, const double* v, const double* u, int cfd, double* Jq, double* Jv, double* Ju) {
+  using D = Dual<double>;
+  Model& m = M(h);
+  const int nq = m.nq, nv = m.nv, nu = m.nu;
+  std::vector<D> qd(nq), vd(nv), ud(std::max(nu, 1)), a(nv);
+  for (int dir = 0; dir < nq + nv + nu; ++dir) {
+    for (int i = 0; i < nq; ++i) qd[i] = D(q[i], dir == i ? 1.0 : 0.0);
+    for (int i = 0; i < nv; ++i) vd[i] = D(v[i], dir == nq + i ? 1.0 : 0.0);
+    for (int i = 0; i < nu; ++i) ud[i] = D(u[i], dir == nq + nv + i ? 1.0 : 0.0);
+    rhs<D>(m, qd.data(), vd.data(), ud.data(), cfd != 0, a.data());
+    for (int i = 0; i < nv; ++i) {
+      if (dir < nq) Jq[i * nq + dir] = a[i].d;
+      else if (dir < nq + nv) Jv[i * nv + dir - nq] = a[i].d;
+      else Ju[i * nu + dir - nq - nv] = a[i].d;
+    }
+  }
+  return 0;
+}
+void orc_integrate_pos(void* h, const double* q, const double* dlt, double* out) { integrate_pos<double>(M(h), q, dlt, out); }
+
+int orc_rollout(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol, double atol, double h0,
+                int max_steps, double* xT, double* xb, int* stats, double* hlog, int hcap) {
+  std::vector<double> hl;
+  Result r = rollout<double>(M(h), x0, ctrl, make_opts(T, NI, rtol, atol, h0, max_steps), xT, xb, nullptr, &hl, nullptr, 0);
+  put_stats(r, stats);
+  if (hlog) for (int i = 0; i < std::min<int>(hcap, (int)hl.size()); ++i) hlog[i] = hl[i];
+  return (int)hl.size();
+}
+int orc_replay(void* h, const double* x0, const double* ctrl, double T, int NI, const double* hlog, int n, double* xT, double* xb) {
+  Result r = rollout<double>(M(h), x0, ctrl, make_opts(T, NI, 0, 0, 0, 0), xT, xb, nullptr, nullptr, hlog, n);
+  return r.nsteps;
+}
+int orc_step_jacobian(void* h, const double* q, const double* v, const double* u, double hs, int cfd, double* Jx, double* Ju) {
+  Model& m = M(h);
+  std::vector<double> A, B;
+  step_jacobian(m, q, v, u, hs, cfd != 0, A, B);
+  std::copy(A.begin(), A.end(), Jx);
+  if (Ju && m.nu) std::copy(B.begin(), B.end(), Ju);
+  return 0;
+}
+int orc_rollout_grad(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol, double atol,
+                     double h0, int max_steps, int cfd, const double* xT_bar, const double* xb_bar, double* xT,
+                     double* x0_bar, double* ctrl_bar, int* stats) {
+  Result r = rollout_grad(M(h), x0, ctrl, make_opts(T, NI, rtol, atol, h0, max_steps), cfd != 0, xT_bar, xb_bar, xT, x0_bar, ctrl_bar);
+  put_stats(r, stats);
+  return 0;
+}
+
+int orc_batch_rollout(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, double rtol,
+                      double atol, double h0, int max_steps, double* xT, double* xb, int* stats, int nthreads) {
+  Model& m = M(h);
+  const int nx = m.nq + m.nv, nu = m.nu;
+  parallel_for(B, nthreads, [&](int b) {
+    Result r = rollout<double>(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr,
+                               make_opts(T[b], NI, rtol, atol, h0, max_steps), xT + (size_t)b * nx,
+                               xb ? xb + (size_t)b * (NI + 1) * nx : nullptr, nullptr, nullptr, nullptr, 0);
+    put_stats(r, stats + 4 * b);
+  });
+  return 0;
+}
+int orc_batch_grad(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, double rtol,
+                   double atol, double h0, int max_steps, int cfd, const double* xT_bar, const double* xb_bar,
+                   double* xT, double* x0_bar, double* ctrl_bar, int* stats, int nthreads) {
+  Model& m = M(h);
+  const int nx = m.nq + m.nv, nu = m.nu;
+  parallel_for(B, nthreads, [&](int b) {
+    Result r = rollout_grad(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr,
+                            make_opts(T[b], NI, rtol, atol, h0, max_steps), cfd != 0, xT_bar + (size_t)b * nx,
+                            xb_bar ? xb_bar + (size_t)b * (NI + 1) * nx : nullptr, xT + (size_t)b * nx,
+                            x0_bar + (size_t)b * nx, ctrl_bar ? ctrl_bar + (size_t)b * NI * nu : nullptr);
+    put_stats(r, stats + 4 * b);
+  });
+  return 0;
+}
+
+// Floating-point operations of one adaptive rollout (counted scalar type).
+long long orc_count_flops(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol, double atol,
+                          double h0, int max_steps, int* stats) {
+  Model& m = M(h);
+  const int nx = m.nq + m.nv, nu = m.nu;
+  std::vector<Cnt> xc(nx), uc((size_t)std::max(1, NI * nu)), xTc(nx);
+  for (int i = 0; i < nx; ++i) xc[i] = Cnt(x0[i]);
+  for (int i = 0; i < NI * nu; ++i) uc[i] = Cnt(ctrl[i]);
+  g_flops = 0;
+  Result r = rollout<Cnt>(m, xc.data(), uc.data(), make_opts(T, NI, rtol, atol, h0, max_steps), xTc.data(), nullptr,
+                          nullptr, nullptr, nullptr, 0);
+  put_stats(r, stats);
+  return (long long)g_flops;
+}
+
+}  // extern "C"

@@ -1,0 +1,335 @@
+// Oracle time integration and discrete adjoint.
+//
+// TEST INFRASTRUCTURE ONLY (see scalar.h).
+//
+// Paper passages followed (arXiv 2506.14186):
+//   Sec. 3.1           adaptive embedded Runge-Kutta: two orders give an error
+//                      estimate, accept/reject, a controller picks the next step
+//   App. B.1 (Fig. 12) PID step-size controller with P = 0.2, I = 0.4, D = 0
+//   App. C.2           Dormand-Prince 5(4) (cited there) with quaternions
+//                      integrated exactly; discretize-then-optimize gradient
+//   Sec. 4 (ST)        x' = sg(F) + F~ - sg(F~): values from F, derivatives
+//                      from F~ evaluated on the F trajectory
+// Step sizes of accepted steps are held constant in the derivative; rejected
+// attempts contribute nothing.
+#pragma once
+#include <cmath>
+#include <vector>
+
+#include "dynamics.h"
+
+namespace orc {
+
+// Dormand & Prince (1980) 5(4) tableau; row 7 equals the 5th-order weights
+// (first-same-as-last), bhat are the embedded 4th-order weights.
+struct Tableau {
+  double a[7][7];
+  double b[7], bhat[7], c[7];
+};
+inline const Tableau& dopri5() {
+  static const Tableau T = [] {
+    Tableau t{};
+    t.a[1][0] = 1.0 / 5.0;
+    t.a[2][0] = 3.0 / 40.0; t.a[2][1] = 9.0 / 40.0;
+    t.a[3][0] = 44.0 / 45.0; t.a[3][1] = -56.0 / 15.0; t.a[3][2] = 32.0 / 9.0;
+    t.a[4][0] = 19372.0 / 6561.0; t.a[4][1] = -25360.0 / 2187.0; t.a[4][2] = 64448.0 / 6561.0; t.a[4][3] = -212.0 / 729.0;
+    t.a[5][0] = 9017.0 / 3168.0; t.a[5][1] = -355.0 / 33.0; t.a[5][2] = 46732.0 / 5247.0; t.a[5][3] = 49.0 / 176.0;
+    t.a[5][4] = -5103.0 / 18656.0;
+    t.a[6][0] = 35.0 / 384.0; t.a[6][1] = 0.0; t.a[6][2] = 500.0 / 1113.0; t.a[6][3] = 125.0 / 192.0;
+    t.a[6][4] = -2187.0 / 6784.0; t.a[6][5] = 11.0 / 84.0;
+    for (int j = 0; j < 7; ++j) t.b[j] = (j < 6) ? t.a[6][j] : 0.0;
+    const double bh[7] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
+    const double c[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
+    for (int j = 0; j < 7; ++j) { t.bhat[j] = bh[j]; t.c[j] = c[j]; }
+    return t;
+  }();
+  return T;
+}
+
+// q (+) delta: positions advanced by a tangent increment.  Free joint:
+// translation += delta[0:3] (world), quaternion <- normalize(quat * exp(delta[3:6] / 2))
+// with the rotation increment in body coordinates.  Hinge: angle += delta.
+template <class S> void integrate_pos(const Model& m, const S* q, const S* dlt, S* out) {
+  for (const Body& B : m.body) {
+    const S* x = q + B.qadr;
+    const S* d = dlt + B.vadr;
+    S* o = out + B.qadr;
+    if (B.jtype == JNT_HINGE) { o[0] = x[0] + d[0]; continue; }
+    for (int i = 0; i < 3; ++i) o[i] = x[i] + d[i];
+    S th2 = d[3] * d[3] + d[4] * d[4] + d[5] * d[5];
+    S cw, sk;   // cos(|th|/2), sin(|th|/2)/|th|
+    if (val(th2) < 1e-12) {
+      cw = 1.0 - th2 / 8.0 + th2 * th2 / 384.0;
+      sk = 0.5 - th2 / 48.0 + th2 * th2 / 3840.0;
+    } else {
+      S th = sqrt(th2);
+      cw = cos(0.5 * th);
+      sk = sin(0.5 * th) / th;
+    }
+    S ew = cw, ex = sk * d[3], ey = sk * d[4], ez = sk * d[5];
+    S w = x[3], a = x[4], b = x[5], c = x[6];
+    S rw = w * ew - a * ex - b * ey - c * ez;
+    S rx = w * ex + a * ew + b * ez - c * ey;
+    S ry = w * ey - a * ez + b * ew + c * ex;
+    S rz = w * ez + a * ey - b * ex + c * ew;
+    S n = sqrt(rw * rw + rx * rx + ry * ry + rz * rz);
+    o[3] = rw / n; o[4] = rx / n; o[5] = ry / n; o[6] = rz / n;
+  }
+}
+
+// Magnitude of the coordinate belonging to tangent component i of the
+// position part (free-joint rotation components have magnitude 1).
+template <class S> S pos_magnitude(const Model& m, const S* q, int i) {
+  const Body& B = m.body[m.dof_body[i]];
+  if (B.jtype == JNT_HINGE) return fabs(q[B.qadr]);
+  const int d = i - B.vadr;
+  return d < 3 ? fabs(q[B.qadr + d]) : S(1.0);
+}
+
+// RMS error norm of the embedded difference e (2 nv tangent components).
+template <class S>
+S error_norm(const Model& m, const S* q0, const S* v0, const S* q1, const S* v1, const S* e, double rtol, double atol) {
+  const int nv = m.nv;
+  S acc = S(0.0);
+  for (int i = 0; i < nv; ++i) {
+    S sc = atol + rtol * smax(pos_magnitude(m, q0, i), pos_magnitude(m, q1, i));
+    S r = e[i] / sc;
+    acc = acc + r * r;
+  }
+  for (int i = 0; i < nv; ++i) {
+    S sc = atol + rtol * smax(fabs(v0[i]), fabs(v1[i]));
+    S r = e[nv + i] / sc;
+    acc = acc + r * r;
+  }
+  return sqrt(acc / (2.0 * nv));
+}
+
+// Stage right-hand side.  Values always from F; with cfd and a derivative
+// type, the tangent is taken from F~ at the same state (straight-through).
+template <class S> struct StageRhs {
+  const Model& m;
+  bool cfd;
+  bool noconv = false;
+  bool operator()(const S* q, const S* v, const S* u, S* a) {
+    bool ok = rhs<S>(m, q, v, u, false, a);
+    if (!ok) noconv = true;
+    return ok;
+  }
+};
+template <> struct StageRhs<Dual<double>> {
+  using D = Dual<double>;
+  const Model& m;
+  bool cfd;
+  bool noconv = false;
+  bool operator()(const D* q, const D* v, const D* u, D* a) {
+    bool ok = rhs<D>(m, q, v, u, false, a);
+    if (cfd) {
+      std::vector<D> at(m.nv);
+      rhs<D>(m, q, v, u, true, at.data());
+      for (int i = 0; i < m.nv; ++i) a[i].d = at[i].d;   // ST: value of F, tangent of F~
+    }
+    if (!ok) noconv = true;
+    return ok;
+  }
+};
+
+// One DOPRI5 attempt of size h from (q, v) with stage-1 derivative a1.
+// Writes the 5th-order solution (q7, v7), its derivative a7 (FSAL) and the
+// embedded difference e (2 nv tangent components).
+template <class S, class R>
+void dopri5_step(const Model& m, R& f, const S* q, const S* v, const S* a1, const S* u, double h,
+                 S* q7, S* v7, S* a7, S* e) {
+  const Tableau& tb = dopri5();
+  const int nv = m.nv, nq = m.nq;
+  std::vector<std::vector<S>> ks_v(7, std::vector<S>(nv)), ks_a(7, std::vector<S>(nv));
+  for (int i = 0; i < nv; ++i) { ks_v[0][i] = v[i]; ks_a[0][i] = a1[i]; }
+  std::vector<S> dq(nv), qs(nq), vs(nv);
+  for (int s = 1; s < 7; ++s) {
+    for (int i = 0; i < nv; ++i) {
+      S sq = S(0.0), sv = S(0.0);
+      for (int j = 0; j < s; ++j) {
+        if (tb.a[s][j] == 0.0) continue;
+        sq = sq + tb.a[s][j] * ks_v[j][i];
+        sv = sv + tb.a[s][j] * ks_a[j][i];
+      }
+      dq[i] = h * sq;
+      vs[i] = v[i] + h * sv;
+    }
+    integrate_pos(m, q, dq.data(), qs.data());
+    for (int i = 0; i < nv; ++i) ks_v[s][i] = vs[i];
+    f(qs.data(), vs.data(), u, ks_a[s].data());
+    if (s == 6) {
+      for (int i = 0; i < nq; ++i) q7[i] = qs[i];
+      for (int i = 0; i < nv; ++i) { v7[i] = vs[i]; a7[i] = ks_a[6][i]; }
+    }
+  }
+  for (int i = 0; i < nv; ++i) {
+    S ep = S(0.0), ev = S(0.0);
+    for (int j = 0; j < 7; ++j) {
+      double w = tb.b[j] - tb.bhat[j];
+      if (w == 0.0) continue;
+      ep = ep + w * ks_v[j][i];
+      ev = ev + w * ks_a[j][i];
+    }
+    e[i] = h * ep;
+    e[nv + i] = h * ev;
+  }
+}
+
+struct Opts {
+  double T = 1.0;
+  int NI = 1;
+  double rtol = 1e-6, atol = 1e-8, h0 = 1e-3;
+  int max_steps = 100000;
+};
+struct Result {
+  int status = ENV_OK, nsteps = 0, nrej = 0, nrhs = 0;
+};
+struct StepRec {
+  std::vector<double> q, v;
+  double h;
+  int k;          // control interval of the step
+  bool reached;   // the step ends on the boundary of interval k
+};
+
+inline double boundary_time(double T, int NI, int k) { return k >= NI ? T : T * k / NI; }
+
+// Adaptive rollout (replay == nullptr) or replay of given accepted step sizes.
+// x0 = [q; v], ctrl = [NI][nu].  xb (optional) receives the states at the NI+1
+// interval boundaries; rec (optional) the accepted steps.
+template <class S>
+Result rollout(const Model& m, const S* x0, const S* ctrl, const Opts& o, S* xT, S* xb,
+               std::vector<StepRec>* rec, std::vector<double>* hlog, const double* replay, int nreplay) {
+  const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
+  Result res;
+  std::vector<S> q(x0, x0 + nq), v(x0 + nq, x0 + nx), a1(nv), q7(nq), v7(nv), a7(nv), e(2 * nv);
+  for (int i = 0; i < nx; ++i) xT[i] = x0[i];
+  bool finite = true;
+  for (int i = 0; i < nx; ++i) finite = finite && std::isfinite(val(x0[i]));
+  if (xb) for (int i = 0; i < nx; ++i) xb[i] = x0[i];
+  if (!finite) { res.status = ENV_NONFINITE; return res; }
+  StageRhs<S> f{m, false};
+  auto uk = [&](int k) { return nu ? ctrl + (size_t)k * nu : ctrl; };
+  int k = 0;
+  double t = 0.0;
+  f(q.data(), v.data(), uk(0), a1.data());
+  res.nrhs = 1;
+  double h = o.h0;
+  double err_prev = 1.0;
+  int attempts = 0, ir = 0;
+  while (t < o.T) {
+    if (replay) { if (ir >= nreplay) break; h = replay[ir]; }
+    else if (attempts >= o.max_steps) { res.status = ENV_MAX_STEPS; break; }
+    const double tn = boundary_time(o.T, o.NI, k + 1);
+    const double hb = tn - t;
+    const bool clamped = replay ? (h == hb) : (h >= hb || hb - h < 1e-12);
+    const double ht = clamped ? hb : h;
+    if (!replay && ht < 1e-12) { res.status = ENV_H_UNDERFLOW; break; }
+    f.noconv = false;
+    dopri5_step(m, f, q.data(), v.data(), a1.data(), uk(k), ht, q7.data(), v7.data(), a7.data(), e.data());
+    res.nrhs += 6;
+    ++attempts;
+    double err = replay ? 0.0 : val(error_norm<S>(m, q.data(), v.data(), q7.data(), v7.data(), e.data(), o.rtol, o.atol));
+    if (err <= 1.0) {
+      if (f.noconv) { res.status = ENV_SOLVER_NOCONV; break; }
+      if (rec) {
+        StepRec r;
+        r.q.resize(nq); r.v.resize(nv);
+        for (int i = 0; i < nq; ++i) r.q[i] = val(q[i]);
+        for (int i = 0; i < nv; ++i) r.v[i] = val(v[i]);
+        r.h = ht; r.k = k; r.reached = false;
+        rec->push_back(r);
+      }
+      if (hlog) hlog->push_back(ht);
+      const bool reached = clamped || (t + ht >= tn);
+      t = reached ? tn : t + ht;
+      q = q7; v = v7; a1 = a7;
+      ++res.nsteps;
+      ++ir;
+      const double errf = std::max(err, 1e-10);
+      double fac = 0.9 * std::pow(errf, -0.6 / 5.0) * std::pow(err_prev, 0.2 / 5.0);
+      fac = std::min(10.0, std::max(0.2, fac));
+      err_prev = errf;
+      h = ht * fac;
+      if (reached) {
+        if (rec) rec->back().reached = true;
+        ++k;
+        if (xb) {
+          for (int i = 0; i < nq; ++i) xb[(size_t)k * nx + i] = q[i];
+          for (int i = 0; i < nv; ++i) xb[(size_t)k * nx + nq + i] = v[i];
+        }
+        if (k < o.NI) { f(q.data(), v.data(), uk(k), a1.data()); res.nrhs += 1; }
+      }
+    } else {
+      ++res.nrej;
+      const double fac = std::isfinite(err) ? std::max(0.2, 0.9 * std::pow(err, -1.0 / 5.0)) : 0.2;
+      h = ht * fac;
+    }
+  }
+  for (int i = 0; i < nq; ++i) xT[i] = q[i];
+  for (int i = 0; i < nv; ++i) xT[nq + i] = v[i];
+  return res;
+}
+
+// Jacobian of one accepted DOPRI5 step (h fixed) of the map
+// (q, v, u) -> (q7, v7), by forward-mode derivatives, one input direction at a
+// time.  Jx is nx x nx, Ju is nx x nu (row major).  With cfd the derivatives
+// of every stage come from F~ (straight-through).
+inline void step_jacobian(const Model& m, const double* q, const double* v, const double* u, double h, bool cfd,
+                          std::vector<double>& Jx, std::vector<double>& Ju) {
+  using D = Dual<double>;
+  const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
+  Jx.assign((size_t)nx * nx, 0.0);
+  Ju.assign((size_t)nx * std::max(nu, 1), 0.0);
+  std::vector<D> qd(nq), vd(nv), ud(std::max(nu, 1)), a1(nv), q7(nq), v7(nv), a7(nv), e(2 * nv);
+  for (int dir = 0; dir < nx + nu; ++dir) {
+    for (int i = 0; i < nq; ++i) qd[i] = D(q[i], dir == i ? 1.0 : 0.0);
+    for (int i = 0; i < nv; ++i) vd[i] = D(v[i], dir == nq + i ? 1.0 : 0.0);
+    for (int i = 0; i < nu; ++i) ud[i] = D(u[i], dir == nx + i ? 1.0 : 0.0);
+    StageRhs<D> f{m, cfd};
+    f(qd.data(), vd.data(), ud.data(), a1.data());
+    dopri5_step(m, f, qd.data(), vd.data(), a1.data(), ud.data(), h, q7.data(), v7.data(), a7.data(), e.data());
+    for (int i = 0; i < nq; ++i) {
+      if (dir < nx) Jx[(size_t)i * nx + dir] = q7[i].d; else Ju[(size_t)i * nu + (dir - nx)] = q7[i].d;
+    }
+    for (int i = 0; i < nv; ++i) {
+      if (dir < nx) Jx[(size_t)(nq + i) * nx + dir] = v7[i].d; else Ju[(size_t)(nq + i) * nu + (dir - nx)] = v7[i].d;
+    }
+  }
+}
+
+// Discrete adjoint (discretize-then-optimize) over the accepted steps of the
+// adaptive rollout: x0_bar = d/dx0 <xT_bar, xT> + sum_k <xb_bar[k], x(t_k)>,
+// ctrl_bar likewise for the piecewise-constant controls.
+inline Result rollout_grad(const Model& m, const double* x0, const double* ctrl, const Opts& o, bool cfd,
+                           const double* xT_bar, const double* xb_bar, double* xT, double* x0_bar, double* ctrl_bar) {
+  const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
+  std::vector<StepRec> rec;
+  Result res = rollout<double>(m, x0, ctrl, o, xT, nullptr, &rec, nullptr, nullptr, 0);
+  std::vector<double> lam(xT_bar, xT_bar + nx), Jx, Ju, nl(nx);
+  if (ctrl_bar) for (int i = 0; i < o.NI * nu; ++i) ctrl_bar[i] = 0.0;
+  for (int n = (int)rec.size() - 1; n >= 0; --n) {
+    const StepRec& r = rec[n];
+    if (r.reached && xb_bar)
+      for (int i = 0; i < nx; ++i) lam[i] += xb_bar[(size_t)(r.k + 1) * nx + i];
+    const double* u = nu ? ctrl + (size_t)r.k * nu : ctrl;
+    step_jacobian(m, r.q.data(), r.v.data(), u, r.h, cfd, Jx, Ju);
+    if (ctrl_bar)
+      for (int j = 0; j < nu; ++j) {
+        double s = 0;
+        for (int i = 0; i < nx; ++i) s += Ju[(size_t)i * nu + j] * lam[i];
+        ctrl_bar[(size_t)r.k * nu + j] += s;
+      }
+    for (int j = 0; j < nx; ++j) {
+      double s = 0;
+      for (int i = 0; i < nx; ++i) s += Jx[(size_t)i * nx + j] * lam[i];
+      nl[j] = s;
+    }
+    lam = nl;
+  }
+  if (xb_bar) for (int i = 0; i < nx; ++i) lam[i] += xb_bar[i];
+  for (int i = 0; i < nx; ++i) x0_bar[i] = lam[i];
+  return res;
+}
+
+}  // namespace orc

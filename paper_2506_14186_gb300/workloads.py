@@ -1,0 +1,251 @@
+"""Scene descriptions and seeded synthetic inputs for the four rollout workloads.
+
+This module holds input data only (geometry, masses, solver parameters and
+seeded random initial states / controls).  It performs none of the method's
+arithmetic, imports nothing else from this package, and is the one module that
+both the CUDA path and the CPU oracle are fed from.
+
+Scenes are plain dicts:
+
+  bodies    : parent (-1 = world, parents precede children), joint ('free' |
+              'hinge'), pos, quat (w, x, y, z) of the body frame in the parent
+              frame, axis (hinge, body frame), mass, com (body frame), inertia
+              (principal moments about the COM, body axes), damping
+  geoms     : type ('sphere' | 'capsule' | 'box'), body, pos, quat, size
+              (sphere: radius; capsule: radius, half length along local x;
+              box: half extents)
+  pairs     : geom1, geom2 (-1 = ground plane z = 0), condim (1 frictionless,
+              3 pyramidal friction with 4 edges), mu
+  actuators : type ('motor' | 'position'), body (hinge), gear, kp, kd
+  options   : gravity, solref (t_c, phi_d), solimp (d_o, d_w, width,
+              midpoint, power), solimp_cfd (d_c, d_0, w_c, m_c, p_c),
+              softplus width
+  qpos0     : reference configuration
+
+Solver parameters follow the paper: solref time constant 0.002 s with damping
+ratio 1 (the stiff setting), solimp (0, 0.95, 0.001, 0.5, 2) (Sec. 3 object
+tosses, App. D.1), solimp-CFD tuple order (d_c, d_0, w_c, m_c, p_c) (Sec. 4).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GRAVITY = (0.0, 0.0, -9.81)
+SOLREF = (0.002, 1.0)
+SOLIMP = (0.0, 0.95, 0.001, 0.5, 2.0)
+SOLIMP_CFD = (0.0, 0.0, 0.05, 1.0, 4.0)
+SOFTPLUS = 1e-3
+IDQ = (1.0, 0.0, 0.0, 0.0)
+
+
+def _options(solimp=SOLIMP, solimp_cfd=SOLIMP_CFD, softplus=SOFTPLUS, gravity=GRAVITY, solref=SOLREF):
+    return {"gravity": list(gravity), "solref": list(solref), "solimp": list(solimp),
+            "solimp_cfd": list(solimp_cfd), "softplus": float(softplus)}
+
+
+def _free_body(mass, inertia, parent=-1):
+    return {"parent": parent, "joint": "free", "pos": [0.0, 0.0, 0.0], "quat": list(IDQ), "axis": [0.0, 0.0, 1.0],
+            "mass": mass, "com": [0.0, 0.0, 0.0], "inertia": list(inertia), "damping": 0.0}
+
+
+def _hinge_body(parent, pos, axis, mass, com, inertia, damping=0.0, quat=IDQ):
+    return {"parent": parent, "joint": "hinge", "pos": list(pos), "quat": list(quat), "axis": list(axis),
+            "mass": mass, "com": list(com), "inertia": list(inertia), "damping": damping}
+
+
+def _geom(gtype, body, size, pos=(0.0, 0.0, 0.0), quat=IDQ):
+    s = list(size) + [0.0] * (3 - len(size))
+    return {"type": gtype, "body": body, "pos": list(pos), "quat": list(quat), "size": s}
+
+
+def _pair(g1, g2, condim, mu):
+    return {"geom1": g1, "geom2": g2, "condim": condim, "mu": mu}
+
+
+def sphere_inertia(m, r):
+    return [0.4 * m * r * r] * 3
+
+
+def box_inertia(m, hx, hy, hz):
+    a, b, c = 2 * hx, 2 * hy, 2 * hz
+    return [m * (b * b + c * c) / 12.0, m * (a * a + c * c) / 12.0, m * (a * a + b * b) / 12.0]
+
+
+def rod_inertia(m, r, length):
+    """Solid cylinder along the local x axis (used for capsule links)."""
+    return [0.5 * m * r * r, m * (3 * r * r + length * length) / 12.0, m * (3 * r * r + length * length) / 12.0]
+
+
+# --------------------------------------------------------------------------- scenes
+def ball_scene(radius=0.1, mass=1.0, **opt):
+    """Free sphere (6 dof, frictionless) above the ground plane."""
+    return {"name": "ball",
+            "bodies": [_free_body(mass, sphere_inertia(mass, radius))],
+            "geoms": [_geom("sphere", 0, [radius])],
+            "pairs": [_pair(0, -1, 1, 0.0)],
+            "actuators": [],
+            "options": _options(**opt),
+            "qpos0": [0.0, 0.0, radius, 1.0, 0.0, 0.0, 0.0]}
+
+
+def box_scene(half=0.05, mass=1.0, mu=1.0, **opt):
+    """Free cube on the ground plane, pyramidal friction, 8 vertex contacts."""
+    return {"name": "box",
+            "bodies": [_free_body(mass, box_inertia(mass, half, half, half))],
+            "geoms": [_geom("box", 0, [half, half, half])],
+            "pairs": [_pair(0, -1, 3, mu)],
+            "actuators": [],
+            "options": _options(**opt),
+            "qpos0": [0.0, 0.0, half, 1.0, 0.0, 0.0, 0.0]}
+
+
+CHAIN_LINKS = 7
+CHAIN_LINK = 0.3
+CHAIN_RADIUS = 0.025
+CHAIN_HEIGHT = 0.05
+CUBE_START = (1.85, 0.25, 0.05)
+CUBE_GOAL = (2.0, 0.5, 0.05)
+
+
+def chain_cube_scene(mu=1.0, **opt):
+    """Fixed-base planar arm of 7 z-axis hinges with capsule links (0.3 m, 1 kg,
+    joint damping 0.1, torque motors) and a free 0.1 m cube on the plane."""
+    bodies, geoms, pairs, acts = [], [], [], []
+    for i in range(CHAIN_LINKS):
+        parent = i - 1
+        pos = (0.0, 0.0, CHAIN_HEIGHT) if i == 0 else (CHAIN_LINK, 0.0, 0.0)
+        bodies.append(_hinge_body(parent, pos, (0, 0, 1), 1.0, (CHAIN_LINK / 2, 0, 0),
+                                  rod_inertia(1.0, CHAIN_RADIUS, CHAIN_LINK), damping=0.1))
+        geoms.append(_geom("capsule", i, [CHAIN_RADIUS, CHAIN_LINK / 2], pos=(CHAIN_LINK / 2, 0, 0)))
+        acts.append({"type": "motor", "body": i, "gear": 1.0, "kp": 0.0, "kd": 0.0})
+    cube = len(bodies)
+    bodies.append(_free_body(1.0, box_inertia(1.0, 0.05, 0.05, 0.05)))
+    gcube = len(geoms)
+    geoms.append(_geom("box", cube, [0.05, 0.05, 0.05]))
+    pairs.append(_pair(gcube, -1, 3, mu))
+    for i in range(CHAIN_LINKS):
+        pairs.append(_pair(i, gcube, 3, mu))
+    for i in range(CHAIN_LINKS):
+        pairs.append(_pair(i, -1, 3, mu))
+    qpos0 = [0.0] * CHAIN_LINKS + list(CUBE_START) + list(IDQ)
+    return {"name": "chain_cube", "bodies": bodies, "geoms": geoms, "pairs": pairs, "actuators": acts,
+            "options": _options(**opt), "qpos0": qpos0}
+
+
+QUAD_TORSO = (0.2, 0.1, 0.05)
+QUAD_LINK = 0.2
+QUAD_LINK_RADIUS = 0.02
+QUAD_FOOT = 0.025
+QUAD_HEIGHT = 0.45
+
+
+def quadruped_scene(mu=0.8, kp=50.0, kd=1.0, **opt):
+    """Box torso (0.4 x 0.2 x 0.1 m, 8 kg, free joint) with four legs of three
+    hinges (abduction about x, hip and knee about y), 0.2 m capsule links of
+    0.5 kg, sphere feet on the plane, PD position servos on all 12 hinges."""
+    bodies = [_free_body(8.0, box_inertia(8.0, *QUAD_TORSO))]
+    geoms = [_geom("box", 0, list(QUAD_TORSO))]
+    pairs, acts = [], []
+    # links lie along the body -z axis: transverse moments about x and y
+    link_inertia = [0.5 * (3 * QUAD_LINK_RADIUS ** 2 + QUAD_LINK ** 2) / 12.0] * 2 + [0.5 * 0.5 * QUAD_LINK_RADIUS ** 2]
+    for sx in (1.0, -1.0):
+        for sy in (1.0, -1.0):
+            hip = (sx * 0.18, sy * 0.1, 0.0)
+            ab = len(bodies)
+            bodies.append(_hinge_body(0, hip, (1, 0, 0), 0.5, (0, 0, 0), sphere_inertia(0.5, 0.03)))
+            th = len(bodies)
+            bodies.append(_hinge_body(ab, (0, 0, 0), (0, 1, 0), 0.5, (0, 0, -QUAD_LINK / 2), link_inertia))
+            # capsule along the link: local x of the geom is rotated onto -z
+            qdown = (math.cos(math.pi / 4), 0.0, math.sin(math.pi / 4), 0.0)
+            geoms.append(_geom("capsule", th, [QUAD_LINK_RADIUS, QUAD_LINK / 2], pos=(0, 0, -QUAD_LINK / 2), quat=qdown))
+            sh = len(bodies)
+            bodies.append(_hinge_body(th, (0, 0, -QUAD_LINK), (0, 1, 0), 0.5, (0, 0, -QUAD_LINK / 2), link_inertia))
+            geoms.append(_geom("capsule", sh, [QUAD_LINK_RADIUS, QUAD_LINK / 2], pos=(0, 0, -QUAD_LINK / 2), quat=qdown))
+            foot = len(geoms)
+            geoms.append(_geom("sphere", sh, [QUAD_FOOT], pos=(0, 0, -QUAD_LINK)))
+            pairs.append(_pair(foot, -1, 3, mu))
+            for b in (ab, th, sh):
+                acts.append({"type": "position", "body": b, "gear": 1.0, "kp": kp, "kd": kd})
+    qpos0 = [0.0, 0.0, QUAD_HEIGHT] + list(IDQ) + [0.0] * 12
+    return {"name": "quadruped", "bodies": bodies, "geoms": geoms, "pairs": pairs, "actuators": acts,
+            "options": _options(**opt), "qpos0": qpos0}
+
+
+def scene_dims(scene):
+    nq = sum(7 if b["joint"] == "free" else 1 for b in scene["bodies"])
+    nv = sum(6 if b["joint"] == "free" else 1 for b in scene["bodies"])
+    return nq, nv, len(scene["actuators"])
+
+
+# --------------------------------------------------------------------------- inputs
+def _rng(seed):
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def _yaw_quat(yaw):
+    return np.stack([np.cos(yaw / 2), np.zeros_like(yaw), np.zeros_like(yaw), np.sin(yaw / 2)], axis=-1)
+
+
+def ball_inputs(B=16, seed=1001, T=1.0):
+    """Ball drops: centre height 0.1 + U[0.5, 1.5] m, v0 ~ N(0, 0.5^2) per axis,
+    identity orientation, zero angular velocity."""
+    g = _rng(seed)
+    x0 = np.zeros((B, 13))
+    x0[:, 0:2] = 0.0
+    x0[:, 2] = 0.1 + g.uniform(0.5, 1.5, B)
+    x0[:, 3] = 1.0
+    x0[:, 7:10] = g.normal(0.0, 0.5, (B, 3))
+    return {"x0": x0, "ctrl": None, "T": np.full(B, T), "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3,
+            "max_steps": 20000}
+
+
+def box_push_inputs(B=4096, seed=1002, T=1.0):
+    """Box pushes: cube resting on the plane (bottom face at z = 0), yaw ~
+    U[-pi, pi], planar push speed ~ U[0, 2] m/s along a direction ~ U[0, 2 pi)."""
+    g = _rng(seed)
+    x0 = np.zeros((B, 13))
+    x0[:, 2] = 0.05
+    x0[:, 3:7] = _yaw_quat(g.uniform(-math.pi, math.pi, B))
+    speed = g.uniform(0.0, 2.0, B)
+    th = g.uniform(0.0, 2 * math.pi, B)
+    x0[:, 7] = speed * np.cos(th)
+    x0[:, 8] = speed * np.sin(th)
+    return {"x0": x0, "ctrl": None, "T": np.full(B, T), "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3,
+            "max_steps": 20000}
+
+
+def chain_inputs(B=16384, seed=1003, T=2.0, NI=50):
+    """Arm at rest straight along +x with the cube resting at its start;
+    torques u ~ N(0, 1) N m per hinge and control interval."""
+    g = _rng(seed)
+    scene = chain_cube_scene()
+    nq, nv, nu = scene_dims(scene)
+    x0 = np.zeros((B, nq + nv))
+    x0[:, :nq] = np.asarray(scene["qpos0"])
+    ctrl = g.normal(0.0, 1.0, (B, NI, nu))
+    return {"x0": x0, "ctrl": ctrl, "T": np.full(B, T), "NI": NI, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3,
+            "max_steps": 20000}
+
+
+def quadruped_inputs(B=8192, seed=1004):
+    """Quadruped released at torso height 0.45 m with zero velocity; PD joint
+    targets ~ U[-0.3, 0.3] rad held over the horizon T ~ U[0.5, 3] s."""
+    g = _rng(seed)
+    scene = quadruped_scene()
+    nq, nv, nu = scene_dims(scene)
+    x0 = np.zeros((B, nq + nv))
+    x0[:, :nq] = np.asarray(scene["qpos0"])
+    ctrl = g.uniform(-0.3, 0.3, (B, 1, nu))
+    T = g.uniform(0.5, 3.0, B)
+    return {"x0": x0, "ctrl": ctrl, "T": T, "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3, "max_steps": 20000}
+
+
+def chain_goal():
+    return np.asarray(CUBE_GOAL)
+
+
+SCENES = {"ball": ball_scene, "box": box_scene, "chain_cube": chain_cube_scene, "quadruped": quadruped_scene}
+INPUTS = {"ball": ball_inputs, "box": box_push_inputs, "chain_cube": chain_inputs, "quadruped": quadruped_inputs}

@@ -1,0 +1,199 @@
+"""Pins of the oracle's discrete adjoint (discretize-then-optimize over the
+accepted steps) and of the straight-through CFD gradient: closed forms,
+frozen-step central differences, and the properties the paper states for the
+straight-through estimator (Sec. 4, App. C.3)."""
+
+import numpy as np
+import pytest
+
+from paper_2506_14186_gb300 import workloads as W
+from tests.conftest import rel_err
+
+CFD_OPT = dict(solimp=(0.1, 0.95, 0.001, 0.5, 2.0), solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+
+
+def test_ballistic_gradient_closed_form(orc):
+    m = orc.OracleModel(W.ball_scene())
+    x0 = np.array([0.1, -0.2, 2.0, 1, 0, 0, 0, 0.7, -0.4, 1.5, 0, 0, 0])
+    T = 0.4
+    xbar = np.zeros(13); xbar[2] = 1.0                     # L = z_T
+    g = m.rollout_grad(x0, xbar, T=T)["x0_bar"]
+    ref = np.zeros(13); ref[2] = 1.0; ref[9] = T
+    np.testing.assert_allclose(g, ref, atol=1e-13)
+    xbar = np.zeros(13); xbar[0] = 1.0; xbar[7] = 2.0      # L = x_T + 2 vx_T
+    g = m.rollout_grad(x0, xbar, T=T)["x0_bar"]
+    ref = np.zeros(13); ref[0] = 1.0; ref[7] = T + 2.0
+    np.testing.assert_allclose(g, ref, atol=1e-13)
+
+
+def _frozen_fd(m, x0, hlog, wT, ctrl=None, T=1.0, NI=1, eps=1e-6, wb=None):
+    """Central differences of <wT, xT> (+ sum_k <wb_k, x(t_k)>) of the replayed
+    (frozen-step) discrete map w.r.t. x0 and the controls."""
+    def L(x, c):
+        xT, xb = m.replay(x, hlog, ctrl=c, T=T, NI=NI)
+        val = wT @ xT
+        if wb is not None:
+            val += (wb * xb).sum()
+        return val
+    gx = np.zeros(m.nx)
+    for i in range(m.nx):
+        e = np.zeros(m.nx); e[i] = eps
+        gx[i] = (L(x0 + e, ctrl) - L(x0 - e, ctrl)) / (2 * eps)
+    gu = None
+    if ctrl is not None and m.nu:
+        gu = np.zeros_like(ctrl)
+        for idx in np.ndindex(ctrl.shape):
+            e = np.zeros_like(ctrl); e[idx] = eps
+            gu[idx] = (L(x0, ctrl + e) - L(x0, ctrl - e)) / (2 * eps)
+    return gx, gu
+
+
+def test_step_jacobian_matches_differences(orc):
+    m = orc.OracleModel(W.box_scene())
+    x0 = W.box_push_inputs(1, seed=5)["x0"][0]
+    r = m.rollout(x0, T=0.02)
+    q, v = r["xT"][:7], r["xT"][7:]
+    h = 1e-3
+    Jx, _ = m.step_jacobian(q, v, None, h)
+    eps = 1e-7
+    for i in range(13):
+        e = np.zeros(13); e[i] = eps
+        xp, _ = m.replay(r["xT"] + e, [h], T=h)
+        xm, _ = m.replay(r["xT"] - e, [h], T=h)
+        np.testing.assert_allclose(Jx[:, i], (xp - xm) / (2 * eps), atol=1e-6)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_ball_bounce_gradient_frozen_steps(orc, seed):
+    m = orc.OracleModel(W.ball_scene())
+    x0 = W.ball_inputs(3, seed=seed)["x0"][seed]
+    r = m.rollout(x0, T=1.0)
+    w = np.zeros(13); w[2] = 1.0; w[7] = 0.3; w[9] = -0.5
+    g = m.rollout_grad(x0, w, T=1.0)
+    np.testing.assert_array_equal(g["xT"], r["xT"])
+    assert _best_fd_err(m, x0, r["hlog"], w, g) < 1e-5
+
+
+def _best_fd_err(m, x0, hlog, w, g, **kw):
+    """Stiff contact makes the frozen-step map strongly curved: central
+    differences converge to the derivative as eps shrinks, so take the best
+    of a small eps sweep (truncation vs round-off)."""
+    errs = []
+    for eps in (1e-6, 1e-7, 1e-8):
+        fdx, fdu = _frozen_fd(m, x0, hlog, w, eps=eps, **kw)
+        e = rel_err(g["x0_bar"], fdx)
+        if fdu is not None:
+            e = max(e, rel_err(g["ctrl_bar"].ravel(), fdu.ravel()))
+        errs.append(e)
+    return min(errs)
+
+
+@pytest.mark.parametrize("T", [0.01, 0.1])
+def test_box_gradient_frozen_steps(orc, T):
+    """Box launched by a push at its base (tumbling, sliding and landing on
+    corners): adjoint vs central differences of the replayed map."""
+    m = orc.OracleModel(W.box_scene())
+    x0 = np.array([0, 0, 0.0497, 1, 0, 0, 0, 2.0, 0.5, 0, 0, 0, 0.0])
+    x1 = m.rollout(x0, T=0.02)["xT"]
+    r = m.rollout(x1, T=T)
+    w = np.random.default_rng(1).normal(size=13)
+    g = m.rollout_grad(x1, w, T=T)
+    assert _best_fd_err(m, x1, r["hlog"], w, g, T=T) < 1e-5
+
+
+def test_chain_control_gradient_frozen_steps(orc):
+    """Chain + cube, piecewise-constant torques: gradient w.r.t. x0 and every
+    control of every interval, with interval-boundary cotangents."""
+    sc = W.chain_cube_scene()
+    m = orc.OracleModel(sc)
+    inp = W.chain_inputs(1, T=0.3, NI=6)
+    x0, ctrl = inp["x0"][0], inp["ctrl"][0]
+    r = m.rollout(x0, ctrl=ctrl, T=0.3, NI=6)
+    g_ = np.random.default_rng(2)
+    w = g_.normal(size=m.nx)
+    wb = g_.normal(size=(7, m.nx))
+    g = m.rollout_grad(x0, w, ctrl=ctrl, T=0.3, NI=6, xb_bar=wb)
+    # the cube starts resting on the plane, where pyramid rows sit at the edge of
+    # the active set (kinks of the map): compare the arm's state and the controls
+    arm = list(range(7)) + list(range(14, 21))
+    best = []
+    for eps in (1e-6, 1e-7):
+        fdx, fdu = _frozen_fd(m, x0, r["hlog"], w, ctrl=ctrl, T=0.3, NI=6, wb=wb, eps=eps)
+        best.append(max(rel_err(g["x0_bar"][arm], fdx[arm]), rel_err(g["ctrl_bar"].ravel(), fdu.ravel())))
+    assert min(best) < 1e-5
+
+
+def test_quadruped_gradient_frozen_steps(orc):
+    sc = W.quadruped_scene()
+    m = orc.OracleModel(sc)
+    inp = W.quadruped_inputs(1)
+    x0, ctrl = inp["x0"][0], inp["ctrl"][0]
+    T = 0.25
+    r = m.rollout(x0, ctrl=ctrl, T=T)
+    w = np.zeros(m.nx); w[0:3] = [1.0, 0.5, -0.7]
+    g = m.rollout_grad(x0, w, ctrl=ctrl, T=T)
+    assert _best_fd_err(m, x0, r["hlog"], w, g, ctrl=ctrl, T=T) < 1e-5
+
+
+def test_gradient_converges_with_tolerance(orc):
+    """Adaptive integration drives the discrete gradient towards the gradient of
+    the continuous flow as the tolerance shrinks (Sec. 3.1, Fig. 5): for a ball
+    in the middle of its impact, the error against a 1e-12 reference falls by
+    more than an order of magnitude from rtol 1e-6 to 1e-10."""
+    m = orc.OracleModel(W.ball_scene())
+    x0 = np.array([0, 0, 0.6, 1, 0, 0, 0, 0.3, 0, -0.5, 0, 0, 0.0])
+    w = np.zeros(13); w[2] = 1.0; w[9] = 0.1
+    g = {rt: m.rollout_grad(x0, w, T=0.33, rtol=rt, atol=rt * 1e-2)["x0_bar"] for rt in (1e-6, 1e-10, 1e-12)}
+    e6, e10 = rel_err(g[1e-6], g[1e-12]), rel_err(g[1e-10], g[1e-12])
+    assert e10 < 0.05 and e10 < e6 / 10
+
+
+# ---------------------------------------------------------------- straight-through CFD
+def test_cfd_does_not_change_the_forward_pass(orc):
+    m = orc.OracleModel(W.box_scene(**CFD_OPT))
+    x0 = W.box_push_inputs(2, seed=3)["x0"][0]
+    w = np.ones(13)
+    a = m.rollout_grad(x0, w, T=0.3, cfd=False)
+    b = m.rollout_grad(x0, w, T=0.3, cfd=True)
+    np.testing.assert_array_equal(a["xT"], b["xT"])
+    assert np.abs(a["x0_bar"] - b["x0_bar"]).max() > 1e-6
+
+
+def test_cfd_gradient_equals_plain_gradient_without_near_contacts(orc):
+    m = orc.OracleModel(W.ball_scene(**CFD_OPT))
+    x0 = np.array([0, 0, 3.0, 1, 0, 0, 0, 0.3, 0.2, 1.0, 0, 0, 0])   # stays above w_c
+    w = np.zeros(13); w[2] = 1.0; w[0] = 0.5
+    a = m.rollout_grad(x0, w, T=0.4, cfd=False)["x0_bar"]
+    b = m.rollout_grad(x0, w, T=0.4, cfd=True)["x0_bar"]
+    np.testing.assert_array_equal(a, b)
+
+
+def test_cfd_gives_informative_gradient_before_contact(orc):
+    """A ball gliding just above the plane (no gravity) never touches it: the
+    plain gradient of its final height w.r.t. its initial height is exactly 1,
+    the CFD gradient sees the plane within w_c (Sec. 4, billiard example)."""
+    m = orc.OracleModel(W.ball_scene(gravity=(0.0, 0.0, 0.0), **CFD_OPT))
+    x0 = np.array([0, 0, 0.12, 1, 0, 0, 0, 1.0, 0, 0, 0, 0, 0])
+    w = np.zeros(13); w[2] = 1.0
+    plain = m.rollout_grad(x0, w, T=0.5, cfd=False)
+    cfd = m.rollout_grad(x0, w, T=0.5, cfd=True)
+    assert abs(plain["x0_bar"][2] - 1.0) < 1e-14 and abs(plain["x0_bar"][9] - 0.5) < 1e-14
+    np.testing.assert_array_equal(plain["xT"], cfd["xT"])
+    # the CFD rows (damping term of a_ref, d(r) > 0 within w_c) react to the
+    # normal velocity: dz_T/dvz_0 departs from the free-flight value T
+    assert abs(cfd["x0_bar"][9] - 0.5) > 1e-2
+    assert np.all(np.isfinite(cfd["x0_bar"]))
+
+
+def test_cfd_step_jacobian_uses_cfd_rhs_at_the_plain_states(orc):
+    """With cfd, the derivative of one step is the derivative of the DOPRI5
+    step built from F~, but evaluated at the stage states of F (compare the
+    one-stage case h -> small: J ~ I + h [0 I; dF~/dq dF~/dv])."""
+    sc = W.ball_scene(gravity=(0.0, 0.0, 0.0), **CFD_OPT)
+    m = orc.OracleModel(sc)
+    q = np.array([0, 0, 0.12, 1, 0, 0, 0]); v = np.array([1.0, 0, -0.1, 0, 0, 0])
+    h = 1e-7
+    Jx, _ = m.step_jacobian(q, v, None, h, cfd=True)
+    Jq, Jv, _ = m.rhs_jacobian(q, v, None, cfd=True)
+    np.testing.assert_allclose((Jx[7:, :7]) / h, Jq, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose((Jx[7:, 7:] - np.eye(6)) / h, Jv, rtol=1e-5, atol=1e-6)
