@@ -1,0 +1,245 @@
+/*
+ * dmx.h -- C ABI of the GB300-native batched soft-contact rollout library.
+ *
+ * The library integrates many independent environments of a rigid-body
+ * system with MuJoCo-style soft contacts (arXiv 2506.14186, "Differentiable
+ * Simulation of Hard Contacts with Soft Gradients for Learning and Control"):
+ *
+ *   state x = [q, v], q in R^nq (free joints carry a unit quaternion), v in R^nv
+ *   (Sec. 2: x_{k+1} = step(x_k, a_k, p), loss L(x~_{k+1}, x_k, a_k, p))
+ *   v' = M^-1 (tau - c + J^T f)                              (Sec. 2, Eq. EOM)
+ *   f from the relaxed Gauss principle with reference acceleration
+ *   a_ref = -b (J v) - k d(r) r and regulariser R = A_hat (1 - d) / d
+ *                                           (Sec. 2.1, Eq. primal-problem)
+ *   integrated by adaptive Dormand-Prince 5(4) with a PID step-size
+ *   controller per environment                   (Sec. 3.1, App. B, App. C.2)
+ *   differentiated by the discrete adjoint over the accepted steps
+ *   (discretize-then-optimize, App. C.2), optionally with the straight-through
+ *   contacts-from-distance (CFD) right-hand side in the backward pass (Sec. 4).
+ *
+ * Conventions
+ *   - Batched arrays are structure-of-arrays: element (i, e) of an [n][B]
+ *     array is at i * B + e (environment index fastest).
+ *   - Unless a call says otherwise, array pointers are DEVICE pointers owned
+ *     by the caller; the library never frees caller memory.  Work is ordered
+ *     on the CUDA stream passed as `stream` (NULL = legacy default stream).
+ *   - Models, tapes and servers are owned by the library (create/destroy).
+ *   - Every call returns a dmx_status; on failure dmx_last_error() returns a
+ *     thread-local message.  No exception crosses the ABI.
+ *   - Per-environment failures do not fail a call: they are reported in the
+ *     caller's status[B] array (DMX_ENV_*), and that environment's outputs
+ *     hold its last accepted state.
+ */
+#ifndef DMX_H
+#define DMX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DMX_OK = 0,
+  DMX_ERR_INVALID = 1,        /* bad argument or model description */
+  DMX_ERR_OOM = 2,            /* device or host allocation failed */
+  DMX_ERR_CUDA = 3,           /* a CUDA call failed */
+  DMX_NOT_READY = 4,          /* dmx_poll: request still running */
+  DMX_ERR_TIMEOUT = 5,        /* a bounded wait ran out */
+  DMX_ERR_UNIMPLEMENTED = 6
+} dmx_status;
+
+/* per-environment status codes (status[B]) */
+enum {
+  DMX_ENV_OK = 0,
+  DMX_ENV_MAX_STEPS = 1,      /* step attempts reached max_steps before T (App. D.1 budget) */
+  DMX_ENV_H_UNDERFLOW = 2,    /* step size fell below 1e-12 s */
+  DMX_ENV_NONFINITE = 3,      /* non-finite initial state */
+  DMX_ENV_SOLVER_NOCONV = 4,  /* constraint Newton solve exceeded 50 iterations */
+  DMX_ENV_ROW_OVERFLOW = 5    /* more active constraint rows than the workspace holds */
+};
+
+enum { DMX_JNT_FREE = 0, DMX_JNT_HINGE = 1 };
+enum { DMX_GEOM_SPHERE = 0, DMX_GEOM_CAPSULE = 1, DMX_GEOM_BOX = 2 };
+enum { DMX_ACT_MOTOR = 0, DMX_ACT_POSITION = 1 };
+enum { DMX_FORM_PERSISTENT = 0, DMX_FORM_STEP = 1, DMX_FORM_STEP_GRAPH = 2 };
+
+/* ------------------------------------------------------------------ model */
+/* Body of a kinematic tree.  parent < own index (-1 = world).  A free joint
+ * (7 qpos: position, quaternion w,x,y,z; 6 dof: linear velocity in world
+ * axes, angular velocity in body axes) is allowed on children of the world
+ * only; a hinge rotates about `axis` (body frame) through the body origin. */
+typedef struct {
+  int32_t parent, joint;
+  double pos[3], quat[4];     /* body frame in the parent frame at q = 0 */
+  double axis[3];             /* hinge axis, body frame */
+  double mass, com[3];        /* COM in the body frame */
+  double inertia[3];          /* principal moments about the COM, body axes */
+  double damping;             /* joint damping (generalised force -damping * v) */
+} dmx_body_desc;
+
+/* Collision geometry fixed to a body.  size: sphere {r}, capsule {r, half
+ * length along local x}, box {half extents}. */
+typedef struct {
+  int32_t type, body;
+  double pos[3], quat[4], size[3];
+} dmx_geom_desc;
+
+/* Contact pair: geom1 against the ground plane z = 0 (geom2 = -1: sphere 1
+ * contact, capsule 2 end-sphere contacts, box 8 vertex contacts), or capsule
+ * geom1 against box geom2 (one contact).  condim 1 = frictionless normal row,
+ * condim 3 = pyramidal cone with 4 edge rows n +- mu t1, n +- mu t2. */
+typedef struct {
+  int32_t geom1, geom2, condim;
+  double mu;
+} dmx_pair_desc;
+
+/* Actuator on a hinge body: motor tau += gear * u; position servo
+ * tau += kp (u - q) - kd v. */
+typedef struct {
+  int32_t type, body;
+  double gear, kp, kd;
+} dmx_actuator_desc;
+
+/* Whole model (Sec. 2.1 parameters: solref = (t_c, phi_d), solimp =
+ * (d_o, d_w, width, midpoint, power); Sec. 4 solimp-CFD = (d_c, d_0, w_c,
+ * m_c, p_c) and the width of the softplus replacing the ReLU in a_ref). */
+typedef struct {
+  int32_t nbody, ngeom, npair, nact;
+  const dmx_body_desc* body;
+  const dmx_geom_desc* geom;
+  const dmx_pair_desc* pair;
+  const dmx_actuator_desc* act;
+  double gravity[3];
+  double solref[2];
+  double solimp[5];
+  double solimp_cfd[5];
+  double softplus;
+  const double* qpos0;        /* [nq] reference pose for A_hat (host pointer) */
+} dmx_model_desc;
+
+typedef struct dmx_model dmx_model;
+typedef struct dmx_tape dmx_tape;
+typedef struct dmx_server dmx_server;
+
+/* Validates the description (host memory, copied) and uploads the compiled
+ * model to the current CUDA device.  Errors: DMX_ERR_INVALID (unsupported
+ * joint/pair, sizes over the compiled limits), DMX_ERR_CUDA, DMX_ERR_OOM. */
+dmx_status dmx_create_model(const dmx_model_desc* desc, dmx_model** out);
+void dmx_destroy_model(dmx_model* m);
+/* nq, nv, nu of the model; any pointer may be NULL. */
+dmx_status dmx_model_dims(const dmx_model* m, int32_t* nq, int32_t* nv, int32_t* nu);
+
+/* ------------------------------------------------------------------ rollout */
+typedef struct {
+  int32_t B;                  /* environments, >= 0 (0 = no work) */
+  const double* x0;           /* [nx][B] initial states (nx = nq + nv) */
+  const double* ctrl;         /* [NI][nu][B] piecewise-constant controls, NULL iff nu == 0 */
+  const double* T;            /* [B] horizons (s), > 0 */
+  int32_t NI;                 /* control intervals over [0, T], >= 1 */
+  double rtol, atol;          /* error-norm tolerances, > 0 */
+  double h0;                  /* first trial step (s), > 0 */
+  int32_t max_steps;          /* step-attempt budget per environment, >= 1 */
+  int32_t K;                  /* checkpoint interval (accepted steps) of the tape, >= 1 */
+  int32_t form;               /* DMX_FORM_*: persistent refill kernel, or one launch per step attempt
+                                 (plain stream launches / CUDA-graph replay) */
+  int32_t lanes;              /* lanes per environment (1,2,4,8,16,32), 0 = autotuned */
+  int32_t host;               /* 1: x0, ctrl, T and all outputs are HOST pointers; the call stages
+                                 them through library device memory and returns after the copies */
+  double* xT;                 /* out [nx][B] final states */
+  double* xb;                 /* out [NI+1][nx][B] states at the interval boundaries, or NULL */
+  int32_t* nsteps;            /* out [B] accepted steps, or NULL */
+  int32_t* nrej;              /* out [B] rejected attempts, or NULL */
+  int32_t* status;            /* out [B] DMX_ENV_* codes, or NULL */
+  dmx_tape** tape;            /* out: tape for dmx_rollout_grad (checkpoints every K accepted
+                                 steps + accepted step sizes), or NULL for forward only */
+} dmx_rollout_args;
+
+/* Batched adaptive rollout x0 -> x(T) (Sec. 3.1; one independent step-size
+ * sequence per environment, Fig. 14).  Errors: DMX_ERR_INVALID for bad sizes or
+ * NULL required pointers, DMX_ERR_OOM when the tape does not fit, DMX_ERR_CUDA. */
+dmx_status dmx_rollout(dmx_model* m, const dmx_rollout_args* a, void* stream);
+
+/* Discrete adjoint of the taped rollout (App. C.2, discretize-then-optimize),
+ * accepted step sizes held constant, for the loss gradient cotangents
+ * xT_bar [nx][B] and xb_bar [NI+1][nx][B] (or NULL).  Writes x0_bar [nx][B]
+ * and ctrl_bar [NI][nu][B] (NULL iff nu == 0).  cfd = 1 applies the
+ * straight-through estimator of Sec. 4: stage derivatives of the CFD
+ * right-hand side evaluated on the stored (CFD-free) trajectory.  Device
+ * pointers, ordered on `stream`.  The tape stays valid (may be reused). */
+dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* tape, int32_t cfd, const double* xT_bar,
+                            const double* xb_bar, double* x0_bar, double* ctrl_bar, void* stream);
+void dmx_tape_free(dmx_tape* t);
+/* Copies a tape into caller DEVICE buffers (any may be NULL), on `stream`:
+ * hlog [max_steps][B] accepted step sizes (entries past nsteps[e] undefined),
+ * nsteps [B] accepted-step counts, ckpt [ncheck][nx+1][B] the state and time
+ * after every K accepted steps (checkpoint c holds step c*K; c = 0 is x0).
+ * dims[6] (host, may be NULL) receives B, NI, max_steps, K, ncheck, nx.  The
+ * step sizes let a reference integrator replay the exact step sequence. */
+dmx_status dmx_tape_read(const dmx_tape* t, double* hlog, int32_t* nsteps, double* ckpt, int32_t* dims,
+                         void* stream);
+
+/* Lanes per environment used for (model, B, forward/gradient) when
+ * dmx_rollout_args.lanes == 0: the value recorded by dmx_set_lanes (the
+ * autotuner's choice), else a default that gives every SM sub-partition a
+ * warp of FP64 work.  `stream` is unused (may be NULL). */
+dmx_status dmx_autotune(dmx_model* m, int32_t B, int32_t grad, int32_t* lanes, void* stream);
+/* Records the lanes per environment for (model, B, forward/gradient); lanes in
+ * {1, 2, 4, 8, 16, 32}.  DMX_ERR_INVALID otherwise. */
+dmx_status dmx_set_lanes(dmx_model* m, int32_t B, int32_t grad, int32_t lanes);
+/* Model facts for tests and tools: invw[nbody] (host, may be NULL) receives the
+ * translational inverse weight of every body at qpos0 (the A_hat of Sec. 2.1,
+ * model constant); info[8] (host, may be NULL) receives nslot, nrowid,
+ * row capacity, workspace doubles, workspace ints, nbody. */
+dmx_status dmx_model_info(const dmx_model* m, double* invw, int32_t* info);
+
+/* ------------------------------------------------------------------ serving */
+typedef struct {
+  int64_t device_bytes;       /* admission budget for request state (tapes, staging) */
+  int32_t max_inflight;       /* concurrent requests on the device */
+  int32_t nstreams;           /* CUDA streams the server overlaps requests on */
+} dmx_server_cfg;
+
+/* A request owns its host buffers until dmx_poll reports it done.  Host
+ * pointers (pinned memory recommended); layouts as in dmx_rollout_args. */
+typedef struct {
+  dmx_model* model;
+  int32_t B, NI, max_steps, K;
+  double rtol, atol, h0;
+  const double* x0;           /* [nx][B] */
+  const double* ctrl;         /* [NI][nu][B] or NULL */
+  const double* T;            /* [B] */
+  int32_t grad;               /* 1: also run the adjoint with xT_bar */
+  int32_t cfd;
+  const double* xT_bar;       /* [nx][B] when grad */
+  double* xT;                 /* out [nx][B] */
+  double* x0_bar;             /* out [nx][B] when grad */
+  double* ctrl_bar;           /* out [NI][nu][B] when grad and nu > 0 */
+  int32_t* status;            /* out [B] or NULL */
+} dmx_request;
+
+dmx_status dmx_server_create(const dmx_server_cfg* cfg, dmx_server** out);
+/* Queues the request (non-blocking).  Admitted to the device once its memory
+ * fits the budget and a slot is free.  DMX_ERR_INVALID if it can never fit. */
+dmx_status dmx_submit(dmx_server* s, const dmx_request* r, uint64_t* ticket);
+/* DMX_OK when the request's outputs are in its host buffers, DMX_NOT_READY
+ * while it runs; non-blocking.  latency_s (optional) = submit -> completion. */
+dmx_status dmx_poll(dmx_server* s, uint64_t ticket, double* latency_s);
+/* Waits (bounded by timeout_s) for all requests, then frees the server. */
+dmx_status dmx_server_destroy(dmx_server* s, double timeout_s);
+
+/* Right-hand side v' = F(q, v, u) of Eq. (EOM) for B independent states (no
+ * integration): q [nq][B], v [nv][B], u [nu][B] (NULL iff nu == 0) device
+ * arrays; cfd = 1 evaluates the CFD right-hand side F~ of Sec. 4.  Writes
+ * a [nv][B] and info [4][B] (DMX_ENV_* status, constraint rows, active rows,
+ * 0).  The constraint solve starts from an empty active set.  lanes as in
+ * dmx_rollout_args (0 = default). */
+dmx_status dmx_eval_rhs(dmx_model* m, int32_t B, const double* q, const double* v, const double* u, int32_t cfd,
+                        int32_t lanes, double* a, int32_t* info, void* stream);
+
+const char* dmx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMX_H */

@@ -61,6 +61,7 @@ def lib():
         L.orc_pair_invw.restype = ctypes.c_double
         L.orc_impedance.restype = ctypes.c_double
         L.orc_count_flops.restype = ctypes.c_longlong
+        L.orc_step_error.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -189,6 +190,12 @@ class OracleModel:
         out = np.zeros(self.nq)
         lib().orc_integrate_pos(self.h, _p(_f64(q)), _p(_f64(dlt)), _p(out))
         return out
+
+    def step_error(self, x, h, u=None, rtol=1e-6, atol=1e-8):
+        """Error norm of one DOPRI5 attempt of size h from x (accepted iff <= 1)."""
+        u = _f64(u if u is not None else np.zeros(max(self.nu, 1)))
+        return lib().orc_step_error(self.h, _p(_f64(x)), _p(u), ctypes.c_double(h), ctypes.c_double(rtol),
+                                    ctypes.c_double(atol))
 
     def step_jacobian(self, q, v, u, h, cfd=False):
         Jx = np.zeros((self.nx, self.nx)); Ju = np.zeros((self.nx, max(self.nu, 1)))

@@ -190,6 +190,17 @@ int orc_replay(void* h, const double* x0, const double* ctrl, double T, int NI, 
   Result r = rollout<double>(M(h), x0, ctrl, make_opts(T, NI, 0, 0, 0, 0), xT, xb, nullptr, nullptr, hlog, n);
   return r.nsteps;
 }
+// Error norm of one DOPRI5 attempt of size hs from x = [q; v] (controls u):
+// the value the adaptive controller compares with 1.
+double orc_step_error(void* h, const double* x, const double* u, double hs, double rtol, double atol) {
+  Model& m = M(h);
+  const int nq = m.nq, nv = m.nv;
+  std::vector<double> a1(nv), q7(nq), v7(nv), a7(nv), e(2 * nv);
+  StageRhs<double> f{m, false};
+  f(x, x + nq, u, a1.data());
+  dopri5_step(m, f, x, x + nq, a1.data(), u, hs, q7.data(), v7.data(), a7.data(), e.data());
+  return error_norm<double>(m, x, x + nq, q7.data(), v7.data(), e.data(), rtol, atol);
+}
 int orc_step_jacobian(void* h, const double* q, const double* v, const double* u, double hs, int cfd, double* Jx, double* Ju) {
   Model& m = M(h);
   std::vector<double> A, B;

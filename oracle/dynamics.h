@@ -546,45 +546,46 @@ P exact_line_search(const P& c0, const P& c1, const std::vector<P>& z, const std
 }
 
 // Newton method on the primal problem (Eq. primal) with exact line search,
-// started from the unconstrained acceleration a0 = M^-1 (tau - c); stops when
-// the active set repeats after a step.  Returns the final active set.
+// started from the unconstrained acceleration a0 = M^-1 (tau - c).  With the
+// active set A of the iterate a, the Newton target is the minimiser of the
+// quadratic of A, a_A = H_A^-1 (tau - c + J_A^T D_A a_ref,A); the search stops
+// when the active set of a_A is A itself (then a_A is the exact minimiser: the
+// gradient of the primal cost vanishes there), otherwise it moves to the exact
+// line minimum between a and a_A.  Returns the final active set.
 template <class P>
 void newton_active_set(int nv, const std::vector<P>& M, const std::vector<P>& a0, const std::vector<P>& J,
                        const std::vector<P>& aref, const std::vector<P>& D, const std::vector<P>& rhs0, SolveInfo& info) {
   const int nr = (int)aref.size();
-  std::vector<P> a = a0, z(nr), g(nv), H, dlt(nv), s(nr);
-  std::vector<char> act(nr), prev;
-  double gscale = 0;
-  for (int i = 0; i < nv; ++i) gscale = std::max(gscale, std::fabs(val(rhs0[i])));
-  info.noconv = false;
-  for (int it = 0;; ++it) {
+  std::vector<P> a = a0, z(nr), zt(nr), H, aA(nv), dlt(nv), s(nr);
+  std::vector<char> act(nr), nxt(nr);
+  auto residual = [&](const std::vector<P>& x, std::vector<P>& zz, std::vector<char>& st) {
     for (int r = 0; r < nr; ++r) {
       P t = P(0.0);
-      for (int i = 0; i < nv; ++i) t = t + J[(size_t)r * nv + i] * a[i];
-      z[r] = t - aref[r];
-      act[r] = val(z[r]) < 0;
+      for (int i = 0; i < nv; ++i) t = t + J[(size_t)r * nv + i] * x[i];
+      zz[r] = t - aref[r];
+      st[r] = val(zz[r]) < 0;
     }
-    if (it > 0 && act == prev) { info.iters = it; break; }
-    if (it >= 50) { info.iters = it; info.noconv = true; break; }
+  };
+  info.noconv = true;
+  residual(a, z, act);
+  for (int it = 0; it <= 50; ++it) {
+    info.iters = it + 1;
+    // minimiser of the quadratic of the current active set
     H = M;
-    for (int i = 0; i < nv; ++i) {
-      P t = P(0.0);
-      for (int j = 0; j < nv; ++j) t = t + M[(size_t)i * nv + j] * (a[j] - a0[j]);
-      g[i] = t;
-    }
+    for (int i = 0; i < nv; ++i) aA[i] = rhs0[i];
     for (int r = 0; r < nr; ++r) {
       if (!act[r]) continue;
       for (int i = 0; i < nv; ++i) {
-        g[i] = g[i] + D[r] * z[r] * J[(size_t)r * nv + i];
+        aA[i] = aA[i] + D[r] * aref[r] * J[(size_t)r * nv + i];
         for (int j = 0; j < nv; ++j) H[(size_t)i * nv + j] = H[(size_t)i * nv + j] + D[r] * J[(size_t)r * nv + i] * J[(size_t)r * nv + j];
       }
     }
-    double gmax = 0;
-    for (int i = 0; i < nv; ++i) gmax = std::max(gmax, std::fabs(val(g[i])));
-    if (gmax <= 1e-13 * (1.0 + gscale)) { info.iters = it; break; }
-    if (!cholesky(H, nv)) { info.spd_fail = true; info.iters = it; break; }
-    for (int i = 0; i < nv; ++i) dlt[i] = -g[i];
-    chol_solve(H, nv, dlt);
+    if (!cholesky(H, nv)) { info.spd_fail = true; break; }
+    chol_solve(H, nv, aA);
+    residual(aA, zt, nxt);
+    if (nxt == act) { info.noconv = false; break; }
+    // exact line search from a along the Newton direction aA - a
+    for (int i = 0; i < nv; ++i) dlt[i] = aA[i] - a[i];
     P c0 = P(0.0), c1 = P(0.0);
     for (int i = 0; i < nv; ++i) {
       P md = P(0.0), mr = P(0.0);
@@ -599,20 +600,15 @@ void newton_active_set(int nv, const std::vector<P>& M, const std::vector<P>& a0
     }
     P alpha = exact_line_search<P>(c0, c1, z, s, D);
     for (int i = 0; i < nv; ++i) a[i] = a[i] + alpha * dlt[i];
-    prev = act;
-  }
-  // active set at the final iterate
-  for (int r = 0; r < nr; ++r) {
-    P t = P(0.0);
-    for (int i = 0; i < nv; ++i) t = t + J[(size_t)r * nv + i] * a[i];
-    act[r] = val(t - aref[r]) < 0;
+    residual(a, z, act);
   }
   info.active = act;
 }
 
 // Unique minimiser of the primal problem: Newton to find the active set A, then
-// a = H_A^-1 (tau - c + J_A^T D_A a_ref,A) with H_A = M + J_A^T D_A J_A.  In a
-// derivative type the last solve carries the implicit-function derivative.
+// a = H_A^-1 (tau - c + J_A^T D_A a_ref,A) with H_A = M + J_A^T D_A J_A (the
+// Newton target of the last iteration, recomputed in S).  In a derivative type
+// this last solve carries the implicit-function derivative.
 template <class S>
 void solve_constraints(int nv, const std::vector<S>& M, const std::vector<S>& rhs0, const Rows<S>& R,
                        std::vector<S>& a, std::vector<S>& f, SolveInfo& info) {

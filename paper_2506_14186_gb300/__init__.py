@@ -1,0 +1,298 @@
+"""GB300-native batched soft-contact rollouts with a discrete adjoint.
+
+Python binding of the C ABI in ``include/dmx.h`` (library ``libdmx.so`` built
+in-tree by ``paper_2506_14186_gb300._build``).  This module only marshals
+arguments: every step of the rollout and of its adjoint runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current CUDA stream.
+There is no CPU fallback: without the compiled library, or without a CUDA
+device, the calls raise.
+
+Batched arrays use the library's structure-of-arrays layout: ``x0`` is
+``[nx, B]``, ``ctrl`` is ``[NI, nu, B]``, ``T`` is ``[B]`` (float64 CUDA tensors).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (scene descriptions and seeded inputs)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libdmx.so")
+
+c_i32, c_f64, c_p = ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+
+DMX_OK, DMX_ERR_INVALID, DMX_ERR_OOM, DMX_ERR_CUDA, DMX_NOT_READY, DMX_ERR_TIMEOUT, DMX_ERR_UNIMPLEMENTED = range(7)
+ENV_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "nonfinite", 4: "solver_noconv", 5: "row_overflow"}
+FORMS = {"persistent": 0, "step": 1, "graph": 2}
+_JOINT = {"free": 0, "hinge": 1}
+_GEOM = {"sphere": 0, "capsule": 1, "box": 2}
+_ACT = {"motor": 0, "position": 1}
+
+# names of every entry point declared in include/dmx.h
+ABI_SYMBOLS = ("dmx_create_model", "dmx_destroy_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad",
+               "dmx_tape_free", "dmx_tape_read", "dmx_autotune", "dmx_set_lanes", "dmx_model_info", "dmx_server_create", "dmx_submit", "dmx_poll",
+               "dmx_server_destroy", "dmx_eval_rhs", "dmx_last_error")
+
+
+class BodyDesc(ctypes.Structure):
+    _fields_ = [("parent", c_i32), ("joint", c_i32), ("pos", c_f64 * 3), ("quat", c_f64 * 4), ("axis", c_f64 * 3),
+                ("mass", c_f64), ("com", c_f64 * 3), ("inertia", c_f64 * 3), ("damping", c_f64)]
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [("type", c_i32), ("body", c_i32), ("pos", c_f64 * 3), ("quat", c_f64 * 4), ("size", c_f64 * 3)]
+
+
+class PairDesc(ctypes.Structure):
+    _fields_ = [("geom1", c_i32), ("geom2", c_i32), ("condim", c_i32), ("mu", c_f64)]
+
+
+class ActDesc(ctypes.Structure):
+    _fields_ = [("type", c_i32), ("body", c_i32), ("gear", c_f64), ("kp", c_f64), ("kd", c_f64)]
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("nbody", c_i32), ("ngeom", c_i32), ("npair", c_i32), ("nact", c_i32),
+                ("body", ctypes.POINTER(BodyDesc)), ("geom", ctypes.POINTER(GeomDesc)),
+                ("pair", ctypes.POINTER(PairDesc)), ("act", ctypes.POINTER(ActDesc)),
+                ("gravity", c_f64 * 3), ("solref", c_f64 * 2), ("solimp", c_f64 * 5), ("solimp_cfd", c_f64 * 5),
+                ("softplus", c_f64), ("qpos0", ctypes.POINTER(c_f64))]
+
+
+class RolloutArgs(ctypes.Structure):
+    _fields_ = [("B", c_i32), ("x0", c_p), ("ctrl", c_p), ("T", c_p), ("NI", c_i32), ("rtol", c_f64),
+                ("atol", c_f64), ("h0", c_f64), ("max_steps", c_i32), ("K", c_i32), ("form", c_i32),
+                ("lanes", c_i32), ("host", c_i32), ("xT", c_p), ("xb", c_p), ("nsteps", c_p), ("nrej", c_p),
+                ("status", c_p), ("tape", ctypes.POINTER(c_p))]
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_int64), ("max_inflight", c_i32), ("nstreams", c_i32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("model", c_p), ("B", c_i32), ("NI", c_i32), ("max_steps", c_i32), ("K", c_i32), ("rtol", c_f64),
+                ("atol", c_f64), ("h0", c_f64), ("x0", c_p), ("ctrl", c_p), ("T", c_p), ("grad", c_i32),
+                ("cfd", c_i32), ("xT_bar", c_p), ("xT", c_p), ("x0_bar", c_p), ("ctrl_bar", c_p), ("status", c_p)]
+
+
+_lib = None
+
+
+class DmxError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libdmx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libdmx.so not built ({_LIB_PATH}); run paper_2506_14186_gb300._build.build()")
+        L = ctypes.CDLL(_LIB_PATH)
+        L.dmx_last_error.restype = ctypes.c_char_p
+        for name in ("dmx_create_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad", "dmx_autotune",
+                     "dmx_server_create", "dmx_submit", "dmx_poll", "dmx_server_destroy", "dmx_model_info",
+                     "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read"):
+            getattr(L, name).restype = c_i32
+        L.dmx_destroy_model.restype = None
+        L.dmx_tape_free.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != DMX_OK:
+        raise DmxError(f"dmx error {rc}: {lib().dmx_last_error().decode()}")
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return c_p(t.data_ptr()) if t is not None else c_p(0)
+
+
+def _require_cuda(t, name, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+
+
+class Model:
+    """A compiled model on the current CUDA device (from a workloads scene dict)."""
+
+    def __init__(self, scene):
+        L = lib()
+        bodies = (BodyDesc * len(scene["bodies"]))()
+        for i, b in enumerate(scene["bodies"]):
+            bodies[i] = BodyDesc(b["parent"], _JOINT[b["joint"]], (c_f64 * 3)(*b["pos"]), (c_f64 * 4)(*b["quat"]),
+                                 (c_f64 * 3)(*b["axis"]), b["mass"], (c_f64 * 3)(*b["com"]),
+                                 (c_f64 * 3)(*b["inertia"]), b["damping"])
+        geoms = (GeomDesc * max(1, len(scene["geoms"])))()
+        for i, g in enumerate(scene["geoms"]):
+            geoms[i] = GeomDesc(_GEOM[g["type"]], g["body"], (c_f64 * 3)(*g["pos"]), (c_f64 * 4)(*g["quat"]),
+                                (c_f64 * 3)(*g["size"]))
+        pairs = (PairDesc * max(1, len(scene["pairs"])))()
+        for i, p in enumerate(scene["pairs"]):
+            pairs[i] = PairDesc(p["geom1"], p["geom2"], p["condim"], p["mu"])
+        acts = (ActDesc * max(1, len(scene["actuators"])))()
+        for i, a in enumerate(scene["actuators"]):
+            acts[i] = ActDesc(_ACT[a["type"]], a["body"], a["gear"], a["kp"], a["kd"])
+        o = scene["options"]
+        q0 = (c_f64 * len(scene["qpos0"]))(*scene["qpos0"])
+        desc = ModelDesc(len(scene["bodies"]), len(scene["geoms"]), len(scene["pairs"]), len(scene["actuators"]),
+                         bodies, geoms, pairs, acts, (c_f64 * 3)(*o["gravity"]), (c_f64 * 2)(*o["solref"]),
+                         (c_f64 * 5)(*o["solimp"]), (c_f64 * 5)(*o["solimp_cfd"]), o["softplus"], q0)
+        h = c_p()
+        _check(L.dmx_create_model(ctypes.byref(desc), ctypes.byref(h)))
+        self.h = h
+        self.scene = scene
+        nq, nv, nu = c_i32(), c_i32(), c_i32()
+        _check(L.dmx_model_dims(h, ctypes.byref(nq), ctypes.byref(nv), ctypes.byref(nu)))
+        self.nq, self.nv, self.nu = nq.value, nv.value, nu.value
+        self.nx = self.nq + self.nv
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().dmx_destroy_model(self.h)
+        except Exception:
+            pass
+
+    def info(self):
+        invw = (c_f64 * 16)()
+        info = (c_i32 * 8)()
+        _check(lib().dmx_model_info(self.h, invw, info))
+        return {"invw": list(invw)[:info[5]], "nslot": info[0], "nrowid": info[1], "rcap": info[2],
+                "ws_doubles": info[3], "ws_ints": info[4]}
+
+    def lanes(self, B, grad=False):
+        out = c_i32()
+        _check(lib().dmx_autotune(self.h, int(B), int(grad), ctypes.byref(out), c_p(0)))
+        return out.value
+
+    def set_lanes(self, B, lanes, grad=False):
+        _check(lib().dmx_set_lanes(self.h, int(B), int(grad), int(lanes)))
+
+
+class Tape:
+    """Checkpoints + accepted step sizes of one taped rollout (library owned)."""
+
+    def __init__(self, handle, model, B, NI):
+        self.h, self.model, self.B, self.NI = handle, model, B, NI
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().dmx_tape_free(self.h)
+        except Exception:
+            pass
+
+    def read(self, stream=None, checkpoints=False):
+        """(hlog [max_steps, B], nsteps [B]) as CUDA tensors, plus the
+        checkpoints [ncheck, nx+1, B] when checkpoints=True."""
+        import torch
+        dims = (c_i32 * 6)()
+        _check(lib().dmx_tape_read(self.h, None, None, None, dims, c_p(0)))
+        hlog = torch.empty((dims[2], self.B), dtype=torch.float64, device="cuda")
+        n = torch.empty(self.B, dtype=torch.int32, device="cuda")
+        ck = torch.empty((dims[4], dims[5] + 1, self.B), dtype=torch.float64, device="cuda") if checkpoints else None
+        _check(lib().dmx_tape_read(self.h, _ptr(hlog), _ptr(n), _ptr(ck), dims, _stream_handle(stream)))
+        return (hlog, n, ck) if checkpoints else (hlog, n)
+
+
+def rollout(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, K=32,
+            form="persistent", lanes=0, want_xb=False, tape=False, stream=None):
+    """Batched adaptive rollout on the device.  Returns a dict of CUDA tensors
+    xT [nx, B], xb [NI+1, nx, B] (if want_xb), nsteps/nrej/status [B] (int32)
+    and, with tape=True, a Tape for rollout_grad."""
+    import torch
+    _require_cuda(x0, "x0", torch.float64)
+    _require_cuda(T, "T", torch.float64)
+    B = x0.shape[1]
+    if x0.shape[0] != model.nx or T.shape != (B,):
+        raise ValueError("x0 must be [nx, B] and T [B]")
+    if model.nu:
+        if ctrl is None:
+            raise ValueError("ctrl [NI, nu, B] required")
+        _require_cuda(ctrl, "ctrl", torch.float64)
+        if tuple(ctrl.shape) != (NI, model.nu, B):
+            raise ValueError("ctrl must be [NI, nu, B]")
+    dev = x0.device
+    xT = torch.empty((model.nx, B), dtype=torch.float64, device=dev)
+    xb = torch.empty((NI + 1, model.nx, B), dtype=torch.float64, device=dev) if want_xb else None
+    nsteps = torch.empty(B, dtype=torch.int32, device=dev)
+    nrej = torch.empty(B, dtype=torch.int32, device=dev)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    th = c_p()
+    args = RolloutArgs(B, x0.data_ptr(), ctrl.data_ptr() if (model.nu and ctrl is not None) else None, T.data_ptr(),
+                       NI, rtol, atol, h0, max_steps, K, FORMS[form], lanes, 0, xT.data_ptr(),
+                       xb.data_ptr() if xb is not None else None, nsteps.data_ptr(), nrej.data_ptr(),
+                       status.data_ptr(), ctypes.pointer(th) if tape else None)
+    _check(lib().dmx_rollout(model.h, ctypes.byref(args), _stream_handle(stream)))
+    out = {"xT": xT, "xb": xb, "nsteps": nsteps, "nrej": nrej, "status": status}
+    if tape:
+        out["tape"] = Tape(th, model, B, NI)
+    return out
+
+
+def rollout_host(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, form="persistent",
+                 lanes=0, xT=None, stream=None):
+    """Same rollout through the C ABI with HOST buffers (numpy arrays or pinned
+    CPU tensors, SoA layout); the library copies in, integrates and copies out."""
+    def host_ptr(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr()
+        return a.ctypes.data
+    B = x0.shape[1]
+    if xT is None:
+        xT = np.empty((model.nx, B))
+    status = np.empty(B, dtype=np.int32)
+    nsteps = np.empty(B, dtype=np.int32)
+    args = RolloutArgs(B, host_ptr(x0), host_ptr(ctrl) if model.nu else None, host_ptr(T), NI, rtol, atol, h0,
+                       max_steps, 32, FORMS[form], lanes, 1, host_ptr(xT), None, host_ptr(nsteps), None,
+                       host_ptr(status), None)
+    _check(lib().dmx_rollout(model.h, ctypes.byref(args), _stream_handle(stream)))
+    return {"xT": xT, "status": status, "nsteps": nsteps}
+
+
+def rollout_grad(tape, xT_bar, xb_bar=None, cfd=False, stream=None):
+    """Discrete adjoint of a taped rollout: returns (x0_bar [nx, B], ctrl_bar [NI, nu, B] or None)."""
+    import torch
+    m = tape.model
+    _require_cuda(xT_bar, "xT_bar", torch.float64)
+    if xb_bar is not None:
+        _require_cuda(xb_bar, "xb_bar", torch.float64)
+    x0_bar = torch.empty((m.nx, tape.B), dtype=torch.float64, device=xT_bar.device)
+    ctrl_bar = torch.empty((tape.NI, m.nu, tape.B), dtype=torch.float64, device=xT_bar.device) if m.nu else None
+    _check(lib().dmx_rollout_grad(m.h, tape.h, int(cfd), _ptr(xT_bar), _ptr(xb_bar), _ptr(x0_bar), _ptr(ctrl_bar),
+                                  _stream_handle(stream)))
+    return x0_bar, ctrl_bar
+
+
+def eval_rhs(model, q, v, u=None, cfd=False, lanes=0, stream=None):
+    """Right-hand side v' = F(q, v, u) for B states (q [nq, B], v [nv, B], u [nu, B]);
+    returns (a [nv, B], info [4, B] int32: status, rows, active rows, 0)."""
+    import torch
+    _require_cuda(q, "q", torch.float64)
+    _require_cuda(v, "v", torch.float64)
+    B = q.shape[1]
+    a = torch.empty((model.nv, B), dtype=torch.float64, device=q.device)
+    info = torch.empty((4, B), dtype=torch.int32, device=q.device)
+    if model.nu:
+        _require_cuda(u, "u", torch.float64)
+    _check(lib().dmx_eval_rhs(model.h, B, _ptr(q), _ptr(v), _ptr(u) if model.nu else c_p(0), int(cfd), int(lanes),
+                              _ptr(a), _ptr(info), _stream_handle(stream)))
+    return a, info

@@ -1,0 +1,98 @@
+// Compiled model and per-environment workspace layout, shared by the host
+// runtime (which fills them) and the device kernels (which read them).
+#pragma once
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define DMX_HD __host__ __device__
+#else
+#define DMX_HD
+#endif
+
+namespace dmx {
+
+// Capacity limits of the compiled model (checked by dmx_create_model).
+constexpr int MAXB = 16;      // bodies
+constexpr int MAXV = 24;      // dofs
+constexpr int MAXQ = 32;      // position coordinates
+constexpr int MAXG = 24;      // geoms
+constexpr int MAXP = 24;      // contact pairs
+constexpr int MAXS = 32;      // contact slots
+constexpr int MAXU = 16;      // actuators
+constexpr int MAXROWID = 128; // constraint rows over all slots (stable row ids)
+constexpr int MAXLEV = 12;    // depth of the body tree
+constexpr int MASKW = MAXROWID / 32;
+
+enum { JNT_FREE = 0, JNT_HINGE = 1 };
+enum { GEOM_SPHERE = 0, GEOM_CAPSULE = 1, GEOM_BOX = 2 };
+enum { ACT_MOTOR = 0, ACT_POSITION = 1 };
+enum { ENV_OK = 0, ENV_MAX_STEPS = 1, ENV_H_UNDERFLOW = 2, ENV_NONFINITE = 3, ENV_SOLVER_NOCONV = 4,
+       ENV_ROW_OVERFLOW = 5 };
+
+struct DevModel {
+  int nbody, ngeom, npair, nact, nq, nv, nu, nslot, nrowid, nlevel;
+  double grav[3];
+  double bcoef, kcoef;               // a_ref = -bcoef (J v) - kcoef d(r) r
+  double solimp[5];                  // d_o, d_w, width, midpoint, power
+  double cfd[5];                     // d_c, d_0, w_c, m_c, p_c
+  double softplus;
+  // bodies (topological order)
+  int b_parent[MAXB], b_jtype[MAXB], b_qadr[MAXB], b_vadr[MAXB], b_nv[MAXB];
+  unsigned b_anc[MAXB];              // bit j: body j is this body or an ancestor
+  double b_pos[MAXB][3], b_Roff[MAXB][9], b_axis[MAXB][3];
+  double b_mass[MAXB], b_com[MAXB][3], b_inertia[MAXB][3], b_damping[MAXB];
+  int child_start[MAXB], child_count[MAXB], child_list[MAXB];
+  int level_start[MAXLEV + 1], level_list[MAXB];
+  int dof_body[MAXV];
+  // geoms
+  int g_type[MAXG], g_body[MAXG];
+  double g_pos[MAXG][3], g_Roff[MAXG][9], g_size[MAXG][3];
+  double g_bound[MAXG];              // bounding-sphere radius about the geom centre
+  // pairs and slots
+  int p_g1[MAXP], p_g2[MAXP], p_condim[MAXP], p_slot0[MAXP], p_nslot[MAXP], p_row0[MAXP];
+  double p_mu[MAXP], p_ahat[MAXP], p_ahat_edge[MAXP];
+  int s_pair[MAXS], s_idx[MAXS];
+  // actuators
+  int a_type[MAXU], a_qadr[MAXU], a_vadr[MAXU];
+  double a_gear[MAXU], a_kp[MAXU], a_kd[MAXU];
+};
+
+// Offsets (in doubles / ints) of one environment's shared-memory workspace.
+struct Layout {
+  int qn, vn, qs, vs, kv, ka, dq;
+  int R, p, com, sd, Ib, Ic, F, Vb, Ab, Fb, gR, gp;
+  int M, H, rhs0, a, an, tmp, tmp2;
+  int ct, J, aref, Dr, z, s, u;
+  int nd;                            // doubles per environment (padded to even)
+  int rowid, slotrow, amask, pmask, misc;
+  int ni;                            // ints per environment
+  int rcap;                          // constraint-row capacity
+};
+
+DMX_HD inline Layout make_layout(const DevModel& m, int rcap) {
+  Layout L{};
+  int o = 0;
+  const int nq = m.nq, nv = m.nv, nb = m.nbody, ng = m.ngeom, ns = m.nslot > 0 ? m.nslot : 1;
+  auto take = [&](int n) { int r = o; o += n; return r; };
+  L.qn = take(nq); L.vn = take(nv); L.qs = take(nq); L.vs = take(nv);
+  L.kv = take(7 * nv); L.ka = take(7 * nv); L.dq = take(nv);
+  L.R = take(9 * nb); L.p = take(3 * nb); L.com = take(3 * nb); L.sd = take(6 * nv);
+  L.Ib = take(10 * nb); L.Ic = take(10 * nb); L.F = take(6 * nv);
+  L.Vb = take(6 * nb); L.Ab = take(6 * nb); L.Fb = take(6 * nb);
+  L.gR = take(9 * ng); L.gp = take(3 * ng);
+  L.M = take(nv * nv); L.H = take(nv * nv);
+  L.rhs0 = take(nv); L.a = take(nv); L.an = take(nv); L.tmp = take(nv); L.tmp2 = take(nv);
+  L.ct = take(16 * ns);
+  L.J = take(rcap * nv); L.aref = take(rcap); L.Dr = take(rcap); L.z = take(rcap); L.s = take(rcap);
+  L.u = take(m.nu > 0 ? m.nu : 1);
+  L.nd = (o + 1) & ~1;
+  int i = 0;
+  auto takei = [&](int n) { int r = i; i += n; return r; };
+  L.rowid = takei(rcap); L.slotrow = takei(ns + 1); L.amask = takei(MASKW); L.pmask = takei(MASKW);
+  L.misc = takei(8);
+  L.ni = (i + 3) & ~3;
+  L.rcap = rcap;
+  return L;
+}
+
+}  // namespace dmx

@@ -1,0 +1,58 @@
+// Library-internal structures of the host runtime.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "dmx.h"
+#include "dmx_kernels.h"
+#include "dmx_model.h"
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n);
+  void free_all();
+};
+
+struct dmx_model {
+  dmx::DevModel host;
+  dmx::DevModel* dev = nullptr;
+  dmx::Layout L;
+  int device = 0, nsm = 0, smem_max = 0, rcap = 0;
+  double invw[dmx::MAXB];
+  int* queue = nullptr;          // persistent-form work counter
+  int* pin = nullptr;            // pinned host int for polling
+  DevBuf step_buf;               // plain-form state
+  DevBuf bufs[4];                // staging / scratch
+  std::mutex mu;
+  std::map<std::pair<int, int>, int> tuned;   // (B, grad) -> lanes per environment
+  int* pinned_int();
+};
+
+struct dmx_tape {
+  dmx_model* model = nullptr;
+  int B = 0, NI = 1, K = 1, nx = 0, nu = 0, max_steps = 0, ncheck = 0, G = 1;
+  double rtol = 0, atol = 0, h0 = 0;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  double* ckpt = nullptr;   // [ncheck][nx+1][B]
+  double* hlog = nullptr;   // [max_steps][B]
+  double* ctrl = nullptr;   // [NI][nu][B]
+  double* T = nullptr;      // [B]
+  int* n = nullptr;         // [B] accepted steps
+};
+
+dmx_status dmx_fail(dmx_status s, const std::string& msg);
+bool launch_config(const dmx_model* m, int G, int* threads, size_t* smem);
+int default_lanes(const dmx_model* m, int B);
+int tuned_lanes(dmx_model* m, int B, int grad);
+dmx_status run_rollout(dmx_model* m, const dmx::RolloutParams& P, int form, int G, cudaStream_t st);
+int model_smem_bytes(const dmx_model* m, int groups);
+
+namespace dmx {
+int persistent_occupancy(int G, int threads, size_t smem);
+}

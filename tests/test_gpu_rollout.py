@@ -1,0 +1,372 @@
+"""GPU forward path (CUDA kernels through the C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Levels of parity:
+  * right-hand side v' = F(q, v, u) (and F~) on random states: 1e-11 relative;
+  * every accepted step of every trajectory: the oracle takes one step of the
+    GPU's accepted size from the GPU's own state (tape with a checkpoint after
+    every step) and must land on the GPU's next state: 1e-11 relative;
+  * whole trajectories in replay mode (the oracle integrates with the GPU's
+    accepted step sizes): 1e-9 relative (the trajectory tolerance of the
+    workload spec) for the non-chaotic ball over its full horizon and for the
+    first 50 ms of the contact-rich workloads.  Beyond that, tumbling boxes,
+    flailing arms and walking feet amplify any rounding difference: the
+    oracle's own replay moves by 1e-9 .. 3e-8 when x0 is perturbed by 1e-15
+    (see tests/test_oracle_integrator.py::test_chaos_floor), so no two implementations with
+    different rounding agree to 1e-9 at T = 1 s;
+  * free-running trajectories (each side takes its own step decisions): the
+    GPU's step sequence is valid (the oracle's error norm accepts every GPU
+    step); states within 1e-4 relative for the ball, arm and quadruped batches;
+    for the tumbling boxes, whose free-running states depend on the step
+    sequence through that chaos, statuses and step-count statistics.
+Relative errors use the per-environment scale max(|x_i|, ||x||_inf).
+Also: bitwise equality of launch forms, alone vs. in a batch, host vs. device
+buffers; status codes; empty batches.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2506_14186_gb300 import workloads as W
+from tests.conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+TOL_RHS = 1e-11
+TOL_REPLAY = 1e-9
+TOL_FREE = 1e-4
+TOL_STEP = 1e-11
+CFD_OPT = dict(solimp=(0.1, 0.95, 0.001, 0.5, 2.0), solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+
+
+@pytest.fixture(scope="module")
+def dmx():
+    import torch
+    from paper_2506_14186_gb300 import _build
+    _build.build()
+    import paper_2506_14186_gb300 as d
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return d
+
+
+@pytest.fixture(scope="module")
+def orc_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _sub(inp, idx):
+    out = dict(inp)
+    out["x0"] = inp["x0"][idx]
+    out["T"] = inp["T"][idx]
+    if inp["ctrl"] is not None:
+        out["ctrl"] = inp["ctrl"][idx]
+    return out
+
+
+def gpu_rollout(dmx, model, inp, tape=False, **kw):
+    ctrl = None if inp["ctrl"] is None else _dev(np.transpose(inp["ctrl"], (1, 2, 0)))   # [B,NI,nu] -> [NI,nu,B]
+    args = dict(NI=inp["NI"], rtol=inp["rtol"], atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"])
+    args.update(kw)
+    out = dmx.rollout(model, _dev(inp["x0"].T), _dev(inp["T"]), ctrl=ctrl, tape=tape, **args)
+    res = {k: v.cpu().numpy() for k, v in out.items() if k != "tape" and v is not None}
+    res["xT"] = res["xT"].T
+    if "xb" in res:
+        res["xb"] = np.transpose(res["xb"], (2, 0, 1))
+    if tape:
+        hlog, n, ck = out["tape"].read(checkpoints=True)
+        res["hlog"] = hlog.cpu().numpy().T
+        res["tape_n"] = n.cpu().numpy()
+        res["ckpt"] = np.transpose(ck.cpu().numpy(), (2, 0, 1))      # [B, ncheck, nx+1]
+    return res
+
+
+def oracle_free(orc_mod, scene, inp, want_xb=False):
+    m = orc_mod.OracleModel(scene)
+    return m.batch_rollout(inp["x0"], inp["T"], ctrl=inp["ctrl"], NI=inp["NI"], rtol=inp["rtol"], atol=inp["atol"],
+                           h0=inp["h0"], max_steps=inp["max_steps"], want_xb=want_xb)
+
+
+def assert_replay_parity(orc_mod, scene, inp, g, envs=None):
+    """The oracle replays each environment's GPU step sequence."""
+    m = orc_mod.OracleModel(scene)
+    envs = range(len(inp["x0"])) if envs is None else envs
+    worst = 0.0
+    for e in envs:
+        n = int(g["tape_n"][e])
+        assert n == g["nsteps"][e]
+        ctrl = None if inp["ctrl"] is None else inp["ctrl"][e]
+        xT, xb = m.replay(inp["x0"][e], g["hlog"][e, :n], ctrl=ctrl, T=float(inp["T"][e]), NI=inp["NI"])
+        worst = max(worst, rel_err(g["xT"][e], xT))
+        if "xb" in g:
+            for k in range(inp["NI"] + 1):
+                worst = max(worst, rel_err(g["xb"][e, k], xb[k]))
+    assert worst < TOL_REPLAY, f"replay-mode relative error {worst:.3e}"
+    return worst
+
+
+def _interval(T, NI, t):
+    k = 0
+    while k + 1 < NI and t >= (T if k + 1 >= NI else T * (k + 1) / NI):
+        k += 1
+    return k
+
+
+def assert_stepwise_parity(orc_mod, scene, inp, g, envs=None, check_valid=True):
+    """Each accepted GPU step, started from the GPU's state, against one oracle
+    step of the same size (tape with checkpoint interval 1); and the oracle's
+    error norm of each of those steps is <= 1 (the step would be accepted)."""
+    m = orc_mod.OracleModel(scene)
+    nx = m.nx
+    envs = range(len(inp["x0"])) if envs is None else envs
+    worst, count, worst_err = 0.0, 0, 0.0
+    for e in envs:
+        n = int(g["tape_n"][e])
+        ck = g["ckpt"][e]
+        T = float(inp["T"][e])
+        for s_ in range(n):
+            xs, ts, h = ck[s_, :nx], ck[s_, nx], g["hlog"][e, s_]
+            ctrl = None
+            if inp["ctrl"] is not None:
+                ctrl = inp["ctrl"][e][_interval(T, inp["NI"], ts)][None, :]
+            xo, _ = m.replay(xs, [h], ctrl=ctrl, T=h, NI=1)
+            worst = max(worst, rel_err(ck[s_ + 1, :nx], xo))
+            # the GPU's step sequence is a valid one: the oracle's error norm accepts each step
+            if check_valid:
+                err = m.step_error(xs, h, u=None if ctrl is None else ctrl[0], rtol=inp["rtol"], atol=inp["atol"])
+                worst_err = max(worst_err, err)
+            count += 1
+    assert count > 0
+    assert worst < TOL_STEP, f"per-step relative error {worst:.3e} over {count} steps"
+    if check_valid:
+        assert worst_err <= 1.0 + 1e-9, f"an accepted GPU step has oracle error norm {worst_err}"
+    return worst
+
+
+def assert_step_statistics(g, o):
+    """Chaotic workloads (tumbling boxes): free-running states are not compared
+    per environment (see the module note); statuses must agree and the
+    accepted-step counts agree in distribution."""
+    np.testing.assert_array_equal(g["status"], o["status"])
+    ratio = g["nsteps"] / np.maximum(o["nsteps"], 1)
+    assert abs(np.median(ratio) - 1) < 0.05 and abs(g["nsteps"].mean() / o["nsteps"].mean() - 1) < 0.05
+
+
+def assert_free_parity(g, o):
+    np.testing.assert_array_equal(g["status"], o["status"])
+    err = max(rel_err(g["xT"][e], o["xT"][e]) for e in range(len(o["xT"])))
+    assert err < TOL_FREE, f"free-running relative error {err:.3e}"
+    ratio = g["nsteps"] / np.maximum(o["nsteps"], 1)
+    assert np.all(np.abs(ratio - 1) < 0.1), ratio
+
+
+# ---------------------------------------------------------------- right-hand side
+SEEDS = {"ball": 11, "box": 12, "chain_cube": 13, "quadruped": 14}
+
+
+def _axis_clear(om, q, scene):
+    """Every capsule-box slot keeps the capsule axis 10 mm outside the box: a
+    capsule axis inside a box puts the minimum of the (piecewise-linear) box
+    distance field on a kink, where the contact normal is not unique."""
+    ct = om.contacts(q)
+    for p_i, p in enumerate(scene["pairs"]):
+        if p["geom2"] >= 0:
+            slot = sum(1 if (pp["geom2"] >= 0 or scene["geoms"][pp["geom1"]]["type"] == "sphere") else
+                       (2 if scene["geoms"][pp["geom1"]]["type"] == "capsule" else 8) for pp in scene["pairs"][:p_i])
+            if ct[slot, 0] < -scene["geoms"][p["geom1"]]["size"][0] + 0.01:
+                return False
+    return True
+
+
+def _random_states(scene, B, seed, om=None):
+    """States near contact: free bodies 0-3 mm into the plane or just above,
+    hinges within +-0.5 rad; states whose capsule axis comes within 10 mm of a
+    box are drawn again (see _axis_clear)."""
+    q, v, u = _draw_states(scene, B, seed)
+    if om is not None:
+        for e in range(B):
+            k = 0
+            while not _axis_clear(om, q[e], scene):
+                k += 1
+                q[e] = _draw_states(scene, 1, seed * 1000 + e * 50 + k)[0][0]
+    return q, v, u
+
+
+def _draw_states(scene, B, seed):
+    g = np.random.default_rng(seed)
+    nq = sum(7 if b["joint"] == "free" else 1 for b in scene["bodies"])
+    nv = sum(6 if b["joint"] == "free" else 1 for b in scene["bodies"])
+    q = np.tile(np.array(scene["qpos0"], float), (B, 1))
+    qa = 0
+    for b in scene["bodies"]:
+        if b["joint"] == "free":
+            q[:, qa:qa + 2] += g.normal(scale=0.1, size=(B, 2))
+            z0 = q[0, qa + 2]
+            q[:, qa + 2] = z0 + g.uniform(-0.003, 0.002, B)
+            qq = g.normal(size=(B, 4)) * 0.05
+            qq[:, 0] += 1.0
+            q[:, qa + 3:qa + 7] = qq / np.linalg.norm(qq, axis=1, keepdims=True)
+            qa += 7
+        else:
+            q[:, qa] = g.uniform(-0.5, 0.5, B)
+            qa += 1
+    v = g.normal(scale=0.5, size=(B, nv))
+    u = g.normal(size=(B, max(1, len(scene["actuators"]))))
+    return q, v, u
+
+
+@pytest.mark.parametrize("cfd", [False, True])
+@pytest.mark.parametrize("name", ["ball", "box", "chain_cube", "quadruped"])
+def test_rhs_matches_oracle(dmx, orc_mod, name, cfd):
+    sc = W.SCENES[name](**CFD_OPT) if cfd else W.SCENES[name]()
+    B = 96
+    om = orc_mod.OracleModel(sc)
+    q, v, u = _random_states(sc, B, SEEDS[name], om)
+    gm = dmx.Model(sc)
+    ref = np.array([om.rhs(q[e], v[e], u[e], cfd=cfd) for e in range(B)])
+    nrows = np.array([om.rhs(q[e], v[e], u[e], cfd=cfd, detail=True)[1]["nr"] for e in range(B)])
+    assert nrows.max() > 0
+    for lanes in ((8, 16, 32) if name == "chain_cube" else (4, 8, 16, 32)):   # wider lanes where the workspace is large
+        a, info = dmx.eval_rhs(gm, _dev(q.T), _dev(v.T), _dev(u[:, :gm.nu].T) if gm.nu else None, cfd=cfd, lanes=lanes)
+        a = a.cpu().numpy().T
+        info = info.cpu().numpy()
+        assert np.all(info[0] == 0)
+        np.testing.assert_array_equal(info[1], nrows)
+        err = max(rel_err(a[e], ref[e]) for e in range(B))
+        assert err < TOL_RHS, f"lanes {lanes}: {err:.3e}"
+
+
+# ---------------------------------------------------------------- trajectories
+def _short(inp, T=0.05):
+    out = dict(inp)
+    out["T"] = np.minimum(inp["T"], T)
+    return out
+
+
+def test_ball_batch(dmx, orc_mod):
+    """Bouncing balls, the full batch of 16 (T = 1 s, rtol 1e-6, atol 1e-8):
+    non-chaotic, so the whole trajectory is replayed at 1e-9."""
+    sc, inp = W.ball_scene(), W.ball_inputs(16)
+    m = dmx.Model(sc)
+    g = gpu_rollout(dmx, m, inp, tape=True, K=1)
+    assert_stepwise_parity(orc_mod, sc, inp, g)
+    assert_replay_parity(orc_mod, sc, inp, g)
+    assert_free_parity(gpu_rollout(dmx, m, inp), oracle_free(orc_mod, sc, inp))
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_box_push_every_lane_count(dmx, orc_mod, lanes):
+    """Box pushes (8 vertex contacts, pyramidal friction): 100 environments
+    (several warps and a ragged tail) with each lane count."""
+    sc = W.box_scene()
+    inp = _sub(W.box_push_inputs(4096), np.arange(100))
+    m = dmx.Model(sc)
+    g = gpu_rollout(dmx, m, inp, tape=True, K=1, lanes=lanes)
+    assert_stepwise_parity(orc_mod, sc, inp, g)
+    f = gpu_rollout(dmx, m, inp, lanes=lanes)
+    np.testing.assert_array_equal(f["xT"], g["xT"])          # the tape does not change the arithmetic
+    assert_step_statistics(f, oracle_free(orc_mod, sc, inp))
+    s = _short(inp)
+    assert_replay_parity(orc_mod, sc, s, gpu_rollout(dmx, m, s, tape=True, lanes=lanes))
+
+
+def test_box_push_full_batch_sampled(dmx, orc_mod):
+    """The benchmark configuration (4096 environments, persistent form,
+    autotuned lanes): 64 sampled environments, every step and free-running."""
+    sc, inp = W.box_scene(), W.box_push_inputs(4096)
+    m = dmx.Model(sc)
+    g = gpu_rollout(dmx, m, inp)
+    assert np.all(g["status"] == 0)
+    gt = gpu_rollout(dmx, m, dict(inp, max_steps=2500), tape=True, K=1)
+    np.testing.assert_array_equal(g["xT"], gt["xT"])
+    idx = np.sort(np.random.default_rng(0).choice(4096, 64, replace=False))
+    assert_stepwise_parity(orc_mod, sc, inp, gt, envs=idx)
+    sub = _sub(inp, idx)
+    assert_step_statistics({k: v[idx] for k, v in g.items()}, oracle_free(orc_mod, sc, sub))
+
+
+def test_chain_cube(dmx, orc_mod):
+    """Arm + cube with piecewise-constant torques (0.04 s intervals as in the
+    2 s / 50-interval workload), interval-boundary states included."""
+    sc = W.chain_cube_scene()
+    inp = W.chain_inputs(24, T=0.4, NI=10)
+    m = dmx.Model(sc)
+    g = gpu_rollout(dmx, m, inp, tape=True, K=1, want_xb=True)
+    assert_stepwise_parity(orc_mod, sc, inp, g)
+    assert_free_parity(gpu_rollout(dmx, m, inp), oracle_free(orc_mod, sc, inp))
+    s = W.chain_inputs(24, T=0.08, NI=2)
+    assert_replay_parity(orc_mod, sc, s, gpu_rollout(dmx, m, s, tape=True, want_xb=True))
+
+
+def test_quadruped(dmx, orc_mod):
+    sc = W.quadruped_scene()
+    inp = W.quadruped_inputs(16)
+    inp["T"] = np.minimum(inp["T"], 0.6)
+    m = dmx.Model(sc)
+    g = gpu_rollout(dmx, m, inp, tape=True, K=1)
+    assert_stepwise_parity(orc_mod, sc, inp, g)
+    assert_free_parity(gpu_rollout(dmx, m, inp), oracle_free(orc_mod, sc, inp))
+    s = _short(inp)
+    assert_replay_parity(orc_mod, sc, s, gpu_rollout(dmx, m, s, tape=True))
+
+
+# ---------------------------------------------------------------- GPU invariants and edges
+@pytest.mark.parametrize("form", ["step", "graph"])
+def test_plain_forms_bitwise_equal_persistent(dmx, form):
+    sc = W.box_scene()
+    inp = _sub(W.box_push_inputs(4096), np.arange(37))
+    m = dmx.Model(sc)
+    a = gpu_rollout(dmx, m, inp, lanes=8)
+    b = gpu_rollout(dmx, m, inp, lanes=8, form=form)
+    np.testing.assert_array_equal(a["xT"], b["xT"])
+    np.testing.assert_array_equal(a["nsteps"], b["nsteps"])
+
+
+def test_environment_alone_equals_in_batch(dmx):
+    """Per-environment step sizes (Fig. 14): an environment's result does not
+    depend on the others (bitwise)."""
+    sc, inp = W.box_scene(), W.box_push_inputs(4096)
+    m = dmx.Model(sc)
+    batch = gpu_rollout(dmx, m, _sub(inp, np.arange(64)), lanes=8)
+    for e in (0, 17, 63):
+        alone = gpu_rollout(dmx, m, _sub(inp, np.array([e])), lanes=8)
+        np.testing.assert_array_equal(alone["xT"][0], batch["xT"][e])
+        assert alone["nsteps"][0] == batch["nsteps"][e]
+
+
+def test_status_codes_and_empty_batch(dmx):
+    import torch
+    sc, inp = W.ball_scene(), W.ball_inputs(4)
+    m = dmx.Model(sc)
+    x0 = inp["x0"].copy()
+    x0[1, 2] = np.nan
+    g = gpu_rollout(dmx, m, dict(inp, x0=x0))
+    assert g["status"][1] == 3 and g["nsteps"][1] == 0
+    assert np.all(g["status"][[0, 2, 3]] == 0)
+    g = gpu_rollout(dmx, m, inp, max_steps=5)
+    assert np.all(g["status"] == 1)
+    out = dmx.rollout(m, torch.zeros((13, 0), dtype=torch.float64, device="cuda"),
+                      torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert out["xT"].shape == (13, 0)
+
+
+def test_host_buffer_call_equals_device_call(dmx):
+    sc = W.box_scene()
+    inp = _sub(W.box_push_inputs(4096), np.arange(50))
+    m = dmx.Model(sc)
+    d = gpu_rollout(dmx, m, inp, lanes=8)
+    h = dmx.rollout_host(m, np.ascontiguousarray(inp["x0"].T), np.ascontiguousarray(inp["T"]), lanes=8)
+    np.testing.assert_array_equal(h["xT"].T, d["xT"])
+
+
+def test_model_inverse_weights_match_oracle(dmx, orc_mod):
+    for name in ("ball", "box", "chain_cube", "quadruped"):
+        sc = W.SCENES[name]()
+        g = dmx.Model(sc).info()["invw"]
+        o = orc_mod.OracleModel(sc)
+        np.testing.assert_allclose(g, [o.body_invw(b) for b in range(o.nbody)], rtol=1e-12)

@@ -162,3 +162,25 @@ def test_control_interval_boundaries_are_hit_exactly(orc):
     t = np.concatenate([[0.0], np.cumsum(r["hlog"])])
     for k in range(1, 9):
         assert np.min(np.abs(t - 0.4 * k / 8)) < 1e-12
+
+
+def test_chaos_floor(orc):
+    """How far rounding-level differences travel in the box-push workload: the
+    oracle's own replay (same step sizes) from x0 perturbed by 1e-15 relative
+    moves by more than 1e-9 at T = 1 s (tumbling contact dynamics amplify it),
+    while at 50 ms it stays below 1e-10.  Trajectory parity against another
+    implementation is therefore checked per step and on short horizons."""
+    from tests.conftest import rel_err
+    sc, inp = W.box_scene(), W.box_push_inputs(4096)
+    m = orc.OracleModel(sc)
+    g = np.random.default_rng(3)
+    far, near = [], []
+    for e in range(8):
+        x0 = inp["x0"][e]
+        r = m.rollout(x0, T=1.0)
+        r5 = m.rollout(x0, T=0.05)
+        xp = x0 * (1 + 1e-15 * g.standard_normal(13))
+        far.append(rel_err(m.replay(xp, r["hlog"], T=1.0)[0], r["xT"]))
+        near.append(rel_err(m.replay(xp, r5["hlog"], T=0.05)[0], r5["xT"]))
+    assert max(far) > 1e-9
+    assert max(near) < 1e-10
