@@ -1,0 +1,43 @@
+"""Autotuner: lanes per environment for a (model, batch size, forward/gradient).
+
+Every lane count whose workspace fits in shared memory is timed on the
+caller's own inputs (CUDA events, after one warm-up run); the fastest is
+recorded in the library (dmx_set_lanes) so that later calls with lanes = 0 use
+it.  Results are cached per process by (scene name, B, grad).
+"""
+
+from __future__ import annotations
+
+import paper_2506_14186_gb300 as dmx
+
+LANES = (1, 2, 4, 8, 16, 32)
+_cache: dict = {}
+
+
+def tune_forward(model, x0, T, ctrl=None, NI=1, reps=1, candidates=LANES, **kw):
+    """Times a forward rollout for each candidate lane count; returns
+    (best_lanes, {lanes: ms})."""
+    import torch
+    key = (model.scene.get("name"), x0.shape[1], 0)
+    if key in _cache:
+        model.set_lanes(x0.shape[1], _cache[key][0])
+        return _cache[key]
+    times = {}
+    for G in candidates:
+        try:
+            dmx.rollout(model, x0, T, ctrl=ctrl, NI=NI, lanes=G, **kw)        # warm-up (and fit check)
+        except dmx.DmxError:
+            continue
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            dmx.rollout(model, x0, T, ctrl=ctrl, NI=NI, lanes=G, **kw)
+        e1.record(st)
+        e1.synchronize()
+        times[G] = e0.elapsed_time(e1) / reps
+    best = min(times, key=times.get)
+    model.set_lanes(x0.shape[1], best)
+    _cache[key] = (best, times)
+    return best, times
