@@ -228,6 +228,31 @@ dmx_status dmx_poll(dmx_server* s, uint64_t ticket, double* latency_s);
 /* Waits (bounded by timeout_s) for all requests, then frees the server. */
 dmx_status dmx_server_destroy(dmx_server* s, double timeout_s);
 
+/* Allocation-free rollout (the paper has no counterpart: this is a service of
+ * the library).  Some callers cannot let a library call cudaMalloc: real-time
+ * control loops, because cudaMalloc may synchronise the whole device and take
+ * milliseconds at an unpredictable moment; hosts that hand out all device
+ * memory from their own fixed arena or budget; processes whose device
+ * footprint must stay constant after start-up.  For them this entry point
+ * runs the same integration as dmx_rollout in the plain one-launch-per-attempt
+ * form, with the per-environment integrator state kept in one fixed device
+ * array compiled into the library (DMX_STATIC_SCRATCH_BYTES, present on every
+ * GPU that loads the library until the process exits).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   - Arguments as in dmx_rollout, with device buffers only (host = 0) and no
+ *     tape (tape = NULL); `form` is ignored.  The caller passes all inputs and
+ *     outputs; the model must come from dmx_create_model on this device.
+ *   - State needed: B * (8 * (nq + 2 nv + 3) + 40) + 8 bytes.  A larger B is
+ *     rejected with DMX_ERR_INVALID and a message naming both sizes.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call on a device uses the same array and leaves its contents
+ *     behind: calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race and corrupt each other.  Serialise them.
+ *   - Returns after the rollout has finished on `stream` (it polls a counter). */
+#define DMX_STATIC_SCRATCH_BYTES (4 << 20)
+dmx_status dmx_rollout_static(dmx_model* m, const dmx_rollout_args* a, void* stream);
+
 /* Right-hand side v' = F(q, v, u) of Eq. (EOM) for B independent states (no
  * integration): q [nq][B], v [nv][B], u [nu][B] (NULL iff nu == 0) device
  * arrays; cfd = 1 evaluates the CFD right-hand side F~ of Sec. 4.  Writes

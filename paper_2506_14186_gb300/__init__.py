@@ -35,7 +35,7 @@ _ACT = {"motor": 0, "position": 1}
 # names of every entry point declared in include/dmx.h
 ABI_SYMBOLS = ("dmx_create_model", "dmx_destroy_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad",
                "dmx_tape_free", "dmx_tape_read", "dmx_autotune", "dmx_set_lanes", "dmx_model_info", "dmx_server_create", "dmx_submit", "dmx_poll",
-               "dmx_server_destroy", "dmx_eval_rhs", "dmx_last_error")
+               "dmx_server_destroy", "dmx_eval_rhs", "dmx_rollout_static", "dmx_last_error")
 
 
 class BodyDesc(ctypes.Structure):
@@ -97,7 +97,7 @@ def lib():
         L.dmx_last_error.restype = ctypes.c_char_p
         for name in ("dmx_create_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad", "dmx_autotune",
                      "dmx_server_create", "dmx_submit", "dmx_poll", "dmx_server_destroy", "dmx_model_info",
-                     "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read"):
+                     "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read", "dmx_rollout_static"):
             getattr(L, name).restype = c_i32
         L.dmx_destroy_model.restype = None
         L.dmx_tape_free.restype = None
@@ -296,3 +296,28 @@ def eval_rhs(model, q, v, u=None, cfd=False, lanes=0, stream=None):
     _check(lib().dmx_eval_rhs(model.h, B, _ptr(q), _ptr(v), _ptr(u) if model.nu else c_p(0), int(cfd), int(lanes),
                               _ptr(a), _ptr(info), _stream_handle(stream)))
     return a, info
+
+
+def rollout_static(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, lanes=0,
+                   xT=None, nsteps=None, status=None, stream=None):
+    """dmx_rollout_static: the rollout without any device allocation inside
+    the call (state in the library's fixed device array).  Outputs go to the
+    caller's tensors xT [nx, B], nsteps / status [B] (int32); allocate them
+    up front if this call must not allocate either.  Returns (xT, nsteps, status)."""
+    import torch
+    _require_cuda(x0, "x0", torch.float64)
+    _require_cuda(T, "T", torch.float64)
+    B = x0.shape[1]
+    if model.nu:
+        _require_cuda(ctrl, "ctrl", torch.float64)
+    if xT is None:
+        xT = torch.empty((model.nx, B), dtype=torch.float64, device=x0.device)
+    if nsteps is None:
+        nsteps = torch.empty(B, dtype=torch.int32, device=x0.device)
+    if status is None:
+        status = torch.empty(B, dtype=torch.int32, device=x0.device)
+    args = RolloutArgs(B, x0.data_ptr(), ctrl.data_ptr() if model.nu else None, T.data_ptr(), NI, rtol, atol, h0,
+                       max_steps, 1, FORMS["step"], lanes, 0, xT.data_ptr(), None, nsteps.data_ptr(), None,
+                       status.data_ptr(), None)
+    _check(lib().dmx_rollout_static(model.h, ctypes.byref(args), _stream_handle(stream)))
+    return xT, nsteps, status
