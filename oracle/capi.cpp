@@ -217,6 +217,20 @@ int orc_rollout_grad(void* h, const double* x0, const double* ctrl, double T, in
   return 0;
 }
 
+// Gradient along a given accepted step sequence (per environment: hlog[e][0:n[e]]).
+int orc_batch_replay_grad(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, const double* hlog,
+                          int hstride, const int* n, int cfd, const double* xT_bar, const double* xb_bar, double* xT,
+                          double* x0_bar, double* ctrl_bar, int nthreads) {
+  Model& m = M(h);
+  const int nx = m.nq + m.nv, nu = m.nu;
+  parallel_for(B, nthreads, [&](int b) {
+    rollout_grad(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr, make_opts(T[b], NI, 1, 1, 1, 1 << 30),
+                 cfd != 0, xT_bar + (size_t)b * nx, xb_bar ? xb_bar + (size_t)b * (NI + 1) * nx : nullptr,
+                 xT + (size_t)b * nx, x0_bar + (size_t)b * nx, ctrl_bar ? ctrl_bar + (size_t)b * NI * nu : nullptr,
+                 hlog + (size_t)b * hstride, n[b]);
+  });
+  return 0;
+}
 int orc_batch_rollout(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, double rtol,
                       double atol, double h0, int max_steps, double* xT, double* xb, int* stats, int nthreads) {
   Model& m = M(h);

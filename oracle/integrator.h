@@ -301,11 +301,14 @@ inline void step_jacobian(const Model& m, const double* q, const double* v, cons
 // Discrete adjoint (discretize-then-optimize) over the accepted steps of the
 // adaptive rollout: x0_bar = d/dx0 <xT_bar, xT> + sum_k <xb_bar[k], x(t_k)>,
 // ctrl_bar likewise for the piecewise-constant controls.
+// With replay != nullptr the forward pass takes the given accepted step sizes
+// instead of choosing them (the gradient of that frozen step sequence).
 inline Result rollout_grad(const Model& m, const double* x0, const double* ctrl, const Opts& o, bool cfd,
-                           const double* xT_bar, const double* xb_bar, double* xT, double* x0_bar, double* ctrl_bar) {
+                           const double* xT_bar, const double* xb_bar, double* xT, double* x0_bar, double* ctrl_bar,
+                           const double* replay = nullptr, int nreplay = 0) {
   const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
   std::vector<StepRec> rec;
-  Result res = rollout<double>(m, x0, ctrl, o, xT, nullptr, &rec, nullptr, nullptr, 0);
+  Result res = rollout<double>(m, x0, ctrl, o, xT, nullptr, &rec, nullptr, replay, nreplay);
   std::vector<double> lam(xT_bar, xT_bar + nx), Jx, Ju, nl(nx);
   if (ctrl_bar) for (int i = 0; i < o.NI * nu; ++i) ctrl_bar[i] = 0.0;
   for (int n = (int)rec.size() - 1; n >= 0; --n) {

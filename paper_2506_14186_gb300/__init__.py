@@ -321,3 +321,45 @@ def rollout_static(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3,
                        status.data_ptr(), None)
     _check(lib().dmx_rollout_static(model.h, ctypes.byref(args), _stream_handle(stream)))
     return xT, nsteps, status
+
+
+def _rollout_fn_class():
+    import torch
+
+    class RolloutFn(torch.autograd.Function):
+        """(x0 [nx, B], ctrl [NI, nu, B] or None) -> (xT [nx, B], xb [NI+1, nx, B]).
+        Forward: taped dmx_rollout; backward: dmx_rollout_grad (discrete adjoint
+        over the accepted steps, straight-through CFD when cfd=True)."""
+
+        @staticmethod
+        def forward(ctx, x0, ctrl, model, T, opts):
+            o = dict(opts)
+            cfd = o.pop("cfd", False)
+            out = rollout(model, x0.detach(), T, ctrl=None if ctrl is None else ctrl.detach(), tape=True,
+                          want_xb=True, **o)
+            ctx.tape, ctx.cfd, ctx.has_ctrl = out["tape"], cfd, ctrl is not None
+            ctx.mark_non_differentiable(out["status"])
+            return out["xT"], out["xb"], out["status"]
+
+        @staticmethod
+        def backward(ctx, xT_bar, xb_bar, _status_bar):
+            import torch as th
+            if xT_bar is None:
+                xT_bar = th.zeros((ctx.tape.model.nx, ctx.tape.B), dtype=th.float64, device="cuda")
+            x0_bar, ctrl_bar = rollout_grad(ctx.tape, xT_bar.contiguous(),
+                                            None if xb_bar is None else xb_bar.contiguous(), cfd=ctx.cfd)
+            return x0_bar, (ctrl_bar if ctx.has_ctrl else None), None, None, None
+
+    return RolloutFn
+
+
+_RolloutFn = None
+
+
+def rollout_fn(model, x0, T, ctrl=None, **opts):
+    """Differentiable rollout: returns (xT, xb, status); gradients of any loss of
+    xT / xb flow to x0 and ctrl through the library's adjoint kernel."""
+    global _RolloutFn
+    if _RolloutFn is None:
+        _RolloutFn = _rollout_fn_class()
+    return _RolloutFn.apply(x0, ctrl, model, T, opts)

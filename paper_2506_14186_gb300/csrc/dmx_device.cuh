@@ -28,6 +28,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
+#include "dmx_dual.cuh"
 #include "dmx_model.h"
 
 namespace dmx {
@@ -60,45 +63,55 @@ struct Grp {
 };
 
 // ------------------------------------------------------------------ small helpers
-__device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
+// Templated on the scalar types so that the same code runs on doubles (the
+// forward path) and on derivative scalars (the adjoint); model constants
+// stay double.
+template <class A, class B, class C>
+__device__ __forceinline__ void cross3(const A* a, const B* b, C* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
-__device__ __forceinline__ double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
-__device__ __forceinline__ void matmul3(const double* A, const double* B, double* C) {
+template <class A, class B>
+__device__ __forceinline__ auto dot3(const A* a, const B* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <class A, class B, class C>
+__device__ __forceinline__ void matmul3(const A* M, const B* N, C* P) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+    for (int j = 0; j < 3; ++j) P[3 * i + j] = M[3 * i] * N[j] + M[3 * i + 1] * N[3 + j] + M[3 * i + 2] * N[6 + j];
 }
-__device__ __forceinline__ void matvec3(const double* A, const double* x, double* y) {
-  y[0] = A[0] * x[0] + A[1] * x[1] + A[2] * x[2];
-  y[1] = A[3] * x[0] + A[4] * x[1] + A[5] * x[2];
-  y[2] = A[6] * x[0] + A[7] * x[1] + A[8] * x[2];
+template <class A, class B, class C>
+__device__ __forceinline__ void matvec3(const A* M, const B* x, C* y) {
+  y[0] = M[0] * x[0] + M[1] * x[1] + M[2] * x[2];
+  y[1] = M[3] * x[0] + M[4] * x[1] + M[5] * x[2];
+  y[2] = M[6] * x[0] + M[7] * x[1] + M[8] * x[2];
 }
-__device__ __forceinline__ void matTvec3(const double* A, const double* x, double* y) {
-  y[0] = A[0] * x[0] + A[3] * x[1] + A[6] * x[2];
-  y[1] = A[1] * x[0] + A[4] * x[1] + A[7] * x[2];
-  y[2] = A[2] * x[0] + A[5] * x[1] + A[8] * x[2];
+template <class A, class B, class C>
+__device__ __forceinline__ void matTvec3(const A* M, const B* x, C* y) {
+  y[0] = M[0] * x[0] + M[3] * x[1] + M[6] * x[2];
+  y[1] = M[1] * x[0] + M[4] * x[1] + M[7] * x[2];
+  y[2] = M[2] * x[0] + M[5] * x[1] + M[8] * x[2];
 }
 // rotation matrix of the normalised quaternion (w, x, y, z)
-__device__ __forceinline__ void quat_to_mat(const double* q, double* R) {
-  const double n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-  const double s = 2.0 / n2;   // 2 / |q|^2 folds the normalisation into the products
-  const double w = q[0], x = q[1], y = q[2], z = q[3];
-  const double xx = s * x * x, yy = s * y * y, zz = s * z * z;
-  const double xy = s * x * y, xz = s * x * z, yz = s * y * z;
-  const double wx = s * w * x, wy = s * w * y, wz = s * w * z;
+template <class T>
+__device__ __forceinline__ void quat_to_mat(const T* q, T* R) {
+  const T n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  const T s = 2.0 / n2;   // 2 / |q|^2 folds the normalisation into the products
+  const T w = q[0], x = q[1], y = q[2], z = q[3];
+  const T xx = s * x * x, yy = s * y * y, zz = s * z * z;
+  const T xy = s * x * y, xz = s * x * z, yz = s * y * z;
+  const T wx = s * w * x, wy = s * w * y, wz = s * w * z;
   R[0] = 1.0 - (yy + zz); R[1] = xy - wz; R[2] = xz + wy;
   R[3] = xy + wz; R[4] = 1.0 - (xx + zz); R[5] = yz - wx;
   R[6] = xz - wy; R[7] = yz + wx; R[8] = 1.0 - (xx + yy);
 }
 // spatial inertia (10 numbers: m, h = m c, I_O xx yy zz xy xz yz about the world
 // origin) applied to a motion vector (w; v): (I_O w + h x v; m v - h x w)
-__device__ __forceinline__ void inertia_apply(const double* I, const double* x, double* y) {
-  const double m = I[0], h0 = I[1], h1 = I[2], h2 = I[3];
-  const double w0 = x[0], w1 = x[1], w2 = x[2], v0 = x[3], v1 = x[4], v2 = x[5];
+template <class T>
+__device__ __forceinline__ void inertia_apply(const T* I, const T* x, T* y) {
+  const T m = I[0], h0 = I[1], h1 = I[2], h2 = I[3];
+  const T w0 = x[0], w1 = x[1], w2 = x[2], v0 = x[3], v1 = x[4], v2 = x[5];
   y[0] = I[4] * w0 + I[7] * w1 + I[8] * w2 + (h1 * v2 - h2 * v1);
   y[1] = I[7] * w0 + I[5] * w1 + I[9] * w2 + (h2 * v0 - h0 * v2);
   y[2] = I[8] * w0 + I[9] * w1 + I[6] * w2 + (h0 * v1 - h1 * v0);
@@ -107,16 +120,18 @@ __device__ __forceinline__ void inertia_apply(const double* I, const double* x, 
   y[5] = m * v2 - (h0 * w1 - h1 * w0);
 }
 // motion cross product (w; v) x (w2; v2) = (w x w2; w x v2 + v x w2)
-__device__ __forceinline__ void crm6(const double* a, const double* b, double* c) {
-  double t[3];
+template <class T>
+__device__ __forceinline__ void crm6(const T* a, const T* b, T* c) {
+  T t[3];
   cross3(a, b, c);
   cross3(a, b + 3, c + 3);
   cross3(a + 3, b, t);
   c[3] += t[0]; c[4] += t[1]; c[5] += t[2];
 }
 // force cross product (w; v) x* (n; f) = (w x n + v x f; w x f)
-__device__ __forceinline__ void crf6(const double* a, const double* b, double* c) {
-  double t[3];
+template <class T>
+__device__ __forceinline__ void crf6(const T* a, const T* b, T* c) {
+  T t[3];
   cross3(a, b, c);
   cross3(a + 3, b + 3, t);
   c[0] += t[0]; c[1] += t[1]; c[2] += t[2];
@@ -124,43 +139,45 @@ __device__ __forceinline__ void crf6(const double* a, const double* b, double* c
 }
 
 // ------------------------------------------------------------------ workspace view
-struct Ws {
-  double* d;
+template <class T>
+struct WsT {
+  T* d;
   int* i;
   const Layout* L;
-  __device__ double* at(int off) const { return d + off; }
+  __device__ T* at(int off) const { return d + off; }
 };
+using Ws = WsT<double>;
 
 // Kinematics: body poses, COMs, dof motion vectors, body spatial inertias, geom poses.
-template <int G>
-__device__ void kinematics(const Grp<G>& g, const DevModel& m, const Ws& w, const double* q) {
+template <int G, class T>
+__device__ void kinematics(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* q) {
   const Layout& L = *w.L;
-  double* R = w.at(L.R); double* P = w.at(L.p); double* C = w.at(L.com);
-  double* S = w.at(L.sd); double* Ib = w.at(L.Ib);
+  T* R = w.at(L.R); T* P = w.at(L.p); T* C = w.at(L.com);
+  T* S = w.at(L.sd); T* Ib = w.at(L.Ib);
   for (int lev = 0; lev < m.nlevel; ++lev) {
     for (int k = m.level_start[lev] + g.lane; k < m.level_start[lev + 1]; k += G) {
       const int b = m.level_list[k];
-      double* Rb = R + 9 * b; double* pb = P + 3 * b;
+      T* Rb = R + 9 * b; T* pb = P + 3 * b;
       if (m.b_jtype[b] == JNT_FREE) {
-        const double* x = q + m.b_qadr[b];
+        const T* x = q + m.b_qadr[b];
         pb[0] = x[0]; pb[1] = x[1]; pb[2] = x[2];
         quat_to_mat(x + 3, Rb);
       } else {
         const int par = m.b_parent[b];
-        double Rp[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, pp[3] = {0, 0, 0};
+        T Rp[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0}, pp[3] = {0.0, 0.0, 0.0};
         if (par >= 0) {
           for (int i = 0; i < 9; ++i) Rp[i] = R[9 * par + i];
           pp[0] = P[3 * par]; pp[1] = P[3 * par + 1]; pp[2] = P[3 * par + 2];
         }
-        double t[3];
+        T t[3];
         matvec3(Rp, m.b_pos[b], t);
         pb[0] = pp[0] + t[0]; pb[1] = pp[1] + t[1]; pb[2] = pp[2] + t[2];
-        double Ro[9], Rj[9];
+        T Ro[9], Rj[9];
         matmul3(Rp, m.b_Roff[b], Ro);
-        double sn, cs;
+        T sn, cs;
         sincos(q[m.b_qadr[b]], &sn, &cs);
         const double* a = m.b_axis[b];
-        const double c1 = 1.0 - cs;
+        const T c1 = 1.0 - cs;
         // Rodrigues: I + sin K + (1 - cos) K^2, K = [a]x
         Rj[0] = cs + c1 * a[0] * a[0];           Rj[1] = c1 * a[0] * a[1] - sn * a[2]; Rj[2] = c1 * a[0] * a[2] + sn * a[1];
         Rj[3] = c1 * a[0] * a[1] + sn * a[2];    Rj[4] = cs + c1 * a[1] * a[1];        Rj[5] = c1 * a[1] * a[2] - sn * a[0];
@@ -168,47 +185,48 @@ __device__ void kinematics(const Grp<G>& g, const DevModel& m, const Ws& w, cons
         matmul3(Ro, Rj, Rb);
       }
       // COM and spatial inertia about the world origin
-      double c[3];
+      T c[3];
       matvec3(Rb, m.b_com[b], c);
       c[0] += pb[0]; c[1] += pb[1]; c[2] += pb[2];
       C[3 * b] = c[0]; C[3 * b + 1] = c[1]; C[3 * b + 2] = c[2];
       const double ms = m.b_mass[b];
       const double* In = m.b_inertia[b];
-      double* I10 = Ib + 10 * b;
-      const double cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+      T* I10 = Ib + 10 * b;
+      const T cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
       I10[0] = ms; I10[1] = ms * c[0]; I10[2] = ms * c[1]; I10[3] = ms * c[2];
       // R diag(I) R^T + m (|c|^2 1 - c c^T)
       const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
       for (int e = 0; e < 6; ++e) {
         const int i = ii[e], j = jj[e];
-        double v = Rb[3 * i] * Rb[3 * j] * In[0] + Rb[3 * i + 1] * Rb[3 * j + 1] * In[1] + Rb[3 * i + 2] * Rb[3 * j + 2] * In[2];
-        v += ms * ((i == j ? cc : 0.0) - c[i] * c[j]);
+        T v = Rb[3 * i] * Rb[3 * j] * In[0] + Rb[3 * i + 1] * Rb[3 * j + 1] * In[1] + Rb[3 * i + 2] * Rb[3 * j + 2] * In[2];
+        v += ms * ((i == j ? cc : T(0.0)) - c[i] * c[j]);
         I10[4 + e] = v;
       }
       // dof motion vectors (w; v at the world origin)
       const int va = m.b_vadr[b];
       if (m.b_jtype[b] == JNT_FREE) {
         for (int d = 0; d < 3; ++d) {
-          double* st = S + 6 * (va + d);
-          st[0] = 0; st[1] = 0; st[2] = 0; st[3] = d == 0; st[4] = d == 1; st[5] = d == 2;
-          double* sr = S + 6 * (va + 3 + d);
+          T* st = S + 6 * (va + d);
+          st[0] = 0.0; st[1] = 0.0; st[2] = 0.0; st[3] = d == 0 ? 1.0 : 0.0; st[4] = d == 1 ? 1.0 : 0.0;
+          st[5] = d == 2 ? 1.0 : 0.0;
+          T* sr = S + 6 * (va + 3 + d);
           sr[0] = Rb[d]; sr[1] = Rb[3 + d]; sr[2] = Rb[6 + d];
           cross3(pb, sr, sr + 3);
         }
       } else {
-        double* sh = S + 6 * va;
+        T* sh = S + 6 * va;
         matvec3(Rb, m.b_axis[b], sh);
         cross3(pb, sh, sh + 3);
       }
     }
     g.sync();
   }
-  double* gR = w.at(L.gR); double* gp = w.at(L.gp);
+  T* gR = w.at(L.gR); T* gp = w.at(L.gp);
   for (int gi = g.lane; gi < m.ngeom; gi += G) {
     const int b = m.g_body[gi];
     matmul3(R + 9 * b, m.g_Roff[gi], gR + 9 * gi);
-    double t[3];
+    T t[3];
     matvec3(R + 9 * b, m.g_pos[gi], t);
     gp[3 * gi] = P[3 * b] + t[0]; gp[3 * gi + 1] = P[3 * b + 1] + t[1]; gp[3 * gi + 2] = P[3 * b + 2] + t[2];
   }
@@ -216,16 +234,16 @@ __device__ void kinematics(const Grp<G>& g, const DevModel& m, const Ws& w, cons
 }
 
 // Composite-rigid-body algorithm: M (dense, both triangles).
-template <int G>
-__device__ void crba(const Grp<G>& g, const DevModel& m, const Ws& w) {
+template <int G, class T>
+__device__ void crba(const Grp<G>& g, const DevModel& m, const WsT<T>& w) {
   const Layout& L = *w.L;
-  const double* Ib = w.at(L.Ib); double* Ic = w.at(L.Ic);
-  const double* S = w.at(L.sd); double* F = w.at(L.F); double* M = w.at(L.M);
+  const T* Ib = w.at(L.Ib); T* Ic = w.at(L.Ic);
+  const T* S = w.at(L.sd); T* F = w.at(L.F); T* M = w.at(L.M);
   const int nv = m.nv;
   for (int lev = m.nlevel - 1; lev >= 0; --lev) {
     for (int k = m.level_start[lev] + g.lane; k < m.level_start[lev + 1]; k += G) {
       const int b = m.level_list[k];
-      double acc[10];
+      T acc[10];
       for (int e = 0; e < 10; ++e) acc[e] = Ib[10 * b + e];
       for (int c = 0; c < m.child_count[b]; ++c) {
         const int ch = m.child_list[m.child_start[b] + c];
@@ -240,9 +258,9 @@ __device__ void crba(const Grp<G>& g, const DevModel& m, const Ws& w) {
   for (int idx = g.lane; idx < nv * nv; idx += G) {
     const int i = idx / nv, j = idx - i * nv;
     if (j > i) continue;
-    double v = 0.0;
+    T v = 0.0;
     if ((m.b_anc[m.dof_body[i]] >> m.dof_body[j]) & 1u) {
-      const double* s = S + 6 * j; const double* f = F + 6 * i;
+      const T* s = S + 6 * j; const T* f = F + 6 * i;
       v = s[0] * f[0] + s[1] * f[1] + s[2] * f[2] + s[3] * f[3] + s[4] * f[4] + s[5] * f[5];
     }
     M[i * nv + j] = v;
@@ -252,32 +270,32 @@ __device__ void crba(const Grp<G>& g, const DevModel& m, const Ws& w) {
 }
 
 // Recursive Newton-Euler with zero joint acceleration: rhs0 = tau - c.
-template <int G>
-__device__ void rne_and_forces(const Grp<G>& g, const DevModel& m, const Ws& w, const double* q, const double* v,
-                               const double* u) {
+template <int G, class T>
+__device__ void rne_and_forces(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* q, const T* v,
+                               const T* u) {
   const Layout& L = *w.L;
-  const double* Ib = w.at(L.Ib); const double* S = w.at(L.sd);
-  double* V = w.at(L.Vb); double* A = w.at(L.Ab); double* Fb = w.at(L.Fb);
+  const T* Ib = w.at(L.Ib); const T* S = w.at(L.sd);
+  T* V = w.at(L.Vb); T* A = w.at(L.Ab); T* Fb = w.at(L.Fb);
   for (int lev = 0; lev < m.nlevel; ++lev) {
     for (int k = m.level_start[lev] + g.lane; k < m.level_start[lev + 1]; k += G) {
       const int b = m.level_list[k];
       const int par = m.b_parent[b];
-      double vb[6], ab[6];
+      T vb[6], ab[6];
       if (par >= 0) {
         for (int e = 0; e < 6; ++e) { vb[e] = V[6 * par + e]; ab[e] = A[6 * par + e]; }
       } else {
-        for (int e = 0; e < 3; ++e) { vb[e] = 0; vb[3 + e] = 0; ab[e] = 0; ab[3 + e] = -m.grav[e]; }
+        for (int e = 0; e < 3; ++e) { vb[e] = 0.0; vb[3 + e] = 0.0; ab[e] = 0.0; ab[3 + e] = -m.grav[e]; }
       }
       const int va = m.b_vadr[b], nd = m.b_nv[b];
       for (int d = 0; d < nd; ++d)
         for (int e = 0; e < 6; ++e) vb[e] += S[6 * (va + d) + e] * v[va + d];
       const int d0 = (m.b_jtype[b] == JNT_FREE) ? 3 : 0;   // world-fixed translation axes
       for (int d = d0; d < nd; ++d) {
-        double sd[6];
+        T sd[6];
         crm6(vb, S + 6 * (va + d), sd);
         for (int e = 0; e < 6; ++e) ab[e] += sd[e] * v[va + d];
       }
-      double f1[6], iv[6], f2[6];
+      T f1[6], iv[6], f2[6];
       inertia_apply(Ib + 10 * b, ab, f1);
       inertia_apply(Ib + 10 * b, vb, iv);
       crf6(vb, iv, f2);
@@ -297,11 +315,11 @@ __device__ void rne_and_forces(const Grp<G>& g, const DevModel& m, const Ws& w, 
     }
     g.sync();
   }
-  double* rhs0 = w.at(L.rhs0);
+  T* rhs0 = w.at(L.rhs0);
   for (int i = g.lane; i < m.nv; i += G) {
-    const double* s = S + 6 * i; const double* f = Fb + 6 * m.dof_body[i];
-    const double c = s[0] * f[0] + s[1] * f[1] + s[2] * f[2] + s[3] * f[3] + s[4] * f[4] + s[5] * f[5];
-    double tau = -m.b_damping[m.dof_body[i]] * v[i];
+    const T* s = S + 6 * i; const T* f = Fb + 6 * m.dof_body[i];
+    const T c = s[0] * f[0] + s[1] * f[1] + s[2] * f[2] + s[3] * f[3] + s[4] * f[4] + s[5] * f[5];
+    const T tau = -m.b_damping[m.dof_body[i]] * v[i];
     rhs0[i] = tau - c;
   }
   g.sync();
@@ -316,26 +334,27 @@ __device__ void rne_and_forces(const Grp<G>& g, const DevModel& m, const Ws& w, 
 }
 
 // ------------------------------------------------------------------ collision
-// contact record (16 doubles): r, pos[3], n[3], t1[3], t2[3], d, pterm, D
-__device__ __forceinline__ double box_sdf(const double* y, const double* h, double* grad) {
-  double qd[3];
+// contact record (16 scalars): r, pos[3], n[3], t1[3], t2[3], d, pterm, D
+template <class T>
+__device__ __forceinline__ T box_sdf(const T* y, const double* h, T* grad) {
+  T qd[3];
   bool out = false;
-  for (int i = 0; i < 3; ++i) { qd[i] = fabs(y[i]) - h[i]; out = out || qd[i] > 0; }
+  for (int i = 0; i < 3; ++i) { qd[i] = fabs(y[i]) - h[i]; out = out || value(qd[i]) > 0; }
   if (out) {
-    double ss = 0;
-    for (int i = 0; i < 3; ++i) if (qd[i] > 0) ss += qd[i] * qd[i];
-    const double d = sqrt(ss), inv = 1.0 / d;
+    T ss = 0.0;
+    for (int i = 0; i < 3; ++i) if (value(qd[i]) > 0) ss += qd[i] * qd[i];
+    const T d = sqrt(ss), inv = 1.0 / d;
     for (int i = 0; i < 3; ++i) {
-      const double gg = qd[i] > 0 ? qd[i] * inv : 0.0;
-      grad[i] = y[i] < 0 ? -gg : gg;
+      const T gg = value(qd[i]) > 0 ? qd[i] * inv : T(0.0);
+      grad[i] = value(y[i]) < 0 ? -gg : gg;
     }
     return d;
   }
   int k = 0;
-  if (qd[1] > qd[k]) k = 1;
-  if (qd[2] > qd[k]) k = 2;
-  grad[0] = grad[1] = grad[2] = 0.0;
-  grad[k] = y[k] < 0 ? -1.0 : 1.0;
+  if (value(qd[1]) > value(qd[k])) k = 1;
+  if (value(qd[2]) > value(qd[k])) k = 2;
+  grad[0] = 0.0; grad[1] = 0.0; grad[2] = 0.0;
+  grad[k] = value(y[k]) < 0 ? -1.0 : 1.0;
   return qd[k];
 }
 __device__ __forceinline__ double box_sdf_slope(const double* y0, const double* wv, double s, const double* h) {
@@ -345,90 +364,122 @@ __device__ __forceinline__ double box_sdf_slope(const double* y0, const double* 
 }
 
 // Capsule (geom g1) against box (geom g2): minimum over the capsule axis of
-// the box distance field (convex along the axis; bisection on its slope).
-static __device__ void capsule_box(const DevModel& m, const double* gR, const double* gp, int g1, int g2, double thr, double* ct) {
+// the box distance field (convex along the axis; bisection on its slope, in
+// values).  In derivative scalars the minimiser s carries ds/dtheta from the
+// implicit function theorem (slope = 0 at an interior minimum of the smooth
+// outside field: ds = -d(slope) / (d slope / ds)); elsewhere s is constant.
+template <class T>
+__device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1, int g2, double thr, T* ct) {
   const double rc = m.g_size[g1][0], Lh = m.g_size[g1][1];
   const double* h = m.g_size[g2];
-  const double* R1 = gR + 9 * g1; const double* R2 = gR + 9 * g2;
-  const double* c1 = gp + 3 * g1; const double* c2 = gp + 3 * g2;
-  double dc[3] = {c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2]};
+  const T* R1 = gR + 9 * g1; const T* R2 = gR + 9 * g2;
+  const T* c1 = gp + 3 * g1; const T* c2 = gp + 3 * g2;
+  T dc[3] = {c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2]};
   const double reach = m.g_bound[g1] + m.g_bound[g2] + (thr > 0 ? thr : 0.0);
-  if (dot3(dc, dc) > reach * reach) { ct[0] = 1e30; return; }   // cannot be within the threshold
-  const double u[3] = {R1[0], R1[3], R1[6]};
-  double y0[3], wv[3];
+  const double dd = value(dc[0]) * value(dc[0]) + value(dc[1]) * value(dc[1]) + value(dc[2]) * value(dc[2]);
+  if (dd > reach * reach) { ct[0] = 1e30; return; }   // cannot be within the threshold
+  const T u[3] = {R1[0], R1[3], R1[6]};
+  T y0[3], wv[3];
   matTvec3(R2, dc, y0);
   matTvec3(R2, u, wv);
-  double s;
-  if (box_sdf_slope(y0, wv, -Lh, h) >= 0) s = -Lh;
-  else if (box_sdf_slope(y0, wv, Lh, h) <= 0) s = Lh;
+  const double y0v[3] = {value(y0[0]), value(y0[1]), value(y0[2])}, wvv[3] = {value(wv[0]), value(wv[1]), value(wv[2])};
+  double sv;
+  if (box_sdf_slope(y0v, wvv, -Lh, h) >= 0) sv = -Lh;
+  else if (box_sdf_slope(y0v, wvv, Lh, h) <= 0) sv = Lh;
   else {
     double lo = -Lh, hi = Lh;
     for (int it = 0; it < 200; ++it) {
       const double mid = 0.5 * (lo + hi);
       if (mid <= lo || mid >= hi) break;
-      if (box_sdf_slope(y0, wv, mid, h) < 0) lo = mid; else hi = mid;
+      if (box_sdf_slope(y0v, wvv, mid, h) < 0) lo = mid; else hi = mid;
     }
-    s = 0.5 * (lo + hi);
+    sv = 0.5 * (lo + hi);
   }
-  double y[3] = {y0[0] + s * wv[0], y0[1] + s * wv[1], y0[2] + s * wv[2]}, gr[3], n[3];
-  const double dist = box_sdf(y, h, gr);
+  T s = sv;
+  if constexpr (!std::is_same<T, double>::value) {
+    // implicit-function tangent of the minimiser (outside the box, interior s)
+    double yv[3] = {y0v[0] + sv * wvv[0], y0v[1] + sv * wvv[1], y0v[2] + sv * wvv[2]}, gv[3];
+    const double phi = box_sdf(yv, h, gv);
+    bool outside = false;
+    for (int i = 0; i < 3; ++i) outside = outside || (fabs(yv[i]) - h[i] > 0);
+    if (outside && sv > -Lh && sv < Lh && phi > 0) {
+      const double gw = gv[0] * wvv[0] + gv[1] * wvv[1] + gv[2] * wvv[2];
+      double ww = 0;
+      for (int i = 0; i < 3; ++i) if (fabs(yv[i]) > h[i]) ww += wvv[i] * wvv[i];
+      const double phi2 = (ww - gw * gw) / phi;
+      if (phi2 > 1e-12) {
+        T yT[3] = {y0[0] + sv * wv[0], y0[1] + sv * wv[1], y0[2] + sv * wv[2]}, gT[3];
+        box_sdf(yT, h, gT);
+        const T slope = gT[0] * wv[0] + gT[1] * wv[1] + gT[2] * wv[2];
+        s = T(sv, -slope.d / phi2);
+      }
+    }
+  }
+  T y[3] = {y0[0] + s * wv[0], y0[1] + s * wv[1], y0[2] + s * wv[2]}, gr[3], n[3];
+  const T dist = box_sdf(y, h, gr);
   matvec3(R2, gr, n);
-  const double r = dist - rc;
+  const T r = dist - rc;
   ct[0] = r;
-  const double off = rc + 0.5 * r;
+  const T off = rc + 0.5 * r;
   for (int i = 0; i < 3; ++i) { ct[1 + i] = c1[i] + s * u[i] - off * n[i]; ct[4 + i] = n[i]; }
   // tangent frame: t1 perpendicular to n and world z (world x when n is near z)
   double ref[3] = {0, 0, 1};
-  if (fabs(n[2]) >= 0.5) { ref[0] = 1; ref[2] = 0; }
-  double t1[3], t2[3];
+  if (fabs(value(n[2])) >= 0.5) { ref[0] = 1; ref[2] = 0; }
+  T t1[3], t2[3];
   cross3(n, ref, t1);
-  const double il = rsqrt(dot3(t1, t1));
+  const T il = rsqrt_t(dot3(t1, t1));
   t1[0] *= il; t1[1] *= il; t1[2] *= il;
   cross3(n, t1, t2);
   for (int i = 0; i < 3; ++i) { ct[7 + i] = t1[i]; ct[10 + i] = t2[i]; }
 }
 
 // Spline of the solimp shape on x in [0, 1] (midpoint mid, power pw).
-__device__ __forceinline__ double spline_shape(double x, double mid, double pw) {
-  if (x <= mid && mid > 0) {
-    const double num = (pw == 2.0) ? x * x : (pw == 4.0 ? (x * x) * (x * x) : pow(x, pw));
-    return num / ((pw == 2.0) ? mid : pow(mid, pw - 1.0));
+template <class T>
+__device__ __forceinline__ T spline_shape(const T& x, double mid, double pw) {
+  if (value(x) <= mid && mid > 0) {
+    const T num = (pw == 2.0) ? x * x : (pw == 4.0 ? (x * x) * (x * x) : pow(x, pw));
+    return num / ((pw == 2.0) ? mid : ::pow(mid, pw - 1.0));
   }
-  const double y = 1.0 - x;
-  const double num = (pw == 2.0) ? y * y : (pw == 4.0 ? (y * y) * (y * y) : pow(y, pw));
-  return 1.0 - num / ((pw == 2.0) ? (1.0 - mid) : pow(1.0 - mid, pw - 1.0));
+  const T y = 1.0 - x;
+  const T num = (pw == 2.0) ? y * y : (pw == 4.0 ? (y * y) * (y * y) : pow(y, pw));
+  return 1.0 - num / ((pw == 2.0) ? (1.0 - mid) : ::pow(1.0 - mid, pw - 1.0));
 }
-__device__ __forceinline__ double impedance(const DevModel& m, double r, bool cfd) {
-  double d;
-  if (cfd && r >= 0) {
-    double x = 1.0 - r / m.cfd[2];
-    if (x < 0) x = 0;
+template <class T>
+__device__ __forceinline__ T impedance(const DevModel& m, const T& r, bool cfd) {
+  T d;
+  if (cfd && value(r) >= 0) {
+    T x = 1.0 - r / m.cfd[2];
+    if (value(x) < 0) x = 0.0;
     d = m.cfd[0] + (m.cfd[1] - m.cfd[0]) * spline_shape(x, m.cfd[3], m.cfd[4]);
   } else {
-    double x = fabs(r) / m.solimp[2];
-    if (x > 1.0) x = 1.0;
+    T x = fabs(r) / m.solimp[2];
+    if (value(x) > 1.0) x = 1.0;
     d = m.solimp[0] + (m.solimp[1] - m.solimp[0]) * spline_shape(x, m.solimp[3], m.solimp[4]);
   }
-  return fmin(fmax(d, 0.0), 0.9999);
+  if (value(d) < 0.0) return T(0.0);
+  if (value(d) > 0.9999) return T(0.9999);
+  return d;
 }
-__device__ __forceinline__ double softplus(double x) { return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
+template <class T>
+__device__ __forceinline__ T softplus(const T& x) { return value(x) > 0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
 
 // All contact slots, then the included ones (r < 0, or r < w_c for F~) and
 // their per-slot impedance terms.
-template <int G>
-__device__ void collide(const Grp<G>& g, const DevModel& m, const Ws& w, bool cfd) {
+template <int G, class T>
+__device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, bool cfd) {
   const Layout& L = *w.L;
-  const double* gR = w.at(L.gR); const double* gp = w.at(L.gp);
-  double* CT = w.at(L.ct);
+  const T* gR = w.at(L.gR); const T* gp = w.at(L.gp);
+  T* CT = w.at(L.ct);
   const double thr = cfd ? m.cfd[2] : 0.0;
   for (int s = g.lane; s < m.nslot; s += G) {
-    double* ct = CT + 16 * s;
+    T* ct = CT + 16 * s;
     const int p = m.s_pair[s], j = m.s_idx[s], g1 = m.p_g1[p];
     if (m.p_g2[p] >= 0) {
       capsule_box(m, gR, gp, g1, m.p_g2[p], thr, ct);
     } else {
-      const double* Rg = gR + 9 * g1; const double* cg = gp + 3 * g1;
-      double pt[3], rad = 0.0;
+      const T* Rg = gR + 9 * g1; const T* cg = gp + 3 * g1;
+      T pt[3];
+      double rad = 0.0;
       const int ty = m.g_type[g1];
       if (ty == GEOM_SPHERE) { pt[0] = cg[0]; pt[1] = cg[1]; pt[2] = cg[2]; rad = m.g_size[g1][0]; }
       else if (ty == GEOM_CAPSULE) {
@@ -438,18 +489,19 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const Ws& w, bool cf
       } else {
         const double ex[3] = {(j & 1) ? m.g_size[g1][0] : -m.g_size[g1][0], (j & 2) ? m.g_size[g1][1] : -m.g_size[g1][1],
                               (j & 4) ? m.g_size[g1][2] : -m.g_size[g1][2]};
-        double t[3];
+        T t[3];
         matvec3(Rg, ex, t);
         pt[0] = cg[0] + t[0]; pt[1] = cg[1] + t[1]; pt[2] = cg[2] + t[2];
       }
-      const double r = pt[2] - rad;
+      const T r = pt[2] - rad;
       ct[0] = r;
       ct[1] = pt[0]; ct[2] = pt[1]; ct[3] = pt[2] - (rad + 0.5 * r);
-      ct[4] = 0; ct[5] = 0; ct[6] = 1; ct[7] = 1; ct[8] = 0; ct[9] = 0; ct[10] = 0; ct[11] = 1; ct[12] = 0;
+      ct[4] = 0.0; ct[5] = 0.0; ct[6] = 1.0; ct[7] = 1.0; ct[8] = 0.0; ct[9] = 0.0; ct[10] = 0.0; ct[11] = 1.0;
+      ct[12] = 0.0;
     }
-    if (ct[0] < thr) {
-      const double r = ct[0];
-      const double d = impedance(m, r, cfd);
+    if (value(ct[0]) < thr) {
+      const T r = ct[0];
+      const T d = impedance(m, r, cfd);
       const int pr = m.s_pair[s];
       const double ahat = m.p_condim[pr] == 1 ? m.p_ahat[pr] : m.p_ahat_edge[pr];
       ct[13] = d;
@@ -462,17 +514,17 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const Ws& w, bool cf
 
 // Constraint rows of the included contacts (compacted in slot order).
 // Returns the number of rows, or -1 when they exceed the workspace.
-template <int G>
-__device__ int make_rows(const Grp<G>& g, const DevModel& m, const Ws& w, const double* v, bool cfd) {
+template <int G, class T>
+__device__ int make_rows(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* v, bool cfd) {
   const Layout& L = *w.L;
-  const double* CT = w.at(L.ct); const double* S = w.at(L.sd);
+  const T* CT = w.at(L.ct); const T* S = w.at(L.sd);
   int* slotrow = w.i + L.slotrow; int* rowid = w.i + L.rowid;
   const double thr = cfd ? m.cfd[2] : 0.0;
   const int nv = m.nv;
   if (g.lane == 0) {
     int n = 0;
     for (int s = 0; s < m.nslot; ++s) {
-      const bool inc = CT[16 * s] < thr;
+      const bool inc = value(CT[16 * s]) < thr;
       slotrow[s] = inc ? n : -1;
       if (inc) n += (m.p_condim[m.s_pair[s]] == 1) ? 1 : 4;
     }
@@ -481,22 +533,22 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const Ws& w, const 
   g.sync();
   const int nr = slotrow[m.nslot];
   if (nr > L.rcap) return -1;
-  double* J = w.at(L.J);
+  T* J = w.at(L.J);
   for (int idx = g.lane; idx < m.nslot * nv; idx += G) {
     const int s = idx / nv, i = idx - s * nv;
     const int r0 = slotrow[s];
     if (r0 < 0) continue;
-    const double* ct = CT + 16 * s;
+    const T* ct = CT + 16 * s;
     const int p = m.s_pair[s];
     const int bA = m.g_body[m.p_g1[p]];
     const int bB = m.p_g2[p] >= 0 ? m.g_body[m.p_g2[p]] : -1;
     const int bi = m.dof_body[i];
     const bool mA = (m.b_anc[bA] >> bi) & 1u;
     const bool mB = bB >= 0 && ((m.b_anc[bB] >> bi) & 1u);
-    double jn = 0, j1 = 0, j2 = 0;
+    T jn = 0.0, j1 = 0.0, j2 = 0.0;
     if (mA != mB) {
-      const double* sv = S + 6 * i;
-      double pv[3];
+      const T* sv = S + 6 * i;
+      T pv[3];
       cross3(sv, ct + 1, pv);
       pv[0] += sv[3]; pv[1] += sv[4]; pv[2] += sv[5];
       const double sg = mA ? 1.0 : -1.0;
@@ -513,16 +565,16 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const Ws& w, const 
     }
   }
   g.sync();
-  double* aref = w.at(L.aref); double* Dr = w.at(L.Dr);
+  T* aref = w.at(L.aref); T* Dr = w.at(L.Dr);
   for (int s = g.lane; s < m.nslot; s += G) {
     const int r0 = slotrow[s];
     if (r0 < 0) continue;
     const int p = m.s_pair[s];
     const int nrow = m.p_condim[p] == 1 ? 1 : 4;
-    const double* ct = CT + 16 * s;
+    const T* ct = CT + 16 * s;
     for (int e = 0; e < nrow; ++e) {
       const int r = r0 + e;
-      double jv = 0;
+      T jv = 0.0;
       for (int i = 0; i < nv; ++i) jv += J[r * nv + i] * v[i];
       aref[r] = -(m.bcoef * jv) + ct[14];
       Dr[r] = ct[15];
@@ -536,13 +588,13 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const Ws& w, const 
 // ------------------------------------------------------------------ dense kernels
 // H <- its Cholesky factor below the diagonal, invd <- 1 / diagonal of the
 // factor.  Returns false if not SPD.
-template <int G>
-__device__ bool cholesky(const Grp<G>& g, double* H, double* invd, int n) {
+template <int G, class T>
+__device__ bool cholesky(const Grp<G>& g, T* H, T* invd, int n) {
   bool ok = true;
   for (int k = 0; k < n; ++k) {
-    const double hkk = H[k * n + k];
-    ok = ok && (hkk > 0);
-    const double il = 1.0 / sqrt(hkk);   // the diagonal of the factor is kept as its reciprocal
+    const T hkk = H[k * n + k];
+    ok = ok && (value(hkk) > 0);
+    const T il = 1.0 / sqrt(hkk);   // the diagonal of the factor is kept as its reciprocal
     for (int i = k + 1 + g.lane; i < n; i += G) H[i * n + k] *= il;
     if (g.lane == 0) invd[k] = il;
     g.sync();
@@ -557,17 +609,17 @@ __device__ bool cholesky(const Grp<G>& g, double* H, double* invd, int n) {
   return ok;
 }
 // x <- H^-1 x with the factor from cholesky().
-template <int G>
-__device__ void chol_solve(const Grp<G>& g, const double* H, const double* invd, double* x, int n) {
+template <int G, class T>
+__device__ void chol_solve(const Grp<G>& g, const T* H, const T* invd, T* x, int n) {
   for (int k = 0; k < n; ++k) {
-    const double xk = x[k] * invd[k];
+    const T xk = x[k] * invd[k];
     g.sync();
     if (g.lane == 0) x[k] = xk;
     for (int i = k + 1 + g.lane; i < n; i += G) x[i] -= H[i * n + k] * xk;
     g.sync();
   }
   for (int k = n - 1; k >= 0; --k) {
-    const double xk = x[k] * invd[k];
+    const T xk = x[k] * invd[k];
     g.sync();
     if (g.lane == 0) x[k] = xk;
     for (int i = g.lane; i < k; i += G) x[i] -= H[k * n + i] * xk;
@@ -578,24 +630,24 @@ __device__ void chol_solve(const Grp<G>& g, const double* H, const double* invd,
 __device__ __forceinline__ bool mask_has(const int* mk, int id) { return (mk[id >> 5] >> (id & 31)) & 1; }
 
 // H = M + J_A^T D_A J_A, b = rhs0 + J_A^T D_A a_ref,A; factor; an = H^-1 b.
-template <int G>
-__device__ bool solve_active(const Grp<G>& g, const DevModel& m, const Ws& w, int nr, const int* act) {
+template <int G, class T>
+__device__ bool solve_active(const Grp<G>& g, const DevModel& m, const WsT<T>& w, int nr, const int* act) {
   const Layout& L = *w.L;
   const int nv = m.nv;
-  const double* M = w.at(L.M); double* H = w.at(L.H);
-  const double* J = w.at(L.J); const double* aref = w.at(L.aref); const double* Dr = w.at(L.Dr);
-  const double* rhs0 = w.at(L.rhs0); double* an = w.at(L.an);
+  const T* M = w.at(L.M); T* H = w.at(L.H);
+  const T* J = w.at(L.J); const T* aref = w.at(L.aref); const T* Dr = w.at(L.Dr);
+  const T* rhs0 = w.at(L.rhs0); T* an = w.at(L.an);
   const int* rowid = w.i + L.rowid;
   for (int idx = g.lane; idx < nv * nv; idx += G) {
     const int i = idx / nv, j = idx - i * nv;
     if (j > i) continue;
-    double h = M[idx];
+    T h = M[idx];
     for (int r = 0; r < nr; ++r)
       if (mask_has(act, rowid[r])) h += Dr[r] * J[r * nv + i] * J[r * nv + j];
     H[idx] = h;
   }
   for (int i = g.lane; i < nv; i += G) {
-    double b = rhs0[i];
+    T b = rhs0[i];
     for (int r = 0; r < nr; ++r)
       if (mask_has(act, rowid[r])) b += Dr[r] * aref[r] * J[r * nv + i];
     an[i] = b;
@@ -607,54 +659,56 @@ __device__ bool solve_active(const Grp<G>& g, const DevModel& m, const Ws& w, in
 }
 
 // z = J a - a_ref for every row; returns the active set {z < 0} in newmask.
-template <int G>
-__device__ void residual_set(const Grp<G>& g, const DevModel& m, const Ws& w, int nr, const double* a, int* newmask) {
+template <int G, class T>
+__device__ void residual_set(const Grp<G>& g, const DevModel& m, const WsT<T>& w, int nr, const T* a, int* newmask) {
   const Layout& L = *w.L;
   const int nv = m.nv;
-  const double* J = w.at(L.J); const double* aref = w.at(L.aref);
-  double* z = w.at(L.z);
+  const T* J = w.at(L.J); const T* aref = w.at(L.aref);
+  T* z = w.at(L.z);
   const int* rowid = w.i + L.rowid;
   for (int r = g.lane; r < nr; r += G) {
-    double t = 0;
+    T t = 0.0;
     for (int i = 0; i < nv; ++i) t += J[r * nv + i] * a[i];
     z[r] = t - aref[r];
   }
   g.sync();
   for (int k = 0; k < MASKW; ++k) newmask[k] = 0;
   for (int r = 0; r < nr; ++r)
-    if (z[r] < 0) newmask[rowid[r] >> 5] |= 1 << (rowid[r] & 31);
+    if (value(z[r]) < 0) newmask[rowid[r] >> 5] |= 1 << (rowid[r] & 31);
 }
 
 // Exact line search along d = an - a: minimiser over alpha >= 0 of the convex
 // piecewise quadratic primal cost; breakpoints compared without divisions.
-template <int G>
-__device__ double line_search(const Grp<G>& g, const DevModel& m, const Ws& w, int nr) {
+// The search only selects the next Newton iterate, so it runs on values.
+template <int G, class T>
+__device__ double line_search(const Grp<G>& g, const DevModel& m, const WsT<T>& w, int nr) {
   const Layout& L = *w.L;
   const int nv = m.nv;
-  const double* M = w.at(L.M); const double* J = w.at(L.J); const double* Dr = w.at(L.Dr);
-  const double* a = w.at(L.a); const double* an = w.at(L.an); const double* rhs0 = w.at(L.rhs0);
-  double* dl = w.at(L.tmp); double* z = w.at(L.z); double* s = w.at(L.s);
+  const T* M = w.at(L.M); const T* J = w.at(L.J); const T* Dr = w.at(L.Dr);
+  const T* a = w.at(L.a); const T* an = w.at(L.an); const T* rhs0 = w.at(L.rhs0);
+  T* dl = w.at(L.tmp); T* z = w.at(L.z); T* s = w.at(L.s);
   for (int i = g.lane; i < nv; i += G) dl[i] = an[i] - a[i];
   g.sync();
   double c0 = 0, c1 = 0;
   for (int i = g.lane; i < nv; i += G) {
     double ma = 0, md = 0;
-    for (int j = 0; j < nv; ++j) { ma += M[i * nv + j] * a[j]; md += M[i * nv + j] * dl[j]; }
-    c0 += dl[i] * (ma - rhs0[i]);
-    c1 += dl[i] * md;
+    for (int j = 0; j < nv; ++j) { ma += value(M[i * nv + j]) * value(a[j]); md += value(M[i * nv + j]) * value(dl[j]); }
+    c0 += value(dl[i]) * (ma - value(rhs0[i]));
+    c1 += value(dl[i]) * md;
   }
-  const double* aref = w.at(L.aref);
+  const T* aref = w.at(L.aref);
   for (int r = g.lane; r < nr; r += G) {
     double t = 0, u = 0;
-    for (int i = 0; i < nv; ++i) { t += J[r * nv + i] * dl[i]; u += J[r * nv + i] * a[i]; }
+    for (int i = 0; i < nv; ++i) { t += value(J[r * nv + i]) * value(dl[i]); u += value(J[r * nv + i]) * value(a[i]); }
     s[r] = t;
-    z[r] = u - aref[r];
+    z[r] = u - value(aref[r]);
   }
   g.sync();
   double s0 = 0, s1 = 0;
   for (int r = g.lane; r < nr; r += G) {
-    const bool act = z[r] < 0 || (z[r] == 0 && s[r] < 0);
-    if (act) { s0 += Dr[r] * z[r] * s[r]; s1 += Dr[r] * s[r] * s[r]; }
+    const double zr = value(z[r]), sr = value(s[r]), dr = value(Dr[r]);
+    const bool act = zr < 0 || (zr == 0 && sr < 0);
+    if (act) { s0 += dr * zr * sr; s1 += dr * sr * sr; }
   }
   double slope0 = g.sum(c0) + g.sum(s0), slope1 = g.sum(c1) + g.sum(s1);
   // sweep the breakpoints below the current root (each row toggles at most once)
@@ -666,18 +720,19 @@ __device__ double line_search(const Grp<G>& g, const DevModel& m, const Ws& w, i
     double bz = 0, bs = 1;
     for (int r = g.lane; r < nr; r += G) {
       if ((tog[r >> 5] >> (r & 31)) & 1u) continue;
-      const bool act = z[r] < 0 || (z[r] == 0 && s[r] < 0);
-      const bool cand = act ? (s[r] > 0) : (s[r] < 0 && z[r] > 0);
+      const double zr = value(z[r]), sr = value(s[r]);
+      const bool act = zr < 0 || (zr == 0 && sr < 0);
+      const bool cand = act ? (sr > 0) : (sr < 0 && zr > 0);
       if (!cand) continue;
       // -z/s < -slope0/slope1  <=>  z slope1 > s slope0 (s > 0) or z slope1 < s slope0 (s < 0)
-      const double lhs = z[r] * slope1, rhs = s[r] * slope0;
-      const bool below = s[r] > 0 ? (lhs > rhs) : (lhs < rhs);
+      const double lhs = zr * slope1, rhs = sr * slope0;
+      const bool below = sr > 0 ? (lhs > rhs) : (lhs < rhs);
       if (!below) continue;
       // smaller breakpoint: -z/s < -bz/bs  <=>  z bs * sign > bz s * sign with sign(s bs)
-      if (best < 0) { best = r; bz = z[r]; bs = s[r]; continue; }
-      const double l2 = z[r] * bs, r2 = bz * s[r];
-      const bool smaller = (s[r] * bs > 0) ? (l2 > r2) : (l2 < r2);
-      if (smaller) { best = r; bz = z[r]; bs = s[r]; }
+      if (best < 0) { best = r; bz = zr; bs = sr; continue; }
+      const double l2 = zr * bs, r2 = bz * sr;
+      const bool smaller = (sr * bs > 0) ? (l2 > r2) : (l2 < r2);
+      if (smaller) { best = r; bz = zr; bs = sr; }
     }
     // group arg-min over lanes
 #pragma unroll
@@ -695,8 +750,9 @@ __device__ double line_search(const Grp<G>& g, const DevModel& m, const Ws& w, i
       }
     }
     if (best < 0) break;
-    const bool act = z[best] < 0 || (z[best] == 0 && s[best] < 0);
-    const double dz = Dr[best] * z[best] * s[best], ds = Dr[best] * s[best] * s[best];
+    const double zb = value(z[best]), sb = value(s[best]), db = value(Dr[best]);
+    const bool act = zb < 0 || (zb == 0 && sb < 0);
+    const double dz = db * zb * sb, ds = db * sb * sb;
     if (act) { slope0 -= dz; slope1 -= ds; } else { slope0 += dz; slope1 += ds; }
     tog[best >> 5] |= 1u << (best & 31);
   }
@@ -711,13 +767,15 @@ __device__ double line_search(const Grp<G>& g, const DevModel& m, const Ws& w, i
 // minimum between the iterate and an.  The first candidate set is the final
 // set of the previous right-hand side of this environment (pmask): when it is
 // still right, one factorisation finishes the solve; when not, Newton starts
-// from its solution.  pmask receives the final set.  Returns 0 or an ENV_* code.
-template <int G>
-__device__ int solve_constraints(const Grp<G>& g, const DevModel& m, const Ws& w, int nr) {
+// from its solution.  pmask receives the final set.  In derivative scalars the
+// final solve with the final set carries the implicit-function derivative.
+// Returns 0 or an ENV_* code.
+template <int G, class T>
+__device__ int solve_constraints(const Grp<G>& g, const DevModel& m, const WsT<T>& w, int nr) {
   const Layout& L = *w.L;
   const int nv = m.nv;
   int* pm = w.i + L.pmask; int* am = w.i + L.amask;
-  double* a = w.at(L.a); const double* an = w.at(L.an);
+  T* a = w.at(L.a); const T* an = w.at(L.an);
   int cur[MASKW], nxt[MASKW];
   for (int k = 0; k < MASKW; ++k) cur[k] = pm[k];
   bool ok = true;
@@ -736,10 +794,10 @@ __device__ int solve_constraints(const Grp<G>& g, const DevModel& m, const Ws& w
       continue;
     }
     const double alpha = line_search(g, m, w, nr);
-    const double* dl = w.at(L.tmp);
+    const T* dl = w.at(L.tmp);
     for (int i = g.lane; i < nv; i += G) a[i] += alpha * dl[i];
     g.sync();
-    residual_set(g, m, w, nr, a, cur);
+    residual_set(g, m, w, nr, (const T*)a, cur);
   }
   g.sync();
   if (g.lane == 0)
@@ -750,9 +808,9 @@ __device__ int solve_constraints(const Grp<G>& g, const DevModel& m, const Ws& w
 }
 
 // v' = F(q, v, u) (or F~ with cfd) into out[nv].  Returns 0 or an ENV_* code.
-template <int G>
-__device__ int rhs(const Grp<G>& g, const DevModel& m, const Ws& w, const double* q, const double* v,
-                   const double* u, bool cfd, double* out) {
+template <int G, class T>
+__device__ int rhs(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* q, const T* v, const T* u, bool cfd,
+                   T* out) {
   const Layout& L = *w.L;
   kinematics(g, m, w, q);
   crba(g, m, w);
@@ -761,7 +819,7 @@ __device__ int rhs(const Grp<G>& g, const DevModel& m, const Ws& w, const double
   const int nr = make_rows(g, m, w, v, cfd);
   if (nr < 0) return ENV_ROW_OVERFLOW;
   const int st = solve_constraints(g, m, w, nr);
-  const double* an = w.at(L.an);
+  const T* an = w.at(L.an);
   for (int i = g.lane; i < m.nv; i += G) out[i] = an[i];
   g.sync();
   return st;
@@ -786,32 +844,32 @@ static __constant__ Tab c_tab = {
      -2187.0 / 6784.0 + 92097.0 / 339200.0, 11.0 / 84.0 - 187.0 / 2100.0, -1.0 / 40.0}};
 
 // q (+) dq for every joint (free: translation + body-frame rotation exponential).
-template <int G>
-__device__ void integrate_pos(const Grp<G>& g, const DevModel& m, const double* q, const double* dq, double* out) {
+template <int G, class T>
+__device__ void integrate_pos(const Grp<G>& g, const DevModel& m, const T* q, const T* dq, T* out) {
   for (int b = g.lane; b < m.nbody; b += G) {
     const int qa = m.b_qadr[b], va = m.b_vadr[b];
     if (m.b_jtype[b] == JNT_HINGE) { out[qa] = q[qa] + dq[va]; continue; }
     out[qa] = q[qa] + dq[va]; out[qa + 1] = q[qa + 1] + dq[va + 1]; out[qa + 2] = q[qa + 2] + dq[va + 2];
-    const double* d = dq + va + 3;
-    const double th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    double cw, sk;
-    if (th2 < 1e-12) {
+    const T* d = dq + va + 3;
+    const T th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    T cw, sk;
+    if (value(th2) < 1e-12) {
       cw = 1.0 - th2 * 0.125 + th2 * th2 * (1.0 / 384.0);
       sk = 0.5 - th2 * (1.0 / 48.0) + th2 * th2 * (1.0 / 3840.0);
     } else {
-      const double th = sqrt(th2);
-      double sn, cs;
+      const T th = sqrt(th2);
+      T sn, cs;
       sincos(0.5 * th, &sn, &cs);
       cw = cs;
       sk = sn / th;
     }
-    const double ex = sk * d[0], ey = sk * d[1], ez = sk * d[2];
-    const double w0 = q[qa + 3], a0 = q[qa + 4], b0 = q[qa + 5], c0 = q[qa + 6];
-    const double rw = w0 * cw - a0 * ex - b0 * ey - c0 * ez;
-    const double rx = w0 * ex + a0 * cw + b0 * ez - c0 * ey;
-    const double ry = w0 * ey - a0 * ez + b0 * cw + c0 * ex;
-    const double rz = w0 * ez + a0 * ey - b0 * ex + c0 * cw;
-    const double in = 1.0 / sqrt(rw * rw + rx * rx + ry * ry + rz * rz);
+    const T ex = sk * d[0], ey = sk * d[1], ez = sk * d[2];
+    const T w0 = q[qa + 3], a0 = q[qa + 4], b0 = q[qa + 5], c0 = q[qa + 6];
+    const T rw = w0 * cw - a0 * ex - b0 * ey - c0 * ez;
+    const T rx = w0 * ex + a0 * cw + b0 * ez - c0 * ey;
+    const T ry = w0 * ey - a0 * ez + b0 * cw + c0 * ex;
+    const T rz = w0 * ez + a0 * ey - b0 * ex + c0 * cw;
+    const T in = 1.0 / sqrt(rw * rw + rx * rx + ry * ry + rz * rz);
     out[qa + 3] = rw * in; out[qa + 4] = rx * in; out[qa + 5] = ry * in; out[qa + 6] = rz * in;
   }
   g.sync();

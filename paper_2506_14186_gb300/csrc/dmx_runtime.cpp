@@ -17,6 +17,7 @@
 #include "dmx_kernels.h"
 #include "dmx_model.h"
 #include "dmx_runtime.h"
+#include "dmx_adjoint.h"
 
 using namespace dmx;
 
@@ -470,8 +471,29 @@ extern "C" dmx_status dmx_set_lanes(dmx_model* m, int32_t B, int32_t grad, int32
 
 extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, const double* xT_bar,
                                        const double* xb_bar, double* x0_bar, double* ctrl_bar, void* stream) {
-  (void)m; (void)t; (void)cfd; (void)xT_bar; (void)xb_bar; (void)x0_bar; (void)ctrl_bar; (void)stream;
-  return dmx_fail(DMX_ERR_UNIMPLEMENTED, "rollout_grad is not built yet");
+  if (!m || !t) return dmx_fail(DMX_ERR_INVALID, "null model or tape");
+  if (t->model != m) return dmx_fail(DMX_ERR_INVALID, "tape belongs to another model");
+  if (t->B == 0) return DMX_OK;
+  if (!xT_bar || !x0_bar) return dmx_fail(DMX_ERR_INVALID, "xT_bar and x0_bar are required");
+  if (m->host.nu > 0 && !ctrl_bar) return dmx_fail(DMX_ERR_INVALID, "ctrl_bar is required when the model has actuators");
+  if (m->L.nd > dmx::adjoint_workspace_limit() || m->L.ni > dmx::adjoint_int_limit())
+    return dmx_fail(DMX_ERR_INVALID, "model workspace exceeds the adjoint kernel's per-lane limit");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nx = t->nx;
+  const int wpb = dmx::adjoint_warps_per_block();
+  int blocks = (t->B + wpb - 1) / wpb;
+  blocks = std::min(blocks, m->nsm * 8);
+  const size_t seg_bytes = sizeof(double) * (size_t)blocks * wpb * t->K * (nx + 1);
+  CK(m->bufs[1].ensure(seg_bytes + 256));
+  dmx::AdjParams P{};
+  P.model = m->dev; P.L = m->L; P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd;
+  P.ckpt = t->ckpt; P.hlog = t->hlog; P.tape_n = t->n; P.ctrl = t->ctrl; P.T = t->T;
+  P.xT_bar = xT_bar; P.xb_bar = xb_bar; P.x0_bar = x0_bar; P.ctrl_bar = m->host.nu ? ctrl_bar : nullptr;
+  P.segbuf = static_cast<double*>(m->bufs[1].p);
+  P.queue = reinterpret_cast<int*>(static_cast<char*>(m->bufs[1].p) + seg_bytes);
+  CK(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
+  CK(dmx::launch_adjoint(P, blocks, st));
+  return DMX_OK;
 }
 
 extern "C" dmx_status dmx_eval_rhs(dmx_model* m, int32_t B, const double* q, const double* v, const double* u,

@@ -1,0 +1,187 @@
+"""GPU discrete adjoint (dmx_rollout_grad through the C ABI) against the CPU
+oracle's discrete adjoint along the SAME accepted step sequence (the GPU's,
+read back from the tape): 1e-6 relative, the gradient tolerance of the
+workload spec, per environment (scale max(|g_i|, ||g||_inf)); with and
+without the straight-through CFD treatment; interval-boundary cotangents;
+checkpoint intervals; central differences of the frozen-step map (eps 1e-6)
+for the arm's controls; the torch.autograd.Function."""
+
+import numpy as np
+import pytest
+
+from paper_2506_14186_gb300 import workloads as W
+from tests.conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-6
+CFD_OPT = dict(solimp=(0.1, 0.95, 0.001, 0.5, 2.0), solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+# CFD continuation only (the forward right-hand side keeps d(0) = 0, so contact
+# forces stay continuous and the box pushes integrate with ordinary step sizes)
+CFD_ONLY = dict(solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+
+
+@pytest.fixture(scope="module")
+def dmx():
+    import torch
+    from paper_2506_14186_gb300 import _build
+    _build.build()
+    import paper_2506_14186_gb300 as d
+    assert torch.cuda.is_available()
+    return d
+
+
+@pytest.fixture(scope="module")
+def orc_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def gpu_grad(dmx, model, inp, xT_bar, xb_bar=None, cfd=False, K=32):
+    """Taped GPU rollout + adjoint.  Arrays env-major in and out."""
+    ctrl = None if inp["ctrl"] is None else _dev(np.transpose(inp["ctrl"], (1, 2, 0)))
+    out = dmx.rollout(model, _dev(inp["x0"].T), _dev(inp["T"]), ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"],
+                      atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"], K=K, tape=True)
+    xbb = None if xb_bar is None else _dev(np.transpose(xb_bar, (1, 2, 0)))
+    gx, gu = dmx.rollout_grad(out["tape"], _dev(xT_bar.T), xbb, cfd=cfd)
+    hlog, n = out["tape"].read()
+    res = {"x0_bar": gx.cpu().numpy().T, "hlog": hlog.cpu().numpy().T, "n": n.cpu().numpy(),
+           "xT": out["xT"].cpu().numpy().T, "status": out["status"].cpu().numpy()}
+    if gu is not None:
+        res["ctrl_bar"] = np.transpose(gu.cpu().numpy(), (2, 0, 1))
+    return res
+
+
+def oracle_grad(orc_mod, scene, inp, g, xT_bar, xb_bar=None, cfd=False):
+    m = orc_mod.OracleModel(scene)
+    return m.batch_replay_grad(inp["x0"], inp["T"], g["hlog"], g["n"], xT_bar, ctrl=inp["ctrl"], NI=inp["NI"],
+                               cfd=cfd, xb_bar=xb_bar)
+
+
+def assert_grad(g, o, key="x0_bar"):
+    B = len(o[key])
+    err = max(rel_err(np.ravel(g[key][e]), np.ravel(o[key][e])) for e in range(B))
+    assert err < TOL, f"{key}: relative error {err:.3e}"
+    return err
+
+
+@pytest.mark.parametrize("cfd", [False, True])
+def test_ball_gradient(dmx, orc_mod, cfd):
+    """Bouncing balls (full batch, T = 1 s): gradient of the final height and
+    velocity w.r.t. the whole initial state; with CFD parameters of App. D.3."""
+    sc = W.ball_scene(**CFD_OPT) if cfd else W.ball_scene()
+    inp = W.ball_inputs(16)
+    rng = np.random.default_rng(0)
+    xT_bar = rng.normal(size=(16, 13))
+    m = dmx.Model(sc)
+    g = gpu_grad(dmx, m, inp, xT_bar, cfd=cfd)
+    o = oracle_grad(orc_mod, sc, inp, g, xT_bar, cfd=cfd)
+    assert_grad(g, o)
+
+
+@pytest.mark.parametrize("cfd", [False, True])
+@pytest.mark.parametrize("K", [1, 7, 32])
+def test_box_gradient(dmx, orc_mod, cfd, K):
+    sc = W.box_scene(**CFD_ONLY) if cfd else W.box_scene()
+    inp = W.box_push_inputs(24, seed=5, T=0.3)
+    rng = np.random.default_rng(1)
+    xT_bar = rng.normal(size=(24, 13))
+    m = dmx.Model(sc)
+    g = gpu_grad(dmx, m, inp, xT_bar, cfd=cfd, K=K)
+    assert np.all(g["status"] == 0)
+    assert_grad(g, oracle_grad(orc_mod, sc, inp, g, xT_bar, cfd=cfd))
+
+
+@pytest.mark.parametrize("cfd", [False, True])
+def test_chain_control_gradient_with_boundary_cotangents(dmx, orc_mod, cfd):
+    """Arm + cube: loss on the cube's final position and on every
+    interval-boundary state; gradient w.r.t. x0 and every control."""
+    sc = W.chain_cube_scene(**CFD_OPT) if cfd else W.chain_cube_scene()
+    inp = W.chain_inputs(8, T=0.24, NI=6)
+    rng = np.random.default_rng(2)
+    nx = 27
+    xT_bar = rng.normal(size=(8, nx))
+    xb_bar = rng.normal(size=(8, 7, nx))
+    m = dmx.Model(sc)
+    g = gpu_grad(dmx, m, inp, xT_bar, xb_bar=xb_bar, cfd=cfd, K=5)
+    o = oracle_grad(orc_mod, sc, inp, g, xT_bar, xb_bar=xb_bar, cfd=cfd)
+    assert_grad(g, o)
+    assert_grad(g, o, "ctrl_bar")
+
+
+def test_quadruped_gradient_two_direction_passes(dmx, orc_mod):
+    """19 + 18 coordinates and 12 servo targets: 49 input directions, two
+    32-lane passes per step."""
+    sc = W.quadruped_scene()
+    inp = W.quadruped_inputs(6)
+    inp["T"] = np.minimum(inp["T"], 0.2)
+    rng = np.random.default_rng(3)
+    xT_bar = np.zeros((6, 37)); xT_bar[:, 0:3] = rng.normal(size=(6, 3))
+    m = dmx.Model(sc)
+    g = gpu_grad(dmx, m, inp, xT_bar, K=16)
+    o = oracle_grad(orc_mod, sc, inp, g, xT_bar)
+    assert_grad(g, o)
+    assert_grad(g, o, "ctrl_bar")
+
+
+def test_chain_gradient_matches_central_differences(dmx, orc_mod):
+    """The workload's check: loss = squared cube-to-goal distance, gradient
+    w.r.t. 16 controls of each of 8 environments against central differences
+    (eps = 1e-6) of the frozen-step map (the GPU's step sizes replayed)."""
+    sc = W.chain_cube_scene()
+    inp = W.chain_inputs(8, T=0.4, NI=10)
+    goal = W.chain_goal()
+    m = dmx.Model(sc)
+    om = orc_mod.OracleModel(sc)
+    # first pass for the final cube position, then the loss cotangent
+    g0 = gpu_grad(dmx, m, inp, np.zeros((8, 27)))
+    xT_bar = np.zeros((8, 27)); xT_bar[:, 7:10] = 2 * (g0["xT"][:, 7:10] - goal)
+    g = gpu_grad(dmx, m, inp, xT_bar)
+    rng = np.random.default_rng(4)
+    worst = 0.0
+    for e in range(8):
+        n = int(g["n"][e])
+        idx = rng.choice(10 * 7, 16, replace=False)
+
+        def loss(ctrl):
+            xT, _ = om.replay(inp["x0"][e], g["hlog"][e, :n], ctrl=ctrl, T=float(inp["T"][e]), NI=10)
+            return float(((xT[7:10] - goal) ** 2).sum())
+        fd = []
+        for j in idx:
+            c = inp["ctrl"][e].copy().ravel(); c[j] += 1e-6
+            lp = loss(c.reshape(10, 7))
+            c[j] -= 2e-6
+            lm = loss(c.reshape(10, 7))
+            fd.append((lp - lm) / 2e-6)
+        fd = np.array(fd)
+        got = g["ctrl_bar"][e].ravel()[idx]
+        scale = max(np.abs(g["ctrl_bar"][e]).max(), 1e-12)
+        worst = max(worst, np.abs(got - fd).max() / scale)
+    assert worst < 1e-5, worst
+
+
+def test_autograd_function(dmx):
+    import torch
+    sc = W.chain_cube_scene()
+    inp = W.chain_inputs(4, T=0.2, NI=5)
+    m = dmx.Model(sc)
+    x0 = _dev(inp["x0"].T).requires_grad_(True)
+    ctrl = _dev(np.transpose(inp["ctrl"], (1, 2, 0))).requires_grad_(True)
+    xT, xb, status = dmx.rollout_fn(m, x0, _dev(inp["T"]), ctrl=ctrl, NI=5, K=8)
+    goal = torch.tensor(W.chain_goal(), device="cuda")[:, None]
+    loss = ((xT[7:10] - goal) ** 2).sum() + 0.1 * (xb[:, 7:10] ** 2).sum() + (xT[0:7] ** 2).sum()
+    loss.backward()
+    assert x0.grad is not None and ctrl.grad is not None
+    assert torch.isfinite(ctrl.grad).all() and ctrl.grad.abs().max() > 0
+    # same as calling the adjoint directly with the loss cotangents
+    out = dmx.rollout(m, x0.detach(), _dev(inp["T"]), ctrl=ctrl.detach(), NI=5, K=8, tape=True, want_xb=True)
+    xT_bar = torch.zeros_like(out["xT"]); xT_bar[7:10] = 2 * (out["xT"][7:10] - goal)
+    xT_bar[0:7] = 2 * out["xT"][0:7]
+    xb_bar = torch.zeros_like(out["xb"]); xb_bar[:, 7:10] = 0.2 * out["xb"][:, 7:10]
+    gx, gu = dmx.rollout_grad(out["tape"], xT_bar, xb_bar)
+    assert torch.allclose(gx, x0.grad, rtol=1e-12, atol=0) and torch.allclose(gu, ctrl.grad, rtol=1e-12, atol=0)
