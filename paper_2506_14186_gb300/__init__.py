@@ -95,6 +95,7 @@ def lib():
             raise ImportError(f"libdmx.so not built ({_LIB_PATH}); run paper_2506_14186_gb300._build.build()")
         L = ctypes.CDLL(_LIB_PATH)
         L.dmx_last_error.restype = ctypes.c_char_p
+        L.dmx_server_destroy.argtypes = [c_p, c_f64]
         for name in ("dmx_create_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad", "dmx_autotune",
                      "dmx_server_create", "dmx_submit", "dmx_poll", "dmx_server_destroy", "dmx_model_info",
                      "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read", "dmx_rollout_static"):
@@ -363,3 +364,79 @@ def rollout_fn(model, x0, T, ctrl=None, **opts):
     if _RolloutFn is None:
         _RolloutFn = _rollout_fn_class()
     return _RolloutFn.apply(x0, ctrl, model, T, opts)
+
+
+class Server:
+    """Continuous-batching request server (dmx_server_*): requests of any
+    model, batch size and horizon are queued by submit() and admitted to the
+    device as slots and memory free up; poll() returns the outputs (host
+    arrays) and the submit-to-completion latency once a request is done."""
+
+    def __init__(self, device_bytes=8 << 30, max_inflight=8, nstreams=8):
+        cfg = ServerCfg(int(device_bytes), int(max_inflight), int(nstreams))
+        h = c_p()
+        _check(lib().dmx_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self._live = {}
+
+    @staticmethod
+    def _host(a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return a
+
+    def submit(self, model, x0, T, ctrl=None, NI=1, grad=False, xT_bar=None, cfd=False, rtol=1e-6, atol=1e-8,
+               h0=1e-3, max_steps=20000, K=32):
+        """x0 [nx, B], T [B], ctrl [NI, nu, B], xT_bar [nx, B] (host arrays, SoA).
+        Returns a ticket."""
+        x0 = self._host(x0); T = self._host(T)
+        B = x0.shape[1]
+        keep = {"x0": x0, "T": T, "model": model}
+        keep["xT"] = np.empty((model.nx, B))
+        keep["status"] = np.empty(B, dtype=np.int32)
+        if model.nu:
+            keep["ctrl"] = self._host(ctrl)
+        if grad:
+            keep["xT_bar"] = self._host(xT_bar)
+            keep["x0_bar"] = np.empty((model.nx, B))
+            keep["ctrl_bar"] = np.empty((NI, model.nu, B)) if model.nu else None
+        ptr = lambda k: keep[k].ctypes.data if keep.get(k) is not None else None
+        req = Request(model.h.value, B, NI, max_steps, K, rtol, atol, h0, ptr("x0"), ptr("ctrl"), ptr("T"), int(grad),
+                      int(cfd), ptr("xT_bar"), ptr("xT"), ptr("x0_bar"), ptr("ctrl_bar"), ptr("status"))
+        t = ctypes.c_uint64()
+        _check(lib().dmx_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
+        self._live[t.value] = keep
+        return t.value
+
+    def poll(self, ticket):
+        """None while the request runs; else a dict of its outputs and latency_s."""
+        lat = c_f64()
+        rc = lib().dmx_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(lat))
+        if rc == DMX_NOT_READY:
+            return None
+        keep = self._live.pop(ticket, None)
+        _check(rc)
+        out = {k: keep[k] for k in ("xT", "status", "x0_bar", "ctrl_bar") if keep.get(k) is not None}
+        out["latency_s"] = lat.value
+        return out
+
+    def wait(self, ticket, timeout=600.0, sleep=1e-4):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout:
+                raise TimeoutError(f"request {ticket} not done after {timeout} s")
+            time.sleep(sleep)
+
+    def close(self, timeout=600.0):
+        if getattr(self, "h", None):
+            _check(lib().dmx_server_destroy(self.h, c_f64(timeout)))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -176,6 +176,14 @@ extern "C" dmx_status dmx_create_model(const dmx_model_desc* desc, dmx_model** o
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, m->device));
   m->nsm = prop.multiProcessorCount;
+  {
+    // keep stream-ordered per-call scratch cached in the device's default pool
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, m->device) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
   m->smem_max = (int)prop.sharedMemPerBlockOptin;
   if (cudaMalloc(&m->dev, sizeof(DevModel)) != cudaSuccess) { delete m; return dmx_fail(DMX_ERR_OOM, "model upload"); }
   CK(cudaMemcpy(m->dev, &m->host, sizeof(DevModel), cudaMemcpyHostToDevice));
@@ -200,7 +208,6 @@ extern "C" dmx_status dmx_create_model(const dmx_model_desc* desc, dmx_model** o
   }
   for (int b = 0; b < m->host.nbody; ++b) m->invw[b] = invw[b];
   CK(cudaMemcpy(m->dev, &m->host, sizeof(DevModel), cudaMemcpyHostToDevice));
-  CK(cudaMalloc(&m->queue, sizeof(int) * 4));
   *out = m;
   return DMX_OK;
 }
@@ -211,9 +218,6 @@ extern "C" void dmx_destroy_model(dmx_model* m) {
   cudaGetDevice(&cur);
   cudaSetDevice(m->device);
   cudaFree(m->dev);
-  cudaFree(m->queue);
-  for (auto& b : m->bufs) b.free_all();
-  m->step_buf.free_all();
   cudaSetDevice(cur);
   delete m;
 }
@@ -271,22 +275,28 @@ dmx_status run_rollout(dmx_model* m, const RolloutParams& P0, int form, int G, c
     return dmx_fail(DMX_ERR_INVALID, "workspace of " + std::to_string(G) + " lanes/env does not fit shared memory");
   if (P.B == 0) return DMX_OK;
   if (form == DMX_FORM_PERSISTENT) {
-    CK(cudaMemsetAsync(m->queue, 0, sizeof(int), st));
-    P.queue = m->queue;
+    // per-call work counter (stream ordered, so concurrent calls on other
+    // streams never share it)
+    int* q = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(int), st));
+    CK(cudaMemsetAsync(q, 0, sizeof(int), st));
+    P.queue = q;
     int per_sm = persistent_occupancy(G, threads, smem);
     if (per_sm < 1) per_sm = 1;
     const long long groups = (long long)m->nsm * per_sm * (threads / G);
     long long blocks = (long long)m->nsm * per_sm;
     if (groups > P.B) blocks = std::max(1LL, ((long long)P.B * G + threads - 1) / threads);
     CK(launch_persistent(G, P, (int)blocks, threads, smem, st));
+    CK(cudaFreeAsync(q, st));
     return DMX_OK;
   }
   // plain form: state in HBM, one launch per attempt
   const int nq = m->host.nq, nv = m->host.nv;
   const size_t B = P.B;
   const size_t need = B * (sizeof(double) * (nq + 2 * nv + 3) + sizeof(int) * (7 + MASKW)) + 64;
-  CK(m->step_buf.ensure(need));
-  char* base = static_cast<char*>(m->step_buf.p);
+  void* mem = nullptr;
+  CK(cudaMallocAsync(&mem, need, st));
+  char* base = static_cast<char*>(mem);
   StepState S;
   size_t off = 0;
   auto takeD = [&](size_t n) { double* r = reinterpret_cast<double*>(base + off); off += n * sizeof(double); return r; };
@@ -298,7 +308,10 @@ dmx_status run_rollout(dmx_model* m, const RolloutParams& P0, int form, int G, c
   const int Bi = P.B;
   CK(cudaMemcpyAsync(S.active, &Bi, sizeof(int), cudaMemcpyHostToDevice, st));
   CK(launch_step(G, P, S, true, threads, smem, st));
-  int* h_active = m->pinned_int();
+  // device-to-pageable copies return once the copy (and the work before it on
+  // the stream) has completed
+  int active_host = P.B;
+  int* h_active = &active_host;
   const int chunk = 64;
   long long launched = 0;
   const long long limit = (long long)P.max_steps + 2;
@@ -315,41 +328,30 @@ dmx_status run_rollout(dmx_model* m, const RolloutParams& P0, int form, int G, c
     for (int i = 0; i < chunk; ++i) launch_step(G, P, S, false, threads, smem, cap);
     CK(cudaStreamEndCapture(cap, &graph));
     CK(cudaGraphInstantiate(&exec, graph, 0));
-    cudaEvent_t ev;
-    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     for (;;) {
       CK(cudaGraphLaunch(exec, st));
       launched += chunk;
       CK(cudaMemcpyAsync(h_active, S.active, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaEventRecord(ev, st));
-      CK(cudaEventSynchronize(ev));
+      CK(cudaStreamSynchronize(st));
       if (*h_active <= 0 || launched > limit) break;
     }
-    cudaEventDestroy(ev);
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
   } else {
-    cudaEvent_t ev;
-    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     for (;;) {
       for (int i = 0; i < chunk; ++i) CK(launch_step(G, P, S, false, threads, smem, st));
       launched += chunk;
       CK(cudaMemcpyAsync(h_active, S.active, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaEventRecord(ev, st));
-      CK(cudaEventSynchronize(ev));
+      CK(cudaStreamSynchronize(st));
       if (*h_active <= 0 || launched > limit) break;
     }
-    cudaEventDestroy(ev);
   }
+  CK(cudaFreeAsync(mem, st));
   if (*h_active > 0) return dmx_fail(DMX_ERR_TIMEOUT, "plain form did not finish within max_steps launches");
   return DMX_OK;
 }
 
-int* dmx_model::pinned_int() {
-  if (!pin) cudaMallocHost(&pin, 64);
-  return pin;
-}
 
 static dmx_status make_tape(dmx_model* m, const dmx_rollout_args* a, const double* ctrl, const double* T,
                             cudaStream_t st, dmx_tape** out) {
@@ -361,7 +363,8 @@ static dmx_status make_tape(dmx_model* m, const dmx_rollout_args* a, const doubl
   const size_t B = a->B;
   const size_t bytes = sizeof(double) * ((size_t)t->ncheck * (t->nx + 1) * B + (size_t)a->max_steps * B +
                                          (size_t)a->NI * t->nu * B + B) + sizeof(int) * B;
-  if (cudaMalloc(&t->mem, bytes) != cudaSuccess) { delete t; return dmx_fail(DMX_ERR_OOM, "tape allocation of " + std::to_string(bytes) + " bytes"); }
+  if (cudaMallocAsync(&t->mem, bytes, st) != cudaSuccess) { delete t; return dmx_fail(DMX_ERR_OOM, "tape allocation of " + std::to_string(bytes) + " bytes"); }
+  t->stream = st;
   t->bytes = bytes;
   double* p = static_cast<double*>(t->mem);
   t->ckpt = p; p += (size_t)t->ncheck * (t->nx + 1) * B;
@@ -377,7 +380,7 @@ static dmx_status make_tape(dmx_model* m, const dmx_rollout_args* a, const doubl
 
 extern "C" void dmx_tape_free(dmx_tape* t) {
   if (!t) return;
-  cudaFree(t->mem);
+  cudaFreeAsync(t->mem, t->stream);   // ordered after the work queued on the tape's stream
   delete t;
 }
 
@@ -410,8 +413,9 @@ extern "C" dmx_status dmx_rollout(dmx_model* m, const dmx_rollout_args* a, void*
     const size_t nin = B * nx + (size_t)a->NI * nu * B + B;
     const size_t nout = B * nx + (a->xb ? (size_t)(a->NI + 1) * nx * B : 0);
     const size_t bytes = sizeof(double) * (nin + nout) + sizeof(int) * 3 * B + 256;
-    CK(m->bufs[0].ensure(bytes));
-    double* p = static_cast<double*>(m->bufs[0].p);
+    void* stage = nullptr;
+    CK(cudaMallocAsync(&stage, bytes, st));
+    double* p = static_cast<double*>(stage);
     double* dx0 = p; p += B * nx;
     double* dctrl = p; p += (size_t)a->NI * nu * B;
     double* dT = p; p += B;
@@ -431,6 +435,7 @@ extern "C" dmx_status dmx_rollout(dmx_model* m, const dmx_rollout_args* a, void*
     if (a->nsteps) CK(cudaMemcpyAsync(a->nsteps, dns, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
     if (a->nrej) CK(cudaMemcpyAsync(a->nrej, dnr, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
     if (a->status) CK(cudaMemcpyAsync(a->status, dst, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(stage, st));
     CK(cudaStreamSynchronize(st));
     return DMX_OK;
   }
@@ -484,15 +489,17 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
   int blocks = (t->B + wpb - 1) / wpb;
   blocks = std::min(blocks, m->nsm * 8);
   const size_t seg_bytes = sizeof(double) * (size_t)blocks * wpb * t->K * (nx + 1);
-  CK(m->bufs[1].ensure(seg_bytes + 256));
+  void* scratch = nullptr;
+  CK(cudaMallocAsync(&scratch, seg_bytes + 256, st));
   dmx::AdjParams P{};
   P.model = m->dev; P.L = m->L; P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd;
   P.ckpt = t->ckpt; P.hlog = t->hlog; P.tape_n = t->n; P.ctrl = t->ctrl; P.T = t->T;
   P.xT_bar = xT_bar; P.xb_bar = xb_bar; P.x0_bar = x0_bar; P.ctrl_bar = m->host.nu ? ctrl_bar : nullptr;
-  P.segbuf = static_cast<double*>(m->bufs[1].p);
-  P.queue = reinterpret_cast<int*>(static_cast<char*>(m->bufs[1].p) + seg_bytes);
+  P.segbuf = static_cast<double*>(scratch);
+  P.queue = reinterpret_cast<int*>(static_cast<char*>(scratch) + seg_bytes);
   CK(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
   CK(dmx::launch_adjoint(P, blocks, st));
+  CK(cudaFreeAsync(scratch, st));
   return DMX_OK;
 }
 

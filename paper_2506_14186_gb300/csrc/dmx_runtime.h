@@ -24,13 +24,8 @@ struct dmx_model {
   dmx::Layout L;
   int device = 0, nsm = 0, smem_max = 0, rcap = 0;
   double invw[dmx::MAXB];
-  int* queue = nullptr;          // persistent-form work counter
-  int* pin = nullptr;            // pinned host int for polling
-  DevBuf step_buf;               // plain-form state
-  DevBuf bufs[4];                // staging / scratch
   std::mutex mu;
   std::map<std::pair<int, int>, int> tuned;   // (B, grad) -> lanes per environment
-  int* pinned_int();
 };
 
 struct dmx_tape {
@@ -44,6 +39,7 @@ struct dmx_tape {
   double* ctrl = nullptr;   // [NI][nu][B]
   double* T = nullptr;      // [B]
   int* n = nullptr;         // [B] accepted steps
+  cudaStream_t stream = nullptr;   // allocation stream (stream-ordered free)
 };
 
 dmx_status dmx_fail(dmx_status s, const std::string& msg);
