@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--form", choices=["persistent", "step", "graph"], default="persistent")
     p.add_argument("--lanes", type=int, default=0, help="lanes per environment (0 = autotuned)")
     p.add_argument("--no-extras", action="store_true", help="skip the plain-form and CPU-baseline legs")
+    p.add_argument("--serving", action="store_true", help="served-request latency benchmark instead of the rollout bench")
+    p.add_argument("--requests", type=int, default=40)
+    p.add_argument("--warmup-requests", type=int, default=5)
+    p.add_argument("--rate", type=float, default=200.0, help="Poisson arrival rate (requests/s)")
     return p.parse_args()
 
 
@@ -279,12 +283,53 @@ def run_ours(args):
                 t = e0.elapsed_time(e1)
                 extra[form] = {"value": int(out["nsteps"].sum().item()) / (t * 1e-3), "ms_per_step": t}
             result["plain_forms"] = extra
+            result["fwd_adjoint"] = grad_leg(dmx, dev)
             rate, sample, cores, _ = oracle_rate(inp)
             result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return result
+
+
+def grad_leg(dmx, dev, B=256):
+    """Forward (taped) + discrete adjoint of the arm-pushes-cube workload (7
+    hinges + free cube, 50 torque intervals over 2 s, K = 32), loss = squared
+    cube-to-goal distance, on a bounded sample of the 16384 environments."""
+    import torch
+    from paper_2506_14186_gb300 import workloads as W
+    sc = W.chain_cube_scene()
+    inp = W.chain_inputs(16384)
+    m = dmx.Model(sc)
+    x0 = torch.tensor(np.ascontiguousarray(inp["x0"][:B].T), device=dev)
+    ctrl = torch.tensor(np.ascontiguousarray(np.transpose(inp["ctrl"][:B], (1, 2, 0))), device=dev)
+    T = torch.tensor(inp["T"][:B], device=dev)
+    goal = torch.tensor(W.chain_goal(), device=dev)[:, None]
+    st = torch.cuda.current_stream()
+
+    def run():
+        out = dmx.rollout(m, x0, T, ctrl=ctrl, NI=50, K=32, tape=True)
+        xT_bar = torch.zeros_like(out["xT"])
+        xT_bar[7:10] = 2 * (out["xT"][7:10] - goal)
+        gx, gu = dmx.rollout_grad(out["tape"], xT_bar)
+        return out, gu
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(st)
+    out = dmx.rollout(m, x0, T, ctrl=ctrl, NI=50, K=32, tape=True)
+    e1.record(st)
+    xT_bar = torch.zeros_like(out["xT"])
+    xT_bar[7:10] = 2 * (out["xT"][7:10] - goal)
+    gx, gu = dmx.rollout_grad(out["tape"], xT_bar)
+    e2.record(st)
+    e2.synchronize()
+    t_f, t_all = e0.elapsed_time(e1) * 1e-3, e0.elapsed_time(e2) * 1e-3
+    steps = int(out["nsteps"].sum().item())
+    return {"workload": "chain_cube (7 hinges + cube, NI=50, T=2 s, K=32)", "sample_envs": B,
+            "grad_rollouts_per_s": B / t_all, "env_steps_per_s": steps / t_all, "forward_s": t_f,
+            "adjoint_s": t_all - t_f, "env_steps": steps, "finite": bool(torch.isfinite(gu).all().item())}
 
 
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
@@ -311,8 +356,120 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ serving
+def make_requests(n, seed=5005):
+    """Seeded request mix: model in {ball, box, chain_cube} uniform, B ~ U{64..1024},
+    T ~ U[0.2, 2] s (arm: NI = round(25 T) torque intervals), half forward-only,
+    half forward + adjoint (loss = squared final position of the last body)."""
+    from paper_2506_14186_gb300 import workloads as W
+    g = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        name = ("ball", "box", "chain_cube")[int(g.integers(0, 3))]
+        B = int(g.integers(64, 1025))
+        T = float(g.uniform(0.2, 2.0))
+        grad = bool(g.integers(0, 2))
+        if name == "chain_cube":
+            NI = max(1, int(round(25 * T)))
+            inp = W.chain_inputs(B, seed=seed + i, T=T, NI=NI)
+        else:
+            NI = 1
+            inp = W.INPUTS[name](B, seed=seed + i, T=T)
+        reqs.append({"name": name, "B": B, "T": T, "NI": NI, "grad": grad, "inp": inp})
+    return reqs
+
+
+def run_serving(args):
+    import torch
+
+    import paper_2506_14186_gb300 as dmx
+    from paper_2506_14186_gb300 import _build
+    from paper_2506_14186_gb300 import workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    models = {n: dmx.Model(W.SCENES[n]()) for n in ("ball", "box", "chain_cube")}
+    total = args.warmup_requests + args.requests
+    reqs = make_requests(total)
+    g = np.random.default_rng(77)
+    arrivals = np.cumsum(g.exponential(1.0 / args.rate, total))
+    host = []
+    for r in reqs:
+        m = models[r["name"]]
+        inp = r["inp"]
+        x0 = np.ascontiguousarray(inp["x0"].T)
+        ctrl = None if inp["ctrl"] is None else np.ascontiguousarray(np.transpose(inp["ctrl"], (1, 2, 0)))
+        xT_bar = None
+        if r["grad"]:
+            xT_bar = np.zeros((m.nx, r["B"]))
+            xT_bar[2] = 1.0                          # d(height of the first free-joint coordinate)
+        host.append((m, x0, np.ascontiguousarray(inp["T"]), ctrl, xT_bar))
+
+    def served():
+        srv = dmx.Server(device_bytes=96 << 30, max_inflight=32, nstreams=16)
+        t0 = time.perf_counter()
+        tickets, lat, done = {}, {}, set()
+        i = 0
+        while len(done) < total:
+            now = time.perf_counter() - t0
+            while i < total and arrivals[i] <= now:
+                m, x0, T, ctrl, xb = host[i]
+                r = reqs[i]
+                tickets[i] = srv.submit(m, x0, T, ctrl=ctrl, NI=r["NI"], grad=r["grad"], xT_bar=xb)
+                i += 1
+            for j, t in list(tickets.items()):
+                if j in done:
+                    continue
+                o = srv.poll(t)
+                if o is not None:
+                    lat[j] = o["latency_s"]
+                    done.add(j)
+            time.sleep(2e-4)
+        makespan = time.perf_counter() - t0
+        srv.close()
+        return lat, makespan
+
+    def plain():
+        """One request at a time in arrival order, forward pass by per-attempt
+        launches (plain form); latency counted from the arrival time."""
+        dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        lat = {}
+        for j in range(total):
+            while time.perf_counter() - t0 < arrivals[j]:
+                time.sleep(1e-4)
+            m, x0, T, ctrl, xb = host[j]
+            r = reqs[j]
+            out = dmx.rollout(m, dev(x0), dev(T), ctrl=None if ctrl is None else dev(ctrl), NI=r["NI"], form="step",
+                              tape=r["grad"])
+            if r["grad"]:
+                gx, gu = dmx.rollout_grad(out["tape"], dev(xb))
+                gx.cpu()
+            out["xT"].cpu()
+            lat[j] = time.perf_counter() - t0 - arrivals[j]
+        return lat, time.perf_counter() - t0
+
+    res = {}
+    for name, fn in (("continuous_batching", served), ("plain_per_request", plain)):
+        lat, makespan = fn()
+        vals = np.array([lat[j] for j in range(args.warmup_requests, total)])
+        rollouts = sum(reqs[j]["B"] for j in range(total))
+        res[name] = {"p50_s": float(np.percentile(vals, 50)), "p99_s": float(np.percentile(vals, 99)),
+                     "mean_s": float(vals.mean()), "rollouts_per_s": rollouts / makespan, "makespan_s": makespan}
+    head = res["continuous_batching"]
+    return {"metric": METRIC, "value": head["p50_s"], "unit": "s (p50 request latency)", "n_gpus": 1,
+            "higher_is_better": False, "steps": args.requests, "warmup": args.warmup_requests,
+            "dtype": "f64", "data": "synthetic (seeded request mix)", "vs_baseline": None,
+            "config": {"workload": "served MPC requests", "arrivals": f"Poisson {args.rate}/s",
+                       "mix": "ball/box/chain_cube uniform, B~U{64..1024}, T~U[0.2,2] s, 50% fwd+adjoint",
+                       "requests": args.requests, "warmup_requests": args.warmup_requests},
+            "serving": res}
+
+
 def main():
     args = parse()
+    if args.serving:
+        print(json.dumps(run_serving(args)), flush=True)
+        return
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
         print(json.dumps(res), flush=True)
