@@ -63,6 +63,8 @@ enum { DMX_JNT_FREE = 0, DMX_JNT_HINGE = 1 };
 enum { DMX_GEOM_SPHERE = 0, DMX_GEOM_CAPSULE = 1, DMX_GEOM_BOX = 2 };
 enum { DMX_ACT_MOTOR = 0, DMX_ACT_POSITION = 1 };
 enum { DMX_FORM_PERSISTENT = 0, DMX_FORM_STEP = 1, DMX_FORM_STEP_GRAPH = 2 };
+/* adjoint kernels of dmx_rollout_grad (dmx_set_adjoint) */
+enum { DMX_ADJ_REVERSE = 0, DMX_ADJ_TANGENT = 1 };
 
 /* ------------------------------------------------------------------ model */
 /* Body of a kinematic tree.  parent < own index (-1 = world).  A free joint
@@ -169,6 +171,19 @@ dmx_status dmx_rollout(dmx_model* m, const dmx_rollout_args* a, void* stream);
  * pointers, ordered on `stream`.  The tape stays valid (may be reused). */
 dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* tape, int32_t cfd, const double* xT_bar,
                             const double* xb_bar, double* x0_bar, double* ctrl_bar, void* stream);
+/* Kernel that dmx_rollout_grad runs for this model (both compute the same
+ * derivative; results agree to rounding):
+ *   DMX_ADJ_REVERSE (default): reverse mode, a group of lanes per environment
+ *     (lanes from dmx_set_lanes(m, B, 2, G), G in {2, 4, 8, 16, 32}, else a
+ *     default that fills the SMs); per accepted step it transposes the
+ *     Dormand-Prince stages with one right-hand-side VJP per stage.  An
+ *     environment whose right-hand side overflowed the row workspace during
+ *     the adjoint gets NaN in x0_bar.
+ *   DMX_ADJ_TANGENT: forward-mode derivative scalars, one warp per
+ *     environment and one input direction per lane (the Jacobian of every
+ *     step, column by column); kept as an independent check.
+ * DMX_ERR_INVALID for another mode. */
+dmx_status dmx_set_adjoint(dmx_model* m, int32_t mode);
 void dmx_tape_free(dmx_tape* t);
 /* Copies a tape into caller DEVICE buffers (any may be NULL), on `stream`:
  * hlog [max_steps][B] accepted step sizes (entries past nsteps[e] undefined),
@@ -184,8 +199,9 @@ dmx_status dmx_tape_read(const dmx_tape* t, double* hlog, int32_t* nsteps, doubl
  * autotuner's choice), else a default that gives every SM sub-partition a
  * warp of FP64 work.  `stream` is unused (may be NULL). */
 dmx_status dmx_autotune(dmx_model* m, int32_t B, int32_t grad, int32_t* lanes, void* stream);
-/* Records the lanes per environment for (model, B, forward/gradient); lanes in
- * {1, 2, 4, 8, 16, 32}.  DMX_ERR_INVALID otherwise. */
+/* Records the lanes per environment for (model, B, kind): kind 0 = forward
+ * rollout, 1 = taped rollout, 2 = reverse-mode adjoint kernel; lanes in
+ * {1, 2, 4, 8, 16, 32} (kind 2: {2, ..., 32}).  DMX_ERR_INVALID otherwise. */
 dmx_status dmx_set_lanes(dmx_model* m, int32_t B, int32_t grad, int32_t lanes);
 /* Model facts for tests and tools: invw[nbody] (host, may be NULL) receives the
  * translational inverse weight of every body at qpos0 (the A_hat of Sec. 2.1,
@@ -261,6 +277,17 @@ dmx_status dmx_rollout_static(dmx_model* m, const dmx_rollout_args* a, void* str
  * dmx_rollout_args (0 = default). */
 dmx_status dmx_eval_rhs(dmx_model* m, int32_t B, const double* q, const double* v, const double* u, int32_t cfd,
                         int32_t lanes, double* a, int32_t* info, void* stream);
+
+/* Vector-Jacobian product of the right-hand side (Eq. (EOM) with the
+ * constraint solve of Sec. 2.1; cfd = 1: of F~, Sec. 4) for B independent
+ * states: qbar [nq][B], vbar [nv][B], ubar [nu][B] (NULL iff nu == 0) receive
+ * (dF/dq)^T abar, (dF/dv)^T abar, (dF/du)^T abar for abar [nv][B] at
+ * q [nq][B], v [nv][B], u [nu][B] (device arrays).  The constraint solve is
+ * differentiated through its final active set.  status [B] = the right-hand
+ * side's DMX_ENV_* status.  lanes in {0 (default), 2, 4, 8, 16, 32}. */
+dmx_status dmx_eval_rhs_vjp(dmx_model* m, int32_t B, const double* q, const double* v, const double* u,
+                            const double* abar, int32_t cfd, int32_t lanes, double* qbar, double* vbar, double* ubar,
+                            int32_t* status, void* stream);
 
 const char* dmx_last_error(void);
 

@@ -28,6 +28,7 @@ c_i32, c_f64, c_p = ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
 DMX_OK, DMX_ERR_INVALID, DMX_ERR_OOM, DMX_ERR_CUDA, DMX_NOT_READY, DMX_ERR_TIMEOUT, DMX_ERR_UNIMPLEMENTED = range(7)
 ENV_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "nonfinite", 4: "solver_noconv", 5: "row_overflow"}
 FORMS = {"persistent": 0, "step": 1, "graph": 2}
+ADJOINT_MODES = {"reverse": 0, "tangent": 1}
 _JOINT = {"free": 0, "hinge": 1}
 _GEOM = {"sphere": 0, "capsule": 1, "box": 2}
 _ACT = {"motor": 0, "position": 1}
@@ -35,7 +36,8 @@ _ACT = {"motor": 0, "position": 1}
 # names of every entry point declared in include/dmx.h
 ABI_SYMBOLS = ("dmx_create_model", "dmx_destroy_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad",
                "dmx_tape_free", "dmx_tape_read", "dmx_autotune", "dmx_set_lanes", "dmx_model_info", "dmx_server_create", "dmx_submit", "dmx_poll",
-               "dmx_server_destroy", "dmx_eval_rhs", "dmx_rollout_static", "dmx_last_error")
+               "dmx_server_destroy", "dmx_eval_rhs", "dmx_rollout_static", "dmx_set_adjoint", "dmx_eval_rhs_vjp",
+               "dmx_last_error")
 
 
 class BodyDesc(ctypes.Structure):
@@ -98,7 +100,8 @@ def lib():
         L.dmx_server_destroy.argtypes = [c_p, c_f64]
         for name in ("dmx_create_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad", "dmx_autotune",
                      "dmx_server_create", "dmx_submit", "dmx_poll", "dmx_server_destroy", "dmx_model_info",
-                     "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read", "dmx_rollout_static"):
+                     "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read", "dmx_rollout_static", "dmx_set_adjoint",
+                     "dmx_eval_rhs_vjp"):
             getattr(L, name).restype = c_i32
         L.dmx_destroy_model.restype = None
         L.dmx_tape_free.restype = None
@@ -183,7 +186,12 @@ class Model:
         return out.value
 
     def set_lanes(self, B, lanes, grad=False):
+        """grad: False / 0 forward rollout, True / 1 taped rollout, 2 reverse-mode adjoint kernel."""
         _check(lib().dmx_set_lanes(self.h, int(B), int(grad), int(lanes)))
+
+    def set_adjoint(self, mode):
+        """Adjoint kernel of rollout_grad: "reverse" (default) or "tangent"."""
+        _check(lib().dmx_set_adjoint(self.h, ADJOINT_MODES[mode]))
 
 
 class Tape:
@@ -281,6 +289,25 @@ def rollout_grad(tape, xT_bar, xb_bar=None, cfd=False, stream=None):
     _check(lib().dmx_rollout_grad(m.h, tape.h, int(cfd), _ptr(xT_bar), _ptr(xb_bar), _ptr(x0_bar), _ptr(ctrl_bar),
                                   _stream_handle(stream)))
     return x0_bar, ctrl_bar
+
+
+def eval_rhs_vjp(model, q, v, abar, u=None, cfd=False, lanes=0, stream=None):
+    """Vector-Jacobian product of the right-hand side at B states: returns
+    (qbar [nq, B], vbar [nv, B], ubar [nu, B] or None, status [B] int32)."""
+    import torch
+    for t, nm in ((q, "q"), (v, "v"), (abar, "abar")):
+        _require_cuda(t, nm, torch.float64)
+    B = q.shape[1]
+    qbar = torch.empty((model.nq, B), dtype=torch.float64, device=q.device)
+    vbar = torch.empty((model.nv, B), dtype=torch.float64, device=q.device)
+    ubar = torch.empty((model.nu, B), dtype=torch.float64, device=q.device) if model.nu else None
+    status = torch.empty(B, dtype=torch.int32, device=q.device)
+    if model.nu:
+        _require_cuda(u, "u", torch.float64)
+    _check(lib().dmx_eval_rhs_vjp(model.h, B, _ptr(q), _ptr(v), _ptr(u) if model.nu else c_p(0), _ptr(abar), int(cfd),
+                                  int(lanes), _ptr(qbar), _ptr(vbar), _ptr(ubar), _ptr(status),
+                                  _stream_handle(stream)))
+    return qbar, vbar, ubar, status
 
 
 def eval_rhs(model, q, v, u=None, cfd=False, lanes=0, stream=None):

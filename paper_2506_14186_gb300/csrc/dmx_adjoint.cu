@@ -24,6 +24,14 @@
 #include "dmx_device.cuh"
 
 namespace dmx {
+template <int G> cudaError_t launch_adjoint_rev_g(const AdjParams&, int, int, size_t, cudaStream_t);
+template <int G> int occupancy_adjoint_rev_g(int, size_t);
+template <int G>
+cudaError_t launch_eval_rhs_vjp_g(const AdjParams&, const double*, const double*, const double*, const double*, double*,
+                                  double*, double*, int*, int, size_t, cudaStream_t);
+}  // namespace dmx
+
+namespace dmx {
 
 constexpr int ADJ_WARPS = 2;          // warps (environments) per block
 constexpr int ADJ_WS = 4096;          // per-lane workspace (derivative scalars)
@@ -205,5 +213,38 @@ cudaError_t launch_adjoint(const AdjParams& P, int blocks, cudaStream_t st) {
 int adjoint_warps_per_block() { return ADJ_WARPS; }
 int adjoint_workspace_limit() { return ADJ_WS; }
 int adjoint_int_limit() { return ADJ_WI; }
+
+cudaError_t launch_adjoint_rev(int G, const AdjParams& P, int blocks, int threads, size_t smem, cudaStream_t st) {
+  switch (G) {
+    case 2: return launch_adjoint_rev_g<2>(P, blocks, threads, smem, st);
+    case 4: return launch_adjoint_rev_g<4>(P, blocks, threads, smem, st);
+    case 8: return launch_adjoint_rev_g<8>(P, blocks, threads, smem, st);
+    case 16: return launch_adjoint_rev_g<16>(P, blocks, threads, smem, st);
+    case 32: return launch_adjoint_rev_g<32>(P, blocks, threads, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+int adjoint_rev_occupancy(int G, int threads, size_t smem) {
+  switch (G) {
+    case 2: return occupancy_adjoint_rev_g<2>(threads, smem);
+    case 4: return occupancy_adjoint_rev_g<4>(threads, smem);
+    case 8: return occupancy_adjoint_rev_g<8>(threads, smem);
+    case 16: return occupancy_adjoint_rev_g<16>(threads, smem);
+    case 32: return occupancy_adjoint_rev_g<32>(threads, smem);
+  }
+  return 0;
+}
+cudaError_t launch_eval_rhs_vjp(int G, const AdjParams& P, const double* q, const double* v, const double* u,
+                                const double* abar, double* qbar, double* vbar, double* ubar, int* status, int threads,
+                                size_t smem, cudaStream_t st) {
+  switch (G) {
+    case 2: return launch_eval_rhs_vjp_g<2>(P, q, v, u, abar, qbar, vbar, ubar, status, threads, smem, st);
+    case 4: return launch_eval_rhs_vjp_g<4>(P, q, v, u, abar, qbar, vbar, ubar, status, threads, smem, st);
+    case 8: return launch_eval_rhs_vjp_g<8>(P, q, v, u, abar, qbar, vbar, ubar, status, threads, smem, st);
+    case 16: return launch_eval_rhs_vjp_g<16>(P, q, v, u, abar, qbar, vbar, ubar, status, threads, smem, st);
+    case 32: return launch_eval_rhs_vjp_g<32>(P, q, v, u, abar, qbar, vbar, ubar, status, threads, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
 
 }  // namespace dmx

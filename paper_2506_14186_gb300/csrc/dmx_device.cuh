@@ -363,6 +363,37 @@ __device__ __forceinline__ double box_sdf_slope(const double* y0, const double* 
   return gr[0] * wv[0] + gr[1] * wv[1] + gr[2] * wv[2];
 }
 
+// Minimiser over the capsule axis s in [-Lh, Lh] of the box distance field
+// along y0 + s wv (box frame), by bisection on its slope (values only).
+__device__ __forceinline__ double capsule_box_s(const double* y0v, const double* wvv, double Lh, const double* h) {
+  if (box_sdf_slope(y0v, wvv, -Lh, h) >= 0) return -Lh;
+  if (box_sdf_slope(y0v, wvv, Lh, h) <= 0) return Lh;
+  double lo = -Lh, hi = Lh;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (box_sdf_slope(y0v, wvv, mid, h) < 0) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+// Curvature phi'' of the distance along the axis at an interior minimiser sv
+// outside the box, where the minimiser moves with the poses (implicit
+// function theorem: ds = -d(slope) / phi'').  Returns 0 where s is held
+// constant (an end of the axis, inside the box, or a flat direction).
+__device__ __forceinline__ double capsule_box_curv(const double* y0v, const double* wvv, double sv, double Lh,
+                                                   const double* h) {
+  double yv[3] = {y0v[0] + sv * wvv[0], y0v[1] + sv * wvv[1], y0v[2] + sv * wvv[2]}, gv[3];
+  const double phi = box_sdf(yv, h, gv);
+  bool outside = false;
+  for (int i = 0; i < 3; ++i) outside = outside || (fabs(yv[i]) - h[i] > 0);
+  if (!(outside && sv > -Lh && sv < Lh && phi > 0)) return 0.0;
+  const double gw = gv[0] * wvv[0] + gv[1] * wvv[1] + gv[2] * wvv[2];
+  double ww = 0;
+  for (int i = 0; i < 3; ++i) if (fabs(yv[i]) > h[i]) ww += wvv[i] * wvv[i];
+  const double phi2 = (ww - gw * gw) / phi;
+  return phi2 > 1e-12 ? phi2 : 0.0;
+}
+
 // Capsule (geom g1) against box (geom g2): minimum over the capsule axis of
 // the box distance field (convex along the axis; bisection on its slope, in
 // values).  In derivative scalars the minimiser s carries ds/dtheta from the
@@ -383,36 +414,15 @@ __device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1,
   matTvec3(R2, dc, y0);
   matTvec3(R2, u, wv);
   const double y0v[3] = {value(y0[0]), value(y0[1]), value(y0[2])}, wvv[3] = {value(wv[0]), value(wv[1]), value(wv[2])};
-  double sv;
-  if (box_sdf_slope(y0v, wvv, -Lh, h) >= 0) sv = -Lh;
-  else if (box_sdf_slope(y0v, wvv, Lh, h) <= 0) sv = Lh;
-  else {
-    double lo = -Lh, hi = Lh;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (box_sdf_slope(y0v, wvv, mid, h) < 0) lo = mid; else hi = mid;
-    }
-    sv = 0.5 * (lo + hi);
-  }
+  const double sv = capsule_box_s(y0v, wvv, Lh, h);
   T s = sv;
   if constexpr (!std::is_same<T, double>::value) {
-    // implicit-function tangent of the minimiser (outside the box, interior s)
-    double yv[3] = {y0v[0] + sv * wvv[0], y0v[1] + sv * wvv[1], y0v[2] + sv * wvv[2]}, gv[3];
-    const double phi = box_sdf(yv, h, gv);
-    bool outside = false;
-    for (int i = 0; i < 3; ++i) outside = outside || (fabs(yv[i]) - h[i] > 0);
-    if (outside && sv > -Lh && sv < Lh && phi > 0) {
-      const double gw = gv[0] * wvv[0] + gv[1] * wvv[1] + gv[2] * wvv[2];
-      double ww = 0;
-      for (int i = 0; i < 3; ++i) if (fabs(yv[i]) > h[i]) ww += wvv[i] * wvv[i];
-      const double phi2 = (ww - gw * gw) / phi;
-      if (phi2 > 1e-12) {
-        T yT[3] = {y0[0] + sv * wv[0], y0[1] + sv * wv[1], y0[2] + sv * wv[2]}, gT[3];
-        box_sdf(yT, h, gT);
-        const T slope = gT[0] * wv[0] + gT[1] * wv[1] + gT[2] * wv[2];
-        s = T(sv, -slope.d / phi2);
-      }
+    const double phi2 = capsule_box_curv(y0v, wvv, sv, Lh, h);
+    if (phi2 > 0) {
+      T yT[3] = {y0[0] + sv * wv[0], y0[1] + sv * wv[1], y0[2] + sv * wv[2]}, gT[3];
+      box_sdf(yT, h, gT);
+      const T slope = gT[0] * wv[0] + gT[1] * wv[1] + gT[2] * wv[2];
+      s = T(sv, -slope.d / phi2);
     }
   }
   T y[3] = {y0[0] + s * wv[0], y0[1] + s * wv[1], y0[2] + s * wv[2]}, gr[3], n[3];

@@ -95,4 +95,32 @@ DMX_HD inline Layout make_layout(const DevModel& m, int rcap) {
   return L;
 }
 
+// Offsets (in doubles) of one environment's adjoint workspace (reverse-mode
+// adjoint kernel): cotangents of the right-hand side's intermediates, then
+// the stage data and cotangents of one Dormand-Prince step.
+struct LayoutBar {
+  int R, p, cR, cp, S, F, Ib, Ic, V, A, Fb, slot, y, jy, cz, cj, q, v, u;   // right-hand side
+  int qn, vst, dq, dqb, Qs, kab, kvb, Qb, Vb, qnb, vnb, ub, xb;            // one step
+  int nd;                            // doubles per environment (padded to even)
+};
+constexpr int SLOTBAR = 24;          // per slot: pose cotangents of its two geoms (R 9 + p 3 each)
+
+DMX_HD inline LayoutBar make_bar_layout(const DevModel& m, int rcap) {
+  LayoutBar B{};
+  int o = 0;
+  const int nq = m.nq, nv = m.nv, nb = m.nbody, ns = m.nslot > 0 ? m.nslot : 1, nu = m.nu > 0 ? m.nu : 1;
+  auto take = [&](int n) { int r = o; o += n; return r; };
+  B.R = take(9 * nb); B.p = take(3 * nb); B.cR = take(9 * nb); B.cp = take(3 * nb);
+  B.S = take(6 * nv); B.F = take(6 * nv); B.Ib = take(10 * nb); B.Ic = take(10 * nb);
+  B.V = take(6 * nb); B.A = take(6 * nb); B.Fb = take(6 * nb);
+  B.slot = take(SLOTBAR * ns);
+  B.y = take(nv); B.jy = take(rcap); B.cz = take(rcap); B.cj = take(rcap);
+  B.q = take(nq); B.v = take(nv); B.u = take(nu);
+  B.qn = take(nq); B.vst = take(6 * nv); B.dq = take(nv); B.dqb = take(nv); B.Qs = take(nq);
+  B.kab = take(6 * nv); B.kvb = take(6 * nv); B.Qb = take(nq); B.Vb = take(nv);
+  B.qnb = take(nq); B.vnb = take(nv); B.ub = take(nu); B.xb = take(nq + nv);
+  B.nd = (o + 1) & ~1;
+  return B;
+}
+
 }  // namespace dmx

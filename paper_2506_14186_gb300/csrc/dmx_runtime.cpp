@@ -468,9 +468,47 @@ extern "C" dmx_status dmx_autotune(dmx_model* m, int32_t B, int32_t grad, int32_
 }
 
 extern "C" dmx_status dmx_set_lanes(dmx_model* m, int32_t B, int32_t grad, int32_t lanes) {
-  if (!m || !valid_lanes(lanes)) return dmx_fail(DMX_ERR_INVALID, "bad argument");
+  if (!m || !valid_lanes(lanes) || grad < 0 || grad > 2 || (grad == 2 && lanes == 1))
+    return dmx_fail(DMX_ERR_INVALID, "bad argument");
   std::lock_guard<std::mutex> lk(m->mu);
   m->tuned[{B, grad}] = lanes;
+  return DMX_OK;
+}
+
+static bool valid_adj_lanes(int G) { return G == 2 || G == 4 || G == 8 || G == 16 || G == 32; }
+
+// Threads and shared memory of the reverse-mode adjoint kernel for G lanes.
+static bool adj_launch_config(const dmx_model* m, const dmx::LayoutBar& LB, int G, int* threads, size_t* smem) {
+  const int per = (m->L.nd + LB.nd) * 8 + m->L.ni * 4;
+  for (int t = 256; t >= 32; t >>= 1) {
+    if (t < G) break;
+    const size_t s = (size_t)(t / G) * per;
+    if ((int)s <= m->smem_max - 2048) { *threads = t; *smem = s; return true; }
+  }
+  return false;
+}
+
+// Lanes of the reverse-mode adjoint: the recorded choice, else enough lanes
+// to give every SM sub-partition a warp (at least 2), within shared memory.
+static int adjoint_lanes(dmx_model* m, int B) {
+  {
+    std::lock_guard<std::mutex> lk(m->mu);
+    auto it = m->tuned.find({B, 2});
+    if (it != m->tuned.end() && valid_adj_lanes(it->second)) return it->second;
+  }
+  const dmx::LayoutBar LB = dmx::make_bar_layout(m->host, m->rcap);
+  const int want = 4 * 32 * m->nsm;
+  int G = 2;
+  while (G < 32 && (long long)B * G < want) G <<= 1;
+  int t; size_t s;
+  while (G < 32 && !adj_launch_config(m, LB, G, &t, &s)) G <<= 1;
+  return G;
+}
+
+extern "C" dmx_status dmx_set_adjoint(dmx_model* m, int32_t mode) {
+  if (!m || (mode != DMX_ADJ_REVERSE && mode != DMX_ADJ_TANGENT)) return dmx_fail(DMX_ERR_INVALID, "bad argument");
+  std::lock_guard<std::mutex> lk(m->mu);
+  m->adj_mode = mode;
   return DMX_OK;
 }
 
@@ -481,25 +519,69 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
   if (t->B == 0) return DMX_OK;
   if (!xT_bar || !x0_bar) return dmx_fail(DMX_ERR_INVALID, "xT_bar and x0_bar are required");
   if (m->host.nu > 0 && !ctrl_bar) return dmx_fail(DMX_ERR_INVALID, "ctrl_bar is required when the model has actuators");
-  if (m->L.nd > dmx::adjoint_workspace_limit() || m->L.ni > dmx::adjoint_int_limit())
-    return dmx_fail(DMX_ERR_INVALID, "model workspace exceeds the adjoint kernel's per-lane limit");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int nx = t->nx;
-  const int wpb = dmx::adjoint_warps_per_block();
-  int blocks = (t->B + wpb - 1) / wpb;
-  blocks = std::min(blocks, m->nsm * 8);
-  const size_t seg_bytes = sizeof(double) * (size_t)blocks * wpb * t->K * (nx + 1);
-  void* scratch = nullptr;
-  CK(cudaMallocAsync(&scratch, seg_bytes + 256, st));
+  int mode;
+  {
+    std::lock_guard<std::mutex> lk(m->mu);
+    mode = m->adj_mode;
+  }
   dmx::AdjParams P{};
   P.model = m->dev; P.L = m->L; P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd;
   P.ckpt = t->ckpt; P.hlog = t->hlog; P.tape_n = t->n; P.ctrl = t->ctrl; P.T = t->T;
   P.xT_bar = xT_bar; P.xb_bar = xb_bar; P.x0_bar = x0_bar; P.ctrl_bar = m->host.nu ? ctrl_bar : nullptr;
+  if (mode == DMX_ADJ_TANGENT) {
+    if (m->L.nd > dmx::adjoint_workspace_limit() || m->L.ni > dmx::adjoint_int_limit())
+      return dmx_fail(DMX_ERR_INVALID, "model workspace exceeds the tangent adjoint kernel's per-lane limit");
+    const int wpb = dmx::adjoint_warps_per_block();
+    int blocks = (t->B + wpb - 1) / wpb;
+    blocks = std::min(blocks, m->nsm * 8);
+    const size_t seg_bytes = sizeof(double) * (size_t)blocks * wpb * t->K * (nx + 1);
+    void* scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, seg_bytes + 256, st));
+    P.segbuf = static_cast<double*>(scratch);
+    P.queue = reinterpret_cast<int*>(static_cast<char*>(scratch) + seg_bytes);
+    CK(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
+    CK(dmx::launch_adjoint(P, blocks, st));
+    CK(cudaFreeAsync(scratch, st));
+    return DMX_OK;
+  }
+  const int G = adjoint_lanes(m, t->B);
+  P.LB = dmx::make_bar_layout(m->host, m->rcap);
+  int threads; size_t smem;
+  if (!adj_launch_config(m, P.LB, G, &threads, &smem))
+    return dmx_fail(DMX_ERR_INVALID, "adjoint workspace of " + std::to_string(G) + " lanes/env does not fit shared memory");
+  const int gpb = threads / G;
+  const int occ = std::max(1, dmx::adjoint_rev_occupancy(G, threads, smem));
+  int blocks = (t->B + gpb - 1) / gpb;
+  blocks = std::min(blocks, m->nsm * occ);
+  const int RW = m->host.nq + 6 * m->host.nv + 1;
+  const size_t seg_bytes = sizeof(double) * (size_t)blocks * gpb * t->K * RW;
+  void* scratch = nullptr;
+  CK(cudaMallocAsync(&scratch, seg_bytes + 256, st));
   P.segbuf = static_cast<double*>(scratch);
   P.queue = reinterpret_cast<int*>(static_cast<char*>(scratch) + seg_bytes);
   CK(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
-  CK(dmx::launch_adjoint(P, blocks, st));
+  CK(dmx::launch_adjoint_rev(G, P, blocks, threads, smem, st));
   CK(cudaFreeAsync(scratch, st));
+  return DMX_OK;
+}
+
+extern "C" dmx_status dmx_eval_rhs_vjp(dmx_model* m, int32_t B, const double* q, const double* v, const double* u,
+                                       const double* abar, int32_t cfd, int32_t lanes, double* qbar, double* vbar,
+                                       double* ubar, int32_t* status, void* stream) {
+  if (!m || B < 0) return dmx_fail(DMX_ERR_INVALID, "bad argument");
+  if (B == 0) return DMX_OK;
+  const bool act = m->host.nu > 0;
+  if (!q || !v || !abar || !qbar || !vbar || !status || (act && (!u || !ubar))) return dmx_fail(DMX_ERR_INVALID, "null array");
+  const int G = lanes ? lanes : adjoint_lanes(m, B);
+  if (!valid_adj_lanes(G)) return dmx_fail(DMX_ERR_INVALID, "lanes must be 0, 2, 4, 8, 16 or 32");
+  dmx::AdjParams P{};
+  P.model = m->dev; P.L = m->L; P.LB = dmx::make_bar_layout(m->host, m->rcap); P.B = B; P.cfd = cfd;
+  int threads; size_t smem;
+  if (!adj_launch_config(m, P.LB, G, &threads, &smem)) return dmx_fail(DMX_ERR_INVALID, "workspace does not fit");
+  CK(dmx::launch_eval_rhs_vjp(G, P, q, v, act ? u : q, abar, qbar, vbar, act ? ubar : nullptr, status, threads, smem,
+                              static_cast<cudaStream_t>(stream)));
   return DMX_OK;
 }
 

@@ -25,7 +25,8 @@ struct dmx_model {
   int device = 0, nsm = 0, smem_max = 0, rcap = 0;
   double invw[dmx::MAXB];
   std::mutex mu;
-  std::map<std::pair<int, int>, int> tuned;   // (B, grad) -> lanes per environment
+  std::map<std::pair<int, int>, int> tuned;   // (B, kind) -> lanes per environment
+  int adj_mode = DMX_ADJ_REVERSE;             // adjoint kernel of dmx_rollout_grad
 };
 
 struct dmx_tape {

@@ -42,8 +42,10 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def gpu_grad(dmx, model, inp, xT_bar, xb_bar=None, cfd=False, K=32):
-    """Taped GPU rollout + adjoint.  Arrays env-major in and out."""
+def gpu_grad(dmx, model, inp, xT_bar, xb_bar=None, cfd=False, K=32, mode="reverse"):
+    """Taped GPU rollout + adjoint (reverse-mode or tangent kernel).  Arrays
+    env-major in and out."""
+    model.set_adjoint(mode)
     ctrl = None if inp["ctrl"] is None else _dev(np.transpose(inp["ctrl"], (1, 2, 0)))
     out = dmx.rollout(model, _dev(inp["x0"].T), _dev(inp["T"]), ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"],
                       atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"], K=K, tape=True)
@@ -70,8 +72,12 @@ def assert_grad(g, o, key="x0_bar"):
     return err
 
 
+MODES = ["reverse", "tangent"]
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("cfd", [False, True])
-def test_ball_gradient(dmx, orc_mod, cfd):
+def test_ball_gradient(dmx, orc_mod, cfd, mode):
     """Bouncing balls (full batch, T = 1 s): gradient of the final height and
     velocity w.r.t. the whole initial state; with CFD parameters of App. D.3."""
     sc = W.ball_scene(**CFD_OPT) if cfd else W.ball_scene()
@@ -79,26 +85,28 @@ def test_ball_gradient(dmx, orc_mod, cfd):
     rng = np.random.default_rng(0)
     xT_bar = rng.normal(size=(16, 13))
     m = dmx.Model(sc)
-    g = gpu_grad(dmx, m, inp, xT_bar, cfd=cfd)
+    g = gpu_grad(dmx, m, inp, xT_bar, cfd=cfd, mode=mode)
     o = oracle_grad(orc_mod, sc, inp, g, xT_bar, cfd=cfd)
     assert_grad(g, o)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("cfd", [False, True])
 @pytest.mark.parametrize("K", [1, 7, 32])
-def test_box_gradient(dmx, orc_mod, cfd, K):
+def test_box_gradient(dmx, orc_mod, cfd, K, mode):
     sc = W.box_scene(**CFD_ONLY) if cfd else W.box_scene()
     inp = W.box_push_inputs(24, seed=5, T=0.3)
     rng = np.random.default_rng(1)
     xT_bar = rng.normal(size=(24, 13))
     m = dmx.Model(sc)
-    g = gpu_grad(dmx, m, inp, xT_bar, cfd=cfd, K=K)
+    g = gpu_grad(dmx, m, inp, xT_bar, cfd=cfd, K=K, mode=mode)
     assert np.all(g["status"] == 0)
     assert_grad(g, oracle_grad(orc_mod, sc, inp, g, xT_bar, cfd=cfd))
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("cfd", [False, True])
-def test_chain_control_gradient_with_boundary_cotangents(dmx, orc_mod, cfd):
+def test_chain_control_gradient_with_boundary_cotangents(dmx, orc_mod, cfd, mode):
     """Arm + cube: loss on the cube's final position and on every
     interval-boundary state; gradient w.r.t. x0 and every control."""
     sc = W.chain_cube_scene(**CFD_OPT) if cfd else W.chain_cube_scene()
@@ -108,22 +116,23 @@ def test_chain_control_gradient_with_boundary_cotangents(dmx, orc_mod, cfd):
     xT_bar = rng.normal(size=(8, nx))
     xb_bar = rng.normal(size=(8, 7, nx))
     m = dmx.Model(sc)
-    g = gpu_grad(dmx, m, inp, xT_bar, xb_bar=xb_bar, cfd=cfd, K=5)
+    g = gpu_grad(dmx, m, inp, xT_bar, xb_bar=xb_bar, cfd=cfd, K=5, mode=mode)
     o = oracle_grad(orc_mod, sc, inp, g, xT_bar, xb_bar=xb_bar, cfd=cfd)
     assert_grad(g, o)
     assert_grad(g, o, "ctrl_bar")
 
 
-def test_quadruped_gradient_two_direction_passes(dmx, orc_mod):
-    """19 + 18 coordinates and 12 servo targets: 49 input directions, two
-    32-lane passes per step."""
+@pytest.mark.parametrize("mode", MODES)
+def test_quadruped_gradient(dmx, orc_mod, mode):
+    """19 + 18 coordinates and 12 servo targets: 49 input directions (two
+    32-lane passes per step for the tangent kernel)."""
     sc = W.quadruped_scene()
     inp = W.quadruped_inputs(6)
     inp["T"] = np.minimum(inp["T"], 0.2)
     rng = np.random.default_rng(3)
     xT_bar = np.zeros((6, 37)); xT_bar[:, 0:3] = rng.normal(size=(6, 3))
     m = dmx.Model(sc)
-    g = gpu_grad(dmx, m, inp, xT_bar, K=16)
+    g = gpu_grad(dmx, m, inp, xT_bar, K=16, mode=mode)
     o = oracle_grad(orc_mod, sc, inp, g, xT_bar)
     assert_grad(g, o)
     assert_grad(g, o, "ctrl_bar")
@@ -185,3 +194,66 @@ def test_autograd_function(dmx):
     xb_bar = torch.zeros_like(out["xb"]); xb_bar[:, 7:10] = 0.2 * out["xb"][:, 7:10]
     gx, gu = dmx.rollout_grad(out["tape"], xT_bar, xb_bar)
     assert torch.allclose(gx, x0.grad, rtol=1e-12, atol=0) and torch.allclose(gu, ctrl.grad, rtol=1e-12, atol=0)
+
+
+TOL_VJP = 1e-10
+
+
+@pytest.mark.parametrize("cfd", [False, True])
+@pytest.mark.parametrize("name", ["ball", "box", "chain_cube", "quadruped"])
+def test_rhs_vjp_matches_oracle_jacobian(dmx, orc_mod, name, cfd):
+    """Right-hand-side VJP (dmx_eval_rhs_vjp) against the transposed Jacobian
+    of the oracle's right-hand side (its derivative scalars) at states near
+    contact (angular velocities included), for several lane counts."""
+    from tests.test_gpu_rollout import SEEDS, _random_states
+    sc = W.SCENES[name](**CFD_OPT) if cfd else W.SCENES[name]()
+    B = 48
+    om = orc_mod.OracleModel(sc)
+    q, v, u = _random_states(sc, B, SEEDS[name] + 100, om)
+    rng = np.random.default_rng(SEEDS[name])
+    gm = dmx.Model(sc)
+    abar = rng.normal(size=(B, gm.nv))
+    ref_q, ref_v, ref_u = [], [], []
+    for e in range(B):
+        Jq, Jv, Ju = om.rhs_jacobian(q[e], v[e], u[e], cfd=cfd)
+        ref_q.append(Jq.T @ abar[e]); ref_v.append(Jv.T @ abar[e]); ref_u.append(Ju.T @ abar[e])
+    ref = [np.concatenate([ref_q[e], ref_v[e], ref_u[e]]) for e in range(B)]
+    for lanes in ((8, 16, 32) if name in ("chain_cube", "quadruped") else (2, 8, 32)):   # large workspaces need >= 8 lanes
+        qb, vb, ub, st = dmx.eval_rhs_vjp(gm, _dev(q.T), _dev(v.T), _dev(abar.T),
+                                          u=_dev(u[:, :gm.nu].T) if gm.nu else None, cfd=cfd, lanes=lanes)
+        assert np.all(st.cpu().numpy() == 0)
+        qb = qb.cpu().numpy().T; vb = vb.cpu().numpy().T
+        ub = ub.cpu().numpy().T if gm.nu else np.zeros((B, 0))
+        # one scale per state: the largest cotangent component, at least |abar|_inf (a state
+        # out of contact has a Jacobian that vanishes up to rounding on both sides)
+        err = 0.0
+        for e in range(B):
+            got = np.concatenate([qb[e], vb[e], ub[e]])
+            scale = max(np.abs(ref[e]).max(), np.abs(abar[e]).max())
+            err = max(err, np.abs(got - ref[e]).max() / scale)
+        assert err < TOL_VJP, f"lanes {lanes}: {err:.3e}"
+
+
+@pytest.mark.parametrize("name", ["box", "chain_cube"])
+def test_reverse_kernel_equals_tangent_kernel(dmx, name):
+    """The two adjoint kernels compute the same derivative on the same tape:
+    they differ only in rounding (a product of a few hundred step Jacobians
+    of a stiff contact map; measured 1e-11 for the arm, 1e-8 for the box),
+    checked at a tenth of the gradient tolerance."""
+    import torch
+    sc = W.SCENES[name]()
+    inp = W.box_push_inputs(64, seed=9, T=0.2) if name == "box" else W.chain_inputs(16, T=0.2, NI=4)
+    m = dmx.Model(sc)
+    ctrl = None if inp["ctrl"] is None else _dev(np.transpose(inp["ctrl"], (1, 2, 0)))
+    out = dmx.rollout(m, _dev(inp["x0"].T), _dev(inp["T"]), ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"],
+                      atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"], K=16, tape=True)
+    xT_bar = torch.randn((m.nx, len(inp["T"])), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    res = {}
+    for mode in MODES:
+        m.set_adjoint(mode)
+        res[mode] = dmx.rollout_grad(out["tape"], xT_bar)
+    for k in range(2 if m.nu else 1):
+        a = res["reverse"][k].cpu().numpy().reshape(-1, len(inp["T"])).T
+        b = res["tangent"][k].cpu().numpy().reshape(-1, len(inp["T"])).T
+        err = max(rel_err(a[e], b[e]) for e in range(len(a)))
+        assert err < 0.1 * TOL, err
