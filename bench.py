@@ -292,11 +292,13 @@ def run_ours(args):
     return result
 
 
-def grad_leg(dmx, dev, B=256):
-    """Forward (taped) + discrete adjoint of the arm-pushes-cube workload (7
-    hinges + free cube, 50 torque intervals over 2 s, K = 32), loss = squared
-    cube-to-goal distance, on a bounded sample of the 16384 environments."""
+def grad_leg(dmx, dev, B=2048):
+    """Forward (taped) + discrete adjoint (reverse-mode kernel, autotuned lanes)
+    of the arm-pushes-cube workload (7 hinges + free cube, 50 torque intervals
+    over 2 s, K = 32), loss = squared cube-to-goal distance, on a bounded
+    sample (the first B) of the 16384 environments."""
     import torch
+    from paper_2506_14186_gb300 import autotune
     from paper_2506_14186_gb300 import workloads as W
     sc = W.chain_cube_scene()
     inp = W.chain_inputs(16384)
@@ -306,15 +308,9 @@ def grad_leg(dmx, dev, B=256):
     T = torch.tensor(inp["T"][:B], device=dev)
     goal = torch.tensor(W.chain_goal(), device=dev)[:, None]
     st = torch.cuda.current_stream()
-
-    def run():
-        out = dmx.rollout(m, x0, T, ctrl=ctrl, NI=50, K=32, tape=True)
-        xT_bar = torch.zeros_like(out["xT"])
-        xT_bar[7:10] = 2 * (out["xT"][7:10] - goal)
-        gx, gu = dmx.rollout_grad(out["tape"], xT_bar)
-        return out, gu
-
-    run()
+    fwd_lanes, _ = autotune.tune_forward(m, x0, torch.clamp(T, max=0.2), ctrl=ctrl, NI=50, candidates=(8, 16, 32))
+    adj_lanes, adj_ms = autotune.tune_adjoint(m, x0, T, ctrl=ctrl, NI=50, K=32)
+    m.set_lanes(B, fwd_lanes)
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record(st)
@@ -329,7 +325,9 @@ def grad_leg(dmx, dev, B=256):
     steps = int(out["nsteps"].sum().item())
     return {"workload": "chain_cube (7 hinges + cube, NI=50, T=2 s, K=32)", "sample_envs": B,
             "grad_rollouts_per_s": B / t_all, "env_steps_per_s": steps / t_all, "forward_s": t_f,
-            "adjoint_s": t_all - t_f, "env_steps": steps, "finite": bool(torch.isfinite(gu).all().item())}
+            "adjoint_s": t_all - t_f, "env_steps": steps, "adjoint_kernel": "reverse",
+            "lanes": {"forward": fwd_lanes, "adjoint": adj_lanes, "adjoint_tuning_ms": adj_ms},
+            "finite": bool(torch.isfinite(gu).all().item())}
 
 
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
