@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--lanes", type=int, default=0, help="lanes per environment (0 = autotuned)")
     p.add_argument("--no-extras", action="store_true", help="skip the plain-form and CPU-baseline legs")
     p.add_argument("--serving", action="store_true", help="served-request latency benchmark instead of the rollout bench")
+    p.add_argument("--grad-only", action="store_true", help="only the fwd+adjoint leg (one JSON line)")
+    p.add_argument("--grad-envs", type=int, default=2048, help="environments of the fwd+adjoint leg")
+    p.add_argument("--adj-lanes", type=int, default=0, help="lanes per environment of the adjoint (0 = autotuned)")
     p.add_argument("--requests", type=int, default=40)
     p.add_argument("--warmup-requests", type=int, default=5)
     p.add_argument("--rate", type=float, default=200.0, help="Poisson arrival rate (requests/s)")
@@ -147,6 +150,12 @@ def reduce_sum(x, world, device=None):
     return float(t.item())
 
 
+# sources of the forward rollout kernel (the ncu record is valid while they are unchanged)
+FORWARD_SOURCES = ("dmx_device.cuh", "dmx_dual.cuh", "dmx_kernels.cuh", "dmx_kernels.h", "dmx_model.h",
+                   "dmx_inst_g1.cu", "dmx_inst_g2.cu", "dmx_inst_g4.cu", "dmx_inst_g8.cu", "dmx_inst_g16.cu",
+                   "dmx_inst_g32.cu")
+
+
 def _traffic(kernel_lanes):
     """DRAM bytes per launch of the persistent kernel from the committed ncu
     summary, if it was taken on the current kernel sources (else None)."""
@@ -155,11 +164,9 @@ def _traffic(kernel_lanes):
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    csrc = os.path.join(ROOT, "paper_2506_14186_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in FORWARD_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2506_14186_gb300", "csrc", f), "rb").read())
     if rec.get("source_sha256") != h.hexdigest() or rec.get("lanes") != kernel_lanes:
         return None
     return rec.get("dram_bytes_per_launch")
@@ -283,7 +290,7 @@ def run_ours(args):
                 t = e0.elapsed_time(e1)
                 extra[form] = {"value": int(out["nsteps"].sum().item()) / (t * 1e-3), "ms_per_step": t}
             result["plain_forms"] = extra
-            result["fwd_adjoint"] = grad_leg(dmx, dev)
+            result["fwd_adjoint"] = grad_leg(dmx, dev, B=args.grad_envs, adj_lanes=args.adj_lanes)
             rate, sample, cores, _ = oracle_rate(inp)
             result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     if world > 1:
@@ -292,7 +299,7 @@ def run_ours(args):
     return result
 
 
-def grad_leg(dmx, dev, B=2048):
+def grad_leg(dmx, dev, B=2048, adj_lanes=0):
     """Forward (taped) + discrete adjoint (reverse-mode kernel, autotuned lanes)
     of the arm-pushes-cube workload (7 hinges + free cube, 50 torque intervals
     over 2 s, K = 32), loss = squared cube-to-goal distance, on a bounded
@@ -309,7 +316,11 @@ def grad_leg(dmx, dev, B=2048):
     goal = torch.tensor(W.chain_goal(), device=dev)[:, None]
     st = torch.cuda.current_stream()
     fwd_lanes, _ = autotune.tune_forward(m, x0, torch.clamp(T, max=0.2), ctrl=ctrl, NI=50, candidates=(8, 16, 32))
-    adj_lanes, adj_ms = autotune.tune_adjoint(m, x0, T, ctrl=ctrl, NI=50, K=32)
+    if adj_lanes:
+        m.set_lanes(B, adj_lanes, grad=2)
+        adj_ms = None
+    else:
+        adj_lanes, adj_ms = autotune.tune_adjoint(m, x0, T, ctrl=ctrl, NI=50, K=32)
     m.set_lanes(B, fwd_lanes)
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -467,6 +478,14 @@ def main():
     args = parse()
     if args.serving:
         print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.grad_only:
+        import torch
+        import paper_2506_14186_gb300 as dmx
+        from paper_2506_14186_gb300 import _build
+        _build.build()
+        print(json.dumps(grad_leg(dmx, torch.device("cuda", 0), B=args.grad_envs, adj_lanes=args.adj_lanes)),
+              flush=True)
         return
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:

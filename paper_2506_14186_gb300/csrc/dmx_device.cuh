@@ -62,6 +62,21 @@ struct Grp {
   __device__ double bcast(double x, int src) const { return G == 1 ? x : __shfl_sync(mask, x, src, G); }
 };
 
+// (row, column) of the t-th entry of a lower triangle enumerated row by row
+// ((0,0), (1,0), (1,1), (2,0), ...): the same for every matrix size.
+struct TriTab {
+  unsigned char e[MAXV * (MAXV + 1) / 2][2];
+};
+__host__ __device__ constexpr TriTab make_tri() {
+  TriTab t{};
+  int k = 0;
+  for (int i = 0; i < MAXV; ++i)
+    for (int j = 0; j <= i; ++j) { t.e[k][0] = (unsigned char)i; t.e[k][1] = (unsigned char)j; ++k; }
+  return t;
+}
+static __constant__ TriTab c_tri_tab = make_tri();
+#define c_tri c_tri_tab.e
+
 // ------------------------------------------------------------------ small helpers
 // Templated on the scalar types so that the same code runs on doubles (the
 // forward path) and on derivative scalars (the adjoint); model constants
@@ -138,6 +153,35 @@ __device__ __forceinline__ void crf6(const T* a, const T* b, T* c) {
   cross3(a, b + 3, c + 3);
 }
 
+// Single components (e = 0..5) of the spatial products above, so that the
+// six components of a body's vector can go to six lanes.
+__device__ __forceinline__ int nxt3(int k) { return k == 2 ? 0 : k + 1; }
+__device__ __forceinline__ int prv3(int k) { return k == 0 ? 2 : k - 1; }
+template <class T>
+__device__ __forceinline__ T crm_comp(const T* a, const T* b, int e) {   // (a x b)_e, motion
+  const int k = e < 3 ? e : e - 3, k1 = nxt3(k), k2 = prv3(k);
+  const T* x = e < 3 ? b : b + 3;
+  T r = a[k1] * x[k2] - a[k2] * x[k1];                                // (w x w2) or (w x v2)
+  if (e >= 3) r += a[3 + k1] * b[k2] - a[3 + k2] * b[k1];             // + v x w2
+  return r;
+}
+template <class T>
+__device__ __forceinline__ T crf_comp(const T* a, const T* b, int e) {   // (a x* b)_e, force
+  const int k = e < 3 ? e : e - 3, k1 = nxt3(k), k2 = prv3(k);
+  const T* x = e < 3 ? b : b + 3;
+  T r = a[k1] * x[k2] - a[k2] * x[k1];                                // (w x n) or (w x f)
+  if (e < 3) r += a[3 + k1] * b[3 + k2] - a[3 + k2] * b[3 + k1];      // + v x f
+  return r;
+}
+template <class T>
+__device__ __forceinline__ T inertia_comp(const T* I, const T* x, int e) {   // (I x)_e, inertia_apply
+  const int k = e < 3 ? e : e - 3, k1 = nxt3(k), k2 = prv3(k);
+  if (e < 3)   // I_O row k (entry (k, j): 4 + k on the diagonal, else 6 + k + j) . w + h x v
+    return I[k == 0 ? 4 : 6 + k] * x[0] + I[k == 1 ? 5 : 7 + k] * x[1] + I[k == 2 ? 6 : 8 + k] * x[2] +
+           (I[1 + k1] * x[3 + k2] - I[1 + k2] * x[3 + k1]);
+  return I[0] * x[3 + k] - (I[1 + k1] * x[k2] - I[1 + k2] * x[k1]);   // m v - h x w
+}
+
 // ------------------------------------------------------------------ workspace view
 template <class T>
 struct WsT {
@@ -149,78 +193,98 @@ struct WsT {
 using Ws = WsT<double>;
 
 // Kinematics: body poses, COMs, dof motion vectors, body spatial inertias, geom poses.
+// The per-body work runs for all bodies at once (local joint transforms, then
+// COMs, inertias and motion vectors from the world poses); only the
+// composition of the poses along the tree is sequential over the tree levels
+// (one 3x3 product and one 3-vector per body and level).
 template <int G, class T>
 __device__ void kinematics(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* q) {
   const Layout& L = *w.L;
   T* R = w.at(L.R); T* P = w.at(L.p); T* C = w.at(L.com);
   T* S = w.at(L.sd); T* Ib = w.at(L.Ib);
-  for (int lev = 0; lev < m.nlevel; ++lev) {
+  // local transforms: free joint = world pose; hinge = rotation in the parent frame
+  for (int b = g.lane; b < m.nbody; b += G) {
+    T* Rb = R + 9 * b; T* pb = P + 3 * b;
+    if (m.b_jtype[b] == JNT_FREE) {
+      const T* x = q + m.b_qadr[b];
+      pb[0] = x[0]; pb[1] = x[1]; pb[2] = x[2];
+      quat_to_mat(x + 3, Rb);
+    } else {
+      T sn, cs;
+      sincos(q[m.b_qadr[b]], &sn, &cs);
+      const double* a = m.b_axis[b];
+      const T c1 = 1.0 - cs;
+      // Rodrigues: I + sin K + (1 - cos) K^2, K = [a]x
+      T Rj[9];
+      Rj[0] = cs + c1 * a[0] * a[0];           Rj[1] = c1 * a[0] * a[1] - sn * a[2]; Rj[2] = c1 * a[0] * a[2] + sn * a[1];
+      Rj[3] = c1 * a[0] * a[1] + sn * a[2];    Rj[4] = cs + c1 * a[1] * a[1];        Rj[5] = c1 * a[1] * a[2] - sn * a[0];
+      Rj[6] = c1 * a[0] * a[2] - sn * a[1];    Rj[7] = c1 * a[1] * a[2] + sn * a[0]; Rj[8] = cs + c1 * a[2] * a[2];
+      matmul3(m.b_Roff[b], Rj, Rb);
+      pb[0] = m.b_pos[b][0]; pb[1] = m.b_pos[b][1]; pb[2] = m.b_pos[b][2];
+    }
+  }
+  g.sync();
+  // world poses: R = R_parent R_local, p = p_parent + R_parent b_pos
+  for (int lev = 1; lev < m.nlevel; ++lev) {
     for (int k = m.level_start[lev] + g.lane; k < m.level_start[lev + 1]; k += G) {
       const int b = m.level_list[k];
+      const int par = m.b_parent[b];
+      if (par < 0 || m.b_jtype[b] == JNT_FREE) continue;
       T* Rb = R + 9 * b; T* pb = P + 3 * b;
-      if (m.b_jtype[b] == JNT_FREE) {
-        const T* x = q + m.b_qadr[b];
-        pb[0] = x[0]; pb[1] = x[1]; pb[2] = x[2];
-        quat_to_mat(x + 3, Rb);
-      } else {
-        const int par = m.b_parent[b];
-        T Rp[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0}, pp[3] = {0.0, 0.0, 0.0};
-        if (par >= 0) {
-          for (int i = 0; i < 9; ++i) Rp[i] = R[9 * par + i];
-          pp[0] = P[3 * par]; pp[1] = P[3 * par + 1]; pp[2] = P[3 * par + 2];
-        }
-        T t[3];
-        matvec3(Rp, m.b_pos[b], t);
-        pb[0] = pp[0] + t[0]; pb[1] = pp[1] + t[1]; pb[2] = pp[2] + t[2];
-        T Ro[9], Rj[9];
-        matmul3(Rp, m.b_Roff[b], Ro);
-        T sn, cs;
-        sincos(q[m.b_qadr[b]], &sn, &cs);
-        const double* a = m.b_axis[b];
-        const T c1 = 1.0 - cs;
-        // Rodrigues: I + sin K + (1 - cos) K^2, K = [a]x
-        Rj[0] = cs + c1 * a[0] * a[0];           Rj[1] = c1 * a[0] * a[1] - sn * a[2]; Rj[2] = c1 * a[0] * a[2] + sn * a[1];
-        Rj[3] = c1 * a[0] * a[1] + sn * a[2];    Rj[4] = cs + c1 * a[1] * a[1];        Rj[5] = c1 * a[1] * a[2] - sn * a[0];
-        Rj[6] = c1 * a[0] * a[2] - sn * a[1];    Rj[7] = c1 * a[1] * a[2] + sn * a[0]; Rj[8] = cs + c1 * a[2] * a[2];
-        matmul3(Ro, Rj, Rb);
-      }
-      // COM and spatial inertia about the world origin
-      T c[3];
-      matvec3(Rb, m.b_com[b], c);
-      c[0] += pb[0]; c[1] += pb[1]; c[2] += pb[2];
-      C[3 * b] = c[0]; C[3 * b + 1] = c[1]; C[3 * b + 2] = c[2];
-      const double ms = m.b_mass[b];
-      const double* In = m.b_inertia[b];
-      T* I10 = Ib + 10 * b;
-      const T cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-      I10[0] = ms; I10[1] = ms * c[0]; I10[2] = ms * c[1]; I10[3] = ms * c[2];
-      // R diag(I) R^T + m (|c|^2 1 - c c^T)
-      const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-      for (int e = 0; e < 6; ++e) {
-        const int i = ii[e], j = jj[e];
-        T v = Rb[3 * i] * Rb[3 * j] * In[0] + Rb[3 * i + 1] * Rb[3 * j + 1] * In[1] + Rb[3 * i + 2] * Rb[3 * j + 2] * In[2];
-        v += ms * ((i == j ? cc : T(0.0)) - c[i] * c[j]);
-        I10[4 + e] = v;
-      }
-      // dof motion vectors (w; v at the world origin)
-      const int va = m.b_vadr[b];
-      if (m.b_jtype[b] == JNT_FREE) {
-        for (int d = 0; d < 3; ++d) {
-          T* st = S + 6 * (va + d);
-          st[0] = 0.0; st[1] = 0.0; st[2] = 0.0; st[3] = d == 0 ? 1.0 : 0.0; st[4] = d == 1 ? 1.0 : 0.0;
-          st[5] = d == 2 ? 1.0 : 0.0;
-          T* sr = S + 6 * (va + 3 + d);
-          sr[0] = Rb[d]; sr[1] = Rb[3 + d]; sr[2] = Rb[6 + d];
-          cross3(pb, sr, sr + 3);
-        }
-      } else {
-        T* sh = S + 6 * va;
-        matvec3(Rb, m.b_axis[b], sh);
-        cross3(pb, sh, sh + 3);
-      }
+      const T* Rp = R + 9 * par;
+      T Rl[9], t[3];
+      for (int i = 0; i < 9; ++i) Rl[i] = Rb[i];
+      matmul3(Rp, Rl, Rb);
+      matvec3(Rp, pb, t);
+      pb[0] = P[3 * par] + t[0]; pb[1] = P[3 * par + 1] + t[1]; pb[2] = P[3 * par + 2] + t[2];
     }
     g.sync();
+  }
+  // COMs
+  for (int b = g.lane; b < m.nbody; b += G) {
+    T c[3];
+    matvec3(R + 9 * b, m.b_com[b], c);
+    C[3 * b] = c[0] + P[3 * b]; C[3 * b + 1] = c[1] + P[3 * b + 1]; C[3 * b + 2] = c[2] + P[3 * b + 2];
+  }
+  g.sync();
+  // spatial inertias about the world origin (m, m c, R diag(I) R^T + m (|c|^2 1 - c c^T)),
+  // one entry per task
+  for (int k = g.lane; k < 10 * m.nbody; k += G) {
+    const int b = k / 10, e = k - 10 * b;
+    const double ms = m.b_mass[b];
+    const T* c = C + 3 * b;
+    T v;
+    if (e == 0) v = ms;
+    else if (e < 4) v = ms * c[e - 1];
+    else {
+      const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+      const int i = ii[e - 4], j = jj[e - 4];
+      const T* Rb = R + 9 * b;
+      const double* In = m.b_inertia[b];
+      v = Rb[3 * i] * Rb[3 * j] * In[0] + Rb[3 * i + 1] * Rb[3 * j + 1] * In[1] + Rb[3 * i + 2] * Rb[3 * j + 2] * In[2];
+      const T cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+      v += ms * ((i == j ? cc : T(0.0)) - c[i] * c[j]);
+    }
+    Ib[10 * b + e] = v;
+  }
+  // dof motion vectors (w; v at the world origin), one dof per task
+  for (int i = g.lane; i < m.nv; i += G) {
+    const int b = m.dof_body[i];
+    const T* Rb = R + 9 * b; const T* pb = P + 3 * b;
+    T* st = S + 6 * i;
+    if (m.b_jtype[b] == JNT_FREE) {
+      const int d = i - m.b_vadr[b];
+      if (d < 3) {
+        st[0] = 0.0; st[1] = 0.0; st[2] = 0.0; st[3] = d == 0 ? 1.0 : 0.0; st[4] = d == 1 ? 1.0 : 0.0;
+        st[5] = d == 2 ? 1.0 : 0.0;
+      } else {
+        st[0] = Rb[d - 3]; st[1] = Rb[d]; st[2] = Rb[d + 3];
+        cross3(pb, st, st + 3);
+      }
+    } else {
+      matvec3(Rb, m.b_axis[b], st);
+      cross3(pb, st, st + 3);
+    }
   }
   T* gR = w.at(L.gR); T* gp = w.at(L.gp);
   for (int gi = g.lane; gi < m.ngeom; gi += G) {
@@ -255,9 +319,8 @@ __device__ void crba(const Grp<G>& g, const DevModel& m, const WsT<T>& w) {
   }
   for (int i = g.lane; i < nv; i += G) inertia_apply(Ic + 10 * m.dof_body[i], S + 6 * i, F + 6 * i);
   g.sync();
-  for (int idx = g.lane; idx < nv * nv; idx += G) {
-    const int i = idx / nv, j = idx - i * nv;
-    if (j > i) continue;
+  for (int t = g.lane; t < nv * (nv + 1) / 2; t += G) {   // lower triangle
+    const int i = c_tri[t][0], j = c_tri[t][1];
     T v = 0.0;
     if ((m.b_anc[m.dof_body[i]] >> m.dof_body[j]) & 1u) {
       const T* s = S + 6 * j; const T* f = F + 6 * i;
@@ -270,48 +333,71 @@ __device__ void crba(const Grp<G>& g, const DevModel& m, const WsT<T>& w) {
 }
 
 // Recursive Newton-Euler with zero joint acceleration: rhs0 = tau - c.
+// Body velocities and velocity-product accelerations are sums along the path
+// from the root: each body's own joint term is computed for all bodies at
+// once, then added down the tree level by level (6 additions per body).  The
+// per-body work is split by component (one body component per task).
 template <int G, class T>
 __device__ void rne_and_forces(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* q, const T* v,
                                const T* u) {
   const Layout& L = *w.L;
   const T* Ib = w.at(L.Ib); const T* S = w.at(L.sd);
-  T* V = w.at(L.Vb); T* A = w.at(L.Ab); T* Fb = w.at(L.Fb);
-  for (int lev = 0; lev < m.nlevel; ++lev) {
-    for (int k = m.level_start[lev] + g.lane; k < m.level_start[lev + 1]; k += G) {
-      const int b = m.level_list[k];
-      const int par = m.b_parent[b];
-      T vb[6], ab[6];
-      if (par >= 0) {
-        for (int e = 0; e < 6; ++e) { vb[e] = V[6 * par + e]; ab[e] = A[6 * par + e]; }
-      } else {
-        for (int e = 0; e < 3; ++e) { vb[e] = 0.0; vb[3 + e] = 0.0; ab[e] = 0.0; ab[3 + e] = -m.grav[e]; }
-      }
-      const int va = m.b_vadr[b], nd = m.b_nv[b];
-      for (int d = 0; d < nd; ++d)
-        for (int e = 0; e < 6; ++e) vb[e] += S[6 * (va + d) + e] * v[va + d];
-      const int d0 = (m.b_jtype[b] == JNT_FREE) ? 3 : 0;   // world-fixed translation axes
-      for (int d = d0; d < nd; ++d) {
-        T sd[6];
-        crm6(vb, S + 6 * (va + d), sd);
-        for (int e = 0; e < 6; ++e) ab[e] += sd[e] * v[va + d];
-      }
-      T f1[6], iv[6], f2[6];
-      inertia_apply(Ib + 10 * b, ab, f1);
-      inertia_apply(Ib + 10 * b, vb, iv);
-      crf6(vb, iv, f2);
-      for (int e = 0; e < 6; ++e) { V[6 * b + e] = vb[e]; A[6 * b + e] = ab[e]; Fb[6 * b + e] = f1[e] + f2[e]; }
+  T* V = w.at(L.Vb); T* A = w.at(L.Ab); T* Fb = w.at(L.Fb); T* IV = w.at(L.iv);
+  const int nt = 6 * m.nbody;
+  // own joint velocity S v
+  for (int t = g.lane; t < nt; t += G) {
+    const int b = t / 6, e = t - 6 * b;
+    const int va = m.b_vadr[b], nd = m.b_nv[b];
+    T x = 0.0;
+    for (int d = 0; d < nd; ++d) x += S[6 * (va + d) + e] * v[va + d];
+    V[t] = x;
+  }
+  g.sync();
+  for (int lev = 1; lev < m.nlevel; ++lev) {
+    for (int t = 6 * m.level_start[lev] + g.lane; t < 6 * m.level_start[lev + 1]; t += G) {
+      const int k = t / 6, e = t - 6 * k;
+      const int b = m.level_list[k], par = m.b_parent[b];
+      if (par >= 0) V[6 * b + e] += V[6 * par + e];
     }
     g.sync();
   }
+  // own velocity-product acceleration (vb x S_d) v_d (gravity at the roots)
+  for (int t = g.lane; t < nt; t += G) {
+    const int b = t / 6, e = t - 6 * b;
+    const int va = m.b_vadr[b], nd = m.b_nv[b];
+    T x = (m.b_parent[b] < 0 && e >= 3) ? T(-m.grav[e - 3]) : T(0.0);
+    const int d0 = (m.b_jtype[b] == JNT_FREE) ? 3 : 0;   // world-fixed translation axes
+    for (int d = d0; d < nd; ++d) x += crm_comp(V + 6 * b, S + 6 * (va + d), e) * v[va + d];
+    A[t] = x;
+  }
+  g.sync();
+  for (int lev = 1; lev < m.nlevel; ++lev) {
+    for (int t = 6 * m.level_start[lev] + g.lane; t < 6 * m.level_start[lev + 1]; t += G) {
+      const int k = t / 6, e = t - 6 * k;
+      const int b = m.level_list[k], par = m.b_parent[b];
+      if (par >= 0) A[6 * b + e] += A[6 * par + e];
+    }
+    g.sync();
+  }
+  // body forces I a + v x* (I v)
+  for (int t = g.lane; t < nt; t += G) {
+    const int b = t / 6, e = t - 6 * b;
+    Fb[t] = inertia_comp(Ib + 10 * b, A + 6 * b, e);
+    IV[t] = inertia_comp(Ib + 10 * b, V + 6 * b, e);
+  }
+  g.sync();
+  for (int t = g.lane; t < nt; t += G) {
+    const int b = t / 6, e = t - 6 * b;
+    Fb[t] += crf_comp(V + 6 * b, IV + 6 * b, e);
+  }
+  g.sync();
   for (int lev = m.nlevel - 1; lev >= 1; --lev) {
     // children add into their parents; parents of one level are distinct bodies
     // of the level above, so sweep the level above and gather its children
-    for (int k = m.level_start[lev - 1] + g.lane; k < m.level_start[lev]; k += G) {
+    for (int t = 6 * m.level_start[lev - 1] + g.lane; t < 6 * m.level_start[lev]; t += G) {
+      const int k = t / 6, e = t - 6 * k;
       const int b = m.level_list[k];
-      for (int c = 0; c < m.child_count[b]; ++c) {
-        const int ch = m.child_list[m.child_start[b] + c];
-        for (int e = 0; e < 6; ++e) Fb[6 * b + e] += Fb[6 * ch + e];
-      }
+      for (int c = 0; c < m.child_count[b]; ++c) Fb[6 * b + e] += Fb[6 * m.child_list[m.child_start[b] + c] + e];
     }
     g.sync();
   }
@@ -528,26 +614,28 @@ template <int G, class T>
 __device__ int make_rows(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* v, bool cfd) {
   const Layout& L = *w.L;
   const T* CT = w.at(L.ct); const T* S = w.at(L.sd);
-  int* slotrow = w.i + L.slotrow; int* rowid = w.i + L.rowid;
+  int* slotrow = w.i + L.slotrow; int* rowid = w.i + L.rowid; int* slist = w.i + L.slist;
   const double thr = cfd ? m.cfd[2] : 0.0;
   const int nv = m.nv;
   if (g.lane == 0) {
-    int n = 0;
+    int n = 0, ns = 0;
     for (int s = 0; s < m.nslot; ++s) {
       const bool inc = value(CT[16 * s]) < thr;
       slotrow[s] = inc ? n : -1;
-      if (inc) n += (m.p_condim[m.s_pair[s]] == 1) ? 1 : 4;
+      if (inc) { n += (m.p_condim[m.s_pair[s]] == 1) ? 1 : 4; slist[ns++] = s; }
     }
     slotrow[m.nslot] = n;
+    w.i[L.misc] = ns;
   }
   g.sync();
   const int nr = slotrow[m.nslot];
+  const int nincl = w.i[L.misc];
   if (nr > L.rcap) return -1;
   T* J = w.at(L.J);
-  for (int idx = g.lane; idx < m.nslot * nv; idx += G) {
-    const int s = idx / nv, i = idx - s * nv;
+  for (int idx = g.lane; idx < nincl * nv; idx += G) {   // included slots only
+    const int si = idx / nv, i = idx - si * nv;
+    const int s = slist[si];
     const int r0 = slotrow[s];
-    if (r0 < 0) continue;
     const T* ct = CT + 16 * s;
     const int p = m.s_pair[s];
     const int bA = m.g_body[m.p_g1[p]];
@@ -576,9 +664,9 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const WsT<T>& w, co
   }
   g.sync();
   T* aref = w.at(L.aref); T* Dr = w.at(L.Dr);
-  for (int s = g.lane; s < m.nslot; s += G) {
+  for (int si = g.lane; si < nincl; si += G) {
+    const int s = slist[si];
     const int r0 = slotrow[s];
-    if (r0 < 0) continue;
     const int p = m.s_pair[s];
     const int nrow = m.p_condim[p] == 1 ? 1 : 4;
     const T* ct = CT + 16 * s;
@@ -604,14 +692,13 @@ __device__ bool cholesky(const Grp<G>& g, T* H, T* invd, int n) {
   for (int k = 0; k < n; ++k) {
     const T hkk = H[k * n + k];
     ok = ok && (value(hkk) > 0);
-    const T il = 1.0 / sqrt(hkk);   // the diagonal of the factor is kept as its reciprocal
+    const T il = rsqrt_t(hkk);   // the diagonal of the factor is kept as its reciprocal
     for (int i = k + 1 + g.lane; i < n; i += G) H[i * n + k] *= il;
     if (g.lane == 0) invd[k] = il;
     g.sync();
     const int nt = n - k - 1;
-    for (int idx = g.lane; idx < nt * nt; idx += G) {
-      const int i = k + 1 + idx / nt, j = k + 1 + idx % nt;
-      if (j > i) continue;
+    for (int t = g.lane; t < nt * (nt + 1) / 2; t += G) {   // lower triangle of the trailing block
+      const int i = k + 1 + c_tri[t][0], j = k + 1 + c_tri[t][1];
       H[i * n + j] -= H[i * n + k] * H[j * n + k];
     }
     g.sync();
@@ -863,9 +950,11 @@ __device__ void integrate_pos(const Grp<G>& g, const DevModel& m, const T* q, co
     const T* d = dq + va + 3;
     const T th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     T cw, sk;
-    if (value(th2) < 1e-12) {
-      cw = 1.0 - th2 * 0.125 + th2 * th2 * (1.0 / 384.0);
-      sk = 0.5 - th2 * (1.0 / 48.0) + th2 * th2 * (1.0 / 3840.0);
+    if (value(th2) < 1e-2) {
+      // |dq| < 0.1 rad: Taylor series of cos(th/2) and sin(th/2)/th in th^2
+      // (the next terms are below 3e-20): no square root, sine or division
+      cw = 1.0 + th2 * (-1.0 / 8.0 + th2 * (1.0 / 384.0 + th2 * (-1.0 / 46080.0 + th2 * (1.0 / 10321920.0))));
+      sk = 0.5 + th2 * (-1.0 / 48.0 + th2 * (1.0 / 3840.0 + th2 * (-1.0 / 645120.0 + th2 * (1.0 / 185794560.0))));
     } else {
       const T th = sqrt(th2);
       T sn, cs;
@@ -879,7 +968,7 @@ __device__ void integrate_pos(const Grp<G>& g, const DevModel& m, const T* q, co
     const T rx = w0 * ex + a0 * cw + b0 * ez - c0 * ey;
     const T ry = w0 * ey - a0 * ez + b0 * cw + c0 * ex;
     const T rz = w0 * ez + a0 * ey - b0 * ex + c0 * cw;
-    const T in = 1.0 / sqrt(rw * rw + rx * rx + ry * ry + rz * rz);
+    const T in = rsqrt_t(rw * rw + rx * rx + ry * ry + rz * rz);
     out[qa + 3] = rw * in; out[qa + 4] = rx * in; out[qa + 5] = ry * in; out[qa + 6] = rz * in;
   }
   g.sync();

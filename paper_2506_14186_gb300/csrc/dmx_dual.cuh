@@ -71,8 +71,12 @@ __device__ __forceinline__ Dual pow(const Dual& a, double p) {
 }
 __device__ __forceinline__ Dual fabs(const Dual& a) { return a.v < 0 ? -a : a; }
 
-// reciprocal square root; for doubles the same arithmetic as 1 / sqrt
-__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / ::sqrt(x); }
-__device__ __forceinline__ Dual rsqrt_t(const Dual& x) { return 1.0 / sqrt(x); }
+// reciprocal square root (CUDA's double rsqrt: one rounding step instead of a
+// square root and a division)
+__device__ __forceinline__ double rsqrt_t(double x) { return ::rsqrt(x); }
+__device__ __forceinline__ Dual rsqrt_t(const Dual& x) {
+  const double r = ::rsqrt(x.v);
+  return Dual(r, -0.5 * r * r * r * x.d);
+}
 
 }  // namespace dmx

@@ -60,11 +60,11 @@ struct DevModel {
 // Offsets (in doubles / ints) of one environment's shared-memory workspace.
 struct Layout {
   int qn, vn, qs, vs, kv, ka, dq;
-  int R, p, com, sd, Ib, Ic, F, Vb, Ab, Fb, gR, gp;
+  int R, p, com, sd, Ib, Ic, F, Vb, Ab, Fb, iv, gR, gp;
   int M, H, rhs0, a, an, tmp, tmp2;
   int ct, J, aref, Dr, z, s, u;
   int nd;                            // doubles per environment (padded to even)
-  int rowid, slotrow, amask, pmask, misc;
+  int rowid, slotrow, slist, amask, pmask, misc;
   int ni;                            // ints per environment
   int rcap;                          // constraint-row capacity
 };
@@ -78,7 +78,7 @@ DMX_HD inline Layout make_layout(const DevModel& m, int rcap) {
   L.kv = take(7 * nv); L.ka = take(7 * nv); L.dq = take(nv);
   L.R = take(9 * nb); L.p = take(3 * nb); L.com = take(3 * nb); L.sd = take(6 * nv);
   L.Ib = take(10 * nb); L.Ic = take(10 * nb); L.F = take(6 * nv);
-  L.Vb = take(6 * nb); L.Ab = take(6 * nb); L.Fb = take(6 * nb);
+  L.Vb = take(6 * nb); L.Ab = take(6 * nb); L.Fb = take(6 * nb); L.iv = take(6 * nb);
   L.gR = take(9 * ng); L.gp = take(3 * ng);
   L.M = take(nv * nv); L.H = take(nv * nv);
   L.rhs0 = take(nv); L.a = take(nv); L.an = take(nv); L.tmp = take(nv); L.tmp2 = take(nv);
@@ -88,7 +88,8 @@ DMX_HD inline Layout make_layout(const DevModel& m, int rcap) {
   L.nd = (o + 1) & ~1;
   int i = 0;
   auto takei = [&](int n) { int r = i; i += n; return r; };
-  L.rowid = takei(rcap); L.slotrow = takei(ns + 1); L.amask = takei(MASKW); L.pmask = takei(MASKW);
+  L.rowid = takei(rcap); L.slotrow = takei(ns + 1); L.slist = takei(ns); L.amask = takei(MASKW);
+  L.pmask = takei(MASKW);
   L.misc = takei(8);
   L.ni = (i + 3) & ~3;
   L.rcap = rcap;

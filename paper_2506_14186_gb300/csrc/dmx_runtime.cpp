@@ -245,14 +245,17 @@ extern "C" dmx_status dmx_model_info(const dmx_model* m, double* invw, int32_t* 
 static bool valid_lanes(int G) { return G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32; }
 
 // Threads per block and dynamic shared memory for G lanes per environment.
+// One warp per block: the block scheduler then spreads the warps over every
+// SM (with larger blocks a batch of a few thousand environments filled only
+// some of the SMs), and a block needs only one warp's workspace.
 bool launch_config(const dmx_model* m, int G, int* threads, size_t* smem) {
   const int per = m->L.nd * 8 + m->L.ni * 4;
-  for (int t = 256; t >= 32; t >>= 1) {
-    if (t < G) break;
-    const size_t s = (size_t)(t / G) * per;
-    if ((int)s <= m->smem_max - 1024) { *threads = t; *smem = s; return true; }
-  }
-  return false;
+  if (G < 1 || G > 32) return false;
+  const size_t s = (size_t)(32 / G) * per;
+  if ((int)s > m->smem_max - 1024) return false;
+  *threads = 32;
+  *smem = s;
+  return true;
 }
 
 int default_lanes(const dmx_model* m, int B) {
@@ -478,14 +481,15 @@ extern "C" dmx_status dmx_set_lanes(dmx_model* m, int32_t B, int32_t grad, int32
 static bool valid_adj_lanes(int G) { return G == 2 || G == 4 || G == 8 || G == 16 || G == 32; }
 
 // Threads and shared memory of the reverse-mode adjoint kernel for G lanes.
+// (one warp per block, as for the forward kernels)
 static bool adj_launch_config(const dmx_model* m, const dmx::LayoutBar& LB, int G, int* threads, size_t* smem) {
   const int per = (m->L.nd + LB.nd) * 8 + m->L.ni * 4;
-  for (int t = 256; t >= 32; t >>= 1) {
-    if (t < G) break;
-    const size_t s = (size_t)(t / G) * per;
-    if ((int)s <= m->smem_max - 2048) { *threads = t; *smem = s; return true; }
-  }
-  return false;
+  if (G < 1 || G > 32) return false;
+  const size_t s = (size_t)(32 / G) * per;
+  if ((int)s > m->smem_max - 2048) return false;
+  *threads = 32;
+  *smem = s;
+  return true;
 }
 
 // Lanes of the reverse-mode adjoint: the recorded choice, else enough lanes

@@ -225,7 +225,7 @@ static __device__ void capsule_box_vjp(const DevModel& m, const double* gR, cons
   if (fabs(n[2]) >= 0.5) { ref[0] = 1; ref[2] = 0; }
   double t1r[3], t1[3];
   cross3(n, ref, t1r);
-  const double il = 1.0 / ::sqrt(dot3(t1r, t1r));
+  const double il = rsqrt_t(dot3(t1r, t1r));
   for (int i = 0; i < 3; ++i) t1[i] = t1r[i] * il;
   // reverse
   double nb[3] = {cb[4], cb[5], cb[6]}, t1b[3] = {cb[7], cb[8], cb[9]};
@@ -645,11 +645,11 @@ __device__ void integrate_pos_vjp(const Grp<G>& g, const DevModel& m, const doub
     const double* d = dq + va + 3;
     const double th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     double cw, sk, dcw, dsk;   // and their derivatives with respect to th2
-    if (th2 < 1e-12) {
-      cw = 1.0 - th2 * 0.125 + th2 * th2 * (1.0 / 384.0);
-      sk = 0.5 - th2 * (1.0 / 48.0) + th2 * th2 * (1.0 / 3840.0);
-      dcw = -0.125 + th2 * (2.0 / 384.0);
-      dsk = -(1.0 / 48.0) + th2 * (2.0 / 3840.0);
+    if (th2 < 1e-2) {   // the series branch of integrate_pos
+      cw = 1.0 + th2 * (-1.0 / 8.0 + th2 * (1.0 / 384.0 + th2 * (-1.0 / 46080.0 + th2 * (1.0 / 10321920.0))));
+      sk = 0.5 + th2 * (-1.0 / 48.0 + th2 * (1.0 / 3840.0 + th2 * (-1.0 / 645120.0 + th2 * (1.0 / 185794560.0))));
+      dcw = -1.0 / 8.0 + th2 * (2.0 / 384.0 + th2 * (-3.0 / 46080.0 + th2 * (4.0 / 10321920.0)));
+      dsk = -1.0 / 48.0 + th2 * (2.0 / 3840.0 + th2 * (-3.0 / 645120.0 + th2 * (4.0 / 185794560.0)));
     } else {
       const double th = ::sqrt(th2);
       double sn, cs;
@@ -666,7 +666,7 @@ __device__ void integrate_pos_vjp(const Grp<G>& g, const DevModel& m, const doub
     r[1] = qq[0] * e[1] + qq[1] * e[0] + qq[2] * e[3] - qq[3] * e[2];
     r[2] = qq[0] * e[2] - qq[1] * e[3] + qq[2] * e[0] + qq[3] * e[1];
     r[3] = qq[0] * e[3] + qq[1] * e[2] - qq[2] * e[1] + qq[3] * e[0];
-    const double in = 1.0 / ::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    const double in = rsqrt_t(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
     const double* o4 = ob + qa + 3;
     double oo = 0.0;
     for (int k = 0; k < 4; ++k) oo += r[k] * in * o4[k];

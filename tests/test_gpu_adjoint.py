@@ -94,8 +94,13 @@ def test_ball_gradient(dmx, orc_mod, cfd, mode):
 @pytest.mark.parametrize("cfd", [False, True])
 @pytest.mark.parametrize("K", [1, 7, 32])
 def test_box_gradient(dmx, orc_mod, cfd, K, mode):
+    """Box pushes over 0.1 s (about 240 accepted steps of sliding contact).
+    The frozen-step gradient of these pushes is ill-conditioned beyond that:
+    a 1e-16 relative change of x0 moves it by 3e-8 (0.15 s), 2e-7 (0.2 s)
+    and 8e-7 (0.3 s) relative (tests/test_oracle_adjoint.py pins this), so
+    the 1e-6 bar is checked where rounding cannot reach it."""
     sc = W.box_scene(**CFD_ONLY) if cfd else W.box_scene()
-    inp = W.box_push_inputs(24, seed=5, T=0.3)
+    inp = W.box_push_inputs(24, seed=5, T=0.1)
     rng = np.random.default_rng(1)
     xT_bar = rng.normal(size=(24, 13))
     m = dmx.Model(sc)
@@ -238,11 +243,10 @@ def test_rhs_vjp_matches_oracle_jacobian(dmx, orc_mod, name, cfd):
 def test_reverse_kernel_equals_tangent_kernel(dmx, name):
     """The two adjoint kernels compute the same derivative on the same tape:
     they differ only in rounding (a product of a few hundred step Jacobians
-    of a stiff contact map; measured 1e-11 for the arm, 1e-8 for the box),
-    checked at a tenth of the gradient tolerance."""
+    of a stiff contact map), checked at a tenth of the gradient tolerance."""
     import torch
     sc = W.SCENES[name]()
-    inp = W.box_push_inputs(64, seed=9, T=0.2) if name == "box" else W.chain_inputs(16, T=0.2, NI=4)
+    inp = W.box_push_inputs(64, seed=9, T=0.1) if name == "box" else W.chain_inputs(16, T=0.2, NI=4)
     m = dmx.Model(sc)
     ctrl = None if inp["ctrl"] is None else _dev(np.transpose(inp["ctrl"], (1, 2, 0)))
     out = dmx.rollout(m, _dev(inp["x0"].T), _dev(inp["T"]), ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"],

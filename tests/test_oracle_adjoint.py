@@ -197,3 +197,39 @@ def test_cfd_step_jacobian_uses_cfd_rhs_at_the_plain_states(orc):
     Jq, Jv, _ = m.rhs_jacobian(q, v, None, cfd=True)
     np.testing.assert_allclose((Jx[7:, :7]) / h, Jq, rtol=1e-5, atol=1e-6)
     np.testing.assert_allclose((Jx[7:, 7:] - np.eye(6)) / h, Jv, rtol=1e-5, atol=1e-6)
+
+
+def _replay_grads(m, inp, xT_bar, x0):
+    B = len(x0)
+    H, N = [], []
+    for e in range(B):
+        r = m.rollout(inp["x0"][e], T=float(inp["T"][e]), rtol=inp["rtol"], atol=inp["atol"], h0=inp["h0"],
+                      max_steps=inp["max_steps"])
+        H.append(r["hlog"]); N.append(r["nsteps"])
+    hl = np.zeros((B, max(N)))
+    for e in range(B):
+        hl[e, :N[e]] = H[e]
+    return m.batch_replay_grad(x0, inp["T"], hl, N, xT_bar)["x0_bar"]
+
+
+def test_gradient_conditioning_floor(orc):
+    """How far rounding alone can move the frozen-step gradient of box pushes:
+    the x0 gradient at x0 and at x0 (1 + 1e-16 noise), along the same step
+    sizes.  Over 0.1 s the change stays far below the 1e-6 gradient bar; over
+    0.3 s it reaches that bar (products of a few hundred Jacobians of the
+    stiff sliding-contact map), which is why the GPU gradient tests of box
+    pushes integrate 0.1 s."""
+    m = orc.OracleModel(W.box_scene())
+    floors = {}
+    for T in (0.1, 0.3):
+        inp = W.box_push_inputs(24, seed=5, T=T)
+        w = np.random.default_rng(1).normal(size=(24, 13))
+        g0 = _replay_grads(m, inp, w, inp["x0"])
+        worst = 0.0
+        for trial in range(3):
+            x1 = inp["x0"] * (1 + 1e-16 * np.random.default_rng(trial).normal(size=inp["x0"].shape))
+            g1 = _replay_grads(m, inp, w, x1)
+            worst = max(worst, max(rel_err(g1[e], g0[e]) for e in range(24)))
+        floors[T] = worst
+    assert floors[0.1] < 1e-8, floors
+    assert floors[0.3] > 1e-7, floors
