@@ -490,46 +490,70 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     }
     g.sync();
   }
-  // ---- recursive Newton-Euler, leaves to root
-  for (int lev = m.nlevel - 1; lev >= 0; --lev) {
-    for (int k = m.level_start[lev] + g.lane; k < m.level_start[lev + 1]; k += G) {
+  // ---- recursive Newton-Euler (forward: V = V_parent + S v, A = A_parent + (V x S) v,
+  // F = I A + V x* (I V)), reversed with the same split: per-body work for all
+  // bodies at once, sums along the tree level by level
+  for (int bb = g.lane; bb < nb; bb += G) {      // F's cotangent -> A, V (own terms)
+    const double* vbv = V + 6 * bb; const double* abv = A + 6 * bb; const double* I = Ib + 10 * bb;
+    const double* fbar = Fbb + 6 * bb;
+    double* ibb = Ibb + 10 * bb;
+    double abar6[6], vbar6[6] = {0, 0, 0, 0, 0, 0}, ivb[6] = {0, 0, 0, 0, 0, 0}, iv[6], t[6];
+    inertia_apply(I, fbar, abar6);               // f1 = I ab
+    inertia_grad(fbar, abv, ibb);
+    inertia_apply(I, vbv, iv);                   // f2 = vb x* (I vb)
+    crf6_vjp(vbv, iv, fbar, vbar6, ivb);
+    inertia_apply(I, ivb, t);
+    for (int e = 0; e < 6; ++e) vbar6[e] += t[e];
+    inertia_grad(ivb, vbv, ibb);
+    for (int e = 0; e < 6; ++e) { Vbb[6 * bb + e] = vbar6[e]; Abb[6 * bb + e] = abar6[e]; }
+  }
+  g.sync();
+  for (int lev = m.nlevel - 1; lev >= 1; --lev) {   // A_child = A_parent + ...: gather into parents
+    for (int k = m.level_start[lev - 1] + g.lane; k < m.level_start[lev]; k += G) {
       const int bb = m.level_list[k];
-      const double* vbv = V + 6 * bb; const double* abv = A + 6 * bb; const double* I = Ib + 10 * bb;
-      const double* fbar = Fbb + 6 * bb;
-      double* ibb = Ibb + 10 * bb;
-      double abar6[6], vbar6[6] = {0, 0, 0, 0, 0, 0}, ivb[6] = {0, 0, 0, 0, 0, 0}, iv[6], t[6];
-      inertia_apply(I, fbar, abar6);             // f1 = I ab
-      inertia_grad(fbar, abv, ibb);
-      inertia_apply(I, vbv, iv);                 // f2 = vb x* (I vb)
-      crf6_vjp(vbv, iv, fbar, vbar6, ivb);
-      inertia_apply(I, ivb, t);
-      for (int e = 0; e < 6; ++e) vbar6[e] += t[e];
-      inertia_grad(ivb, vbv, ibb);
       for (int c = 0; c < m.child_count[bb]; ++c) {
         const int ch = m.child_list[m.child_start[bb] + c];
-        for (int e = 0; e < 6; ++e) { abar6[e] += Abb[6 * ch + e]; vbar6[e] += Vbb[6 * ch + e]; }
+        for (int e = 0; e < 6; ++e) Abb[6 * bb + e] += Abb[6 * ch + e];
       }
-      const int va = m.b_vadr[bb], nd = m.b_nv[bb];
-      const int d0 = (m.b_jtype[bb] == JNT_FREE) ? 3 : 0;
-      for (int d = d0; d < nd; ++d) {            // ab += (vb x S_d) v_d
-        const double* sd = S + 6 * (va + d);
-        double cm[6];
-        crm6(vbv, sd, cm);
-        double s1 = 0.0, cb6[6];
-        for (int e = 0; e < 6; ++e) { s1 += abar6[e] * cm[e]; cb6[e] = abar6[e] * v[va + d]; }
-        vb[va + d] += s1;
-        crm6_vjp(vbv, sd, cb6, vbar6, Sb + 6 * (va + d));
-      }
-      for (int d = 0; d < nd; ++d) {             // vb += S_d v_d
-        const double* sd = S + 6 * (va + d);
-        double s1 = 0.0;
-        for (int e = 0; e < 6; ++e) { s1 += vbar6[e] * sd[e]; Sb[6 * (va + d) + e] += vbar6[e] * v[va + d]; }
-        vb[va + d] += s1;
-      }
-      for (int e = 0; e < 6; ++e) { Vbb[6 * bb + e] = vbar6[e]; Abb[6 * bb + e] = abar6[e]; }
     }
     g.sync();
   }
+  for (int bb = g.lane; bb < nb; bb += G) {      // A's own term (V x S_d) v_d
+    const double* vbv = V + 6 * bb; const double* abar6 = Abb + 6 * bb;
+    const int va = m.b_vadr[bb], nd = m.b_nv[bb];
+    const int d0 = (m.b_jtype[bb] == JNT_FREE) ? 3 : 0;
+    for (int d = d0; d < nd; ++d) {
+      const double* sd = S + 6 * (va + d);
+      double cm[6];
+      crm6(vbv, sd, cm);
+      double s1 = 0.0, cb6[6];
+      for (int e = 0; e < 6; ++e) { s1 += abar6[e] * cm[e]; cb6[e] = abar6[e] * v[va + d]; }
+      vb[va + d] += s1;
+      crm6_vjp(vbv, sd, cb6, Vbb + 6 * bb, Sb + 6 * (va + d));
+    }
+  }
+  g.sync();
+  for (int lev = m.nlevel - 1; lev >= 1; --lev) {   // V_child = V_parent + ...
+    for (int k = m.level_start[lev - 1] + g.lane; k < m.level_start[lev]; k += G) {
+      const int bb = m.level_list[k];
+      for (int c = 0; c < m.child_count[bb]; ++c) {
+        const int ch = m.child_list[m.child_start[bb] + c];
+        for (int e = 0; e < 6; ++e) Vbb[6 * bb + e] += Vbb[6 * ch + e];
+      }
+    }
+    g.sync();
+  }
+  for (int bb = g.lane; bb < nb; bb += G) {      // V's own term S_d v_d
+    const double* vbar6 = Vbb + 6 * bb;
+    const int va = m.b_vadr[bb], nd = m.b_nv[bb];
+    for (int d = 0; d < nd; ++d) {
+      const double* sd = S + 6 * (va + d);
+      double s1 = 0.0;
+      for (int e = 0; e < 6; ++e) { s1 += vbar6[e] * sd[e]; Sb[6 * (va + d) + e] += vbar6[e] * v[va + d]; }
+      vb[va + d] += s1;
+    }
+  }
+  g.sync();
   if (g.lane == 0) {
     for (int a = 0; a < m.nact; ++a) {
       const int vi = m.a_vadr[a];
@@ -537,96 +561,113 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
       else { ub[a] += m.a_kp[a] * y[vi]; qb[m.a_qadr[a]] -= m.a_kp[a] * y[vi]; vb[vi] -= m.a_kd[a] * y[vi]; }
     }
   }
+  // ---- kinematics (forward: local rotation Rl = Roff Rj(theta) or the free joint's
+  // pose; R = R_parent Rl, p = p_parent + R_parent b_pos; then COMs, inertias,
+  // motion vectors and geoms from (R, p)).  Own terms of every body first.
+  for (int bb = g.lane; bb < nb; bb += G) {
+    double* rb = Rb + 9 * bb; double* pbv = pb + 3 * bb;   // geom terms are already in
+    const double* Rv = R + 9 * bb; const double* pv = P + 3 * bb; const double* c = C + 3 * bb;
+    // spatial inertia about the origin: (m, m c, R diag(In) R^T + m (|c|^2 - c c^T))
+    const double ms = m.b_mass[bb];
+    const double* In = m.b_inertia[bb];
+    const double* ib = Ibb + 10 * bb;
+    double cb3[3] = {ms * ib[1], ms * ib[2], ms * ib[3]};
+    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+    for (int e = 0; e < 6; ++e) {
+      const int i = ii[e], j = jj[e];
+      const double be = ib[4 + e];
+      for (int kk = 0; kk < 3; ++kk) {
+        rb[3 * i + kk] += be * Rv[3 * j + kk] * In[kk];
+        rb[3 * j + kk] += be * Rv[3 * i + kk] * In[kk];
+      }
+      if (i == j) for (int kk = 0; kk < 3; ++kk) cb3[kk] += be * ms * 2.0 * c[kk];
+      cb3[i] -= be * ms * c[j];
+      cb3[j] -= be * ms * c[i];
+    }
+    // c = R com + p
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) rb[3 * i + j] += cb3[i] * m.b_com[bb][j];
+      pbv[i] += cb3[i];
+    }
+    // dof motion vectors
+    const int va = m.b_vadr[bb];
+    if (m.b_jtype[bb] == JNT_FREE) {
+      for (int d = 0; d < 3; ++d) {
+        const double* sbd = Sb + 6 * (va + 3 + d);
+        const double sr[3] = {Rv[d], Rv[3 + d], Rv[6 + d]};
+        double srb[3] = {sbd[0], sbd[1], sbd[2]};
+        acc_cross(sbd + 3, pv, srb);           // lin = p x sr
+        acc_cross(sr, sbd + 3, pbv);
+        rb[d] += srb[0]; rb[3 + d] += srb[1]; rb[6 + d] += srb[2];
+      }
+    } else {
+      const double* sbd = Sb + 6 * va;
+      const double* ax = m.b_axis[bb];
+      double sh[3];
+      matvec3(Rv, ax, sh);
+      double shb[3] = {sbd[0], sbd[1], sbd[2]};
+      acc_cross(sbd + 3, pv, shb);             // lin = p x sh
+      acc_cross(sh, sbd + 3, pbv);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) rb[3 * i + j] += shb[i] * ax[j];
+      // the local rotation, for the composition below
+      double Rj[9], dRj[9], sn, cs;
+      ::sincos(q[m.b_qadr[bb]], &sn, &cs);
+      rodrigues(ax, sn, cs, Rj, dRj);
+      matmul3(m.b_Roff[bb], Rj, cR + 9 * bb);
+    }
+  }
   g.sync();
-  // ---- kinematics, leaves to root
-  for (int lev = m.nlevel - 1; lev >= 0; --lev) {
-    for (int k = m.level_start[lev] + g.lane; k < m.level_start[lev + 1]; k += G) {
+  // composition, leaves to root: R_parent gets Rbar Rl^T + pbar b_pos^T, p_parent gets pbar
+  for (int lev = m.nlevel - 1; lev >= 1; --lev) {
+    for (int k = m.level_start[lev - 1] + g.lane; k < m.level_start[lev]; k += G) {
       const int bb = m.level_list[k];
-      double rb[9], pbv[3];
-      for (int e = 0; e < 9; ++e) rb[e] = Rb[9 * bb + e];
-      for (int e = 0; e < 3; ++e) pbv[e] = pb[3 * bb + e];
+      double* rb = Rb + 9 * bb; double* pbv = pb + 3 * bb;
       for (int c = 0; c < m.child_count[bb]; ++c) {
         const int ch = m.child_list[m.child_start[bb] + c];
-        for (int e = 0; e < 9; ++e) rb[e] += cR[9 * ch + e];
-        for (int e = 0; e < 3; ++e) pbv[e] += cp[3 * ch + e];
-      }
-      const double* Rv = R + 9 * bb; const double* pv = P + 3 * bb; const double* c = C + 3 * bb;
-      // spatial inertia about the origin: (m, m c, R diag(In) R^T + m (|c|^2 - c c^T))
-      const double ms = m.b_mass[bb];
-      const double* In = m.b_inertia[bb];
-      const double* ib = Ibb + 10 * bb;
-      double cb3[3] = {ms * ib[1], ms * ib[2], ms * ib[3]};
-      const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
-      for (int e = 0; e < 6; ++e) {
-        const int i = ii[e], j = jj[e];
-        const double be = ib[4 + e];
-        for (int kk = 0; kk < 3; ++kk) {
-          rb[3 * i + kk] += be * Rv[3 * j + kk] * In[kk];
-          rb[3 * j + kk] += be * Rv[3 * i + kk] * In[kk];
-        }
-        if (i == j) for (int kk = 0; kk < 3; ++kk) cb3[kk] += be * ms * 2.0 * c[kk];
-        cb3[i] -= be * ms * c[j];
-        cb3[j] -= be * ms * c[i];
-      }
-      // c = R com + p
-      for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) rb[3 * i + j] += cb3[i] * m.b_com[bb][j];
-        pbv[i] += cb3[i];
-      }
-      // dof motion vectors
-      const int va = m.b_vadr[bb];
-      if (m.b_jtype[bb] == JNT_FREE) {
-        for (int d = 0; d < 3; ++d) {
-          const double* sbd = Sb + 6 * (va + 3 + d);
-          const double sr[3] = {Rv[d], Rv[3 + d], Rv[6 + d]};
-          double srb[3] = {sbd[0], sbd[1], sbd[2]};
-          acc_cross(sbd + 3, pv, srb);           // lin = p x sr
-          acc_cross(sr, sbd + 3, pbv);
-          rb[d] += srb[0]; rb[3 + d] += srb[1]; rb[6 + d] += srb[2];
-        }
-        const int qa = m.b_qadr[bb];
-        qb[qa] += pbv[0]; qb[qa + 1] += pbv[1]; qb[qa + 2] += pbv[2];
-        quat_to_mat_vjp(q + qa + 3, rb, qb + qa + 3);
-      } else {
-        const double* sbd = Sb + 6 * va;
-        const double* ax = m.b_axis[bb];
-        double sh[3];
-        matvec3(Rv, ax, sh);
-        double shb[3] = {sbd[0], sbd[1], sbd[2]};
-        acc_cross(sbd + 3, pv, shb);             // lin = p x sh
-        acc_cross(sh, sbd + 3, pbv);
-        for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) rb[3 * i + j] += shb[i] * ax[j];
-        // R = Rp Roff Rj(theta), p = pp + Rp b_pos
-        const int par = m.b_parent[bb];
-        double Rp[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-        if (par >= 0) for (int e = 0; e < 9; ++e) Rp[e] = R[9 * par + e];
-        double Ro[9], Rj[9], dRj[9], sn, cs;
-        matmul3(Rp, m.b_Roff[bb], Ro);
-        ::sincos(q[m.b_qadr[bb]], &sn, &cs);
-        rodrigues(ax, sn, cs, Rj, dRj);
-        double th = 0.0;
-        double robar[9];
-        for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) {
-            // (Ro^T Rbar)_ij and (Rbar Rj^T)_ij
-            th += (Ro[i] * rb[j] + Ro[3 + i] * rb[3 + j] + Ro[6 + i] * rb[6 + j]) * dRj[3 * i + j];
-            robar[3 * i + j] = rb[3 * i] * Rj[3 * j] + rb[3 * i + 1] * Rj[3 * j + 1] + rb[3 * i + 2] * Rj[3 * j + 2];
-          }
-        qb[m.b_qadr[bb]] += th;
-        if (par >= 0) {
-          const double* Rf = m.b_Roff[bb]; const double* bp = m.b_pos[bb];
-          for (int i = 0; i < 3; ++i) {
-            for (int j = 0; j < 3; ++j)
-              cR[9 * bb + 3 * i + j] = robar[3 * i] * Rf[3 * j] + robar[3 * i + 1] * Rf[3 * j + 1] +
-                                       robar[3 * i + 2] * Rf[3 * j + 2] + pbv[i] * bp[j];
-            cp[3 * bb + i] = pbv[i];
-          }
+        if (m.b_jtype[ch] == JNT_FREE) continue;
+        const double* rc = Rb + 9 * ch; const double* pc = pb + 3 * ch;
+        const double* Rl = cR + 9 * ch; const double* bp = m.b_pos[ch];
+        for (int i = 0; i < 3; ++i) {
+          for (int j = 0; j < 3; ++j)
+            rb[3 * i + j] += rc[3 * i] * Rl[3 * j] + rc[3 * i + 1] * Rl[3 * j + 1] + rc[3 * i + 2] * Rl[3 * j + 2] +
+                             pc[i] * bp[j];
+          pbv[i] += pc[i];
         }
       }
     }
     g.sync();
   }
+  // joint coordinates
+  for (int bb = g.lane; bb < nb; bb += G) {
+    const double* rb = Rb + 9 * bb; const double* pbv = pb + 3 * bb;
+    const int qa = m.b_qadr[bb];
+    if (m.b_jtype[bb] == JNT_FREE) {
+      qb[qa] += pbv[0]; qb[qa + 1] += pbv[1]; qb[qa + 2] += pbv[2];
+      quat_to_mat_vjp(q + qa + 3, rb, qb + qa + 3);
+      continue;
+    }
+    // Rl bar = R_parent^T Rbar; Rj bar = Roff^T Rl bar; theta bar = <Rj bar, dRj/dtheta>
+    const int par = m.b_parent[bb];
+    double rl[9];
+    if (par >= 0) {
+      const double* Rp = R + 9 * par;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) rl[3 * i + j] = Rp[i] * rb[j] + Rp[3 + i] * rb[3 + j] + Rp[6 + i] * rb[6 + j];
+    } else {
+      for (int e = 0; e < 9; ++e) rl[e] = rb[e];
+    }
+    double Rj[9], dRj[9], sn, cs;
+    ::sincos(q[qa], &sn, &cs);
+    rodrigues(m.b_axis[bb], sn, cs, Rj, dRj);
+    const double* Ro = m.b_Roff[bb];
+    double th = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        th += (Ro[i] * rl[j] + Ro[3 + i] * rl[3 + j] + Ro[6 + i] * rl[6 + j]) * dRj[3 * i + j];
+    qb[qa] += th;
+  }
+  g.sync();
   for (int i = g.lane; i < nq; i += G) qbar[i] += qb[i];
   for (int i = g.lane; i < nv; i += G) vbar[i] += vb[i];
   for (int a = g.lane; a < m.nu; a += G) ubar[a] += ub[a];
