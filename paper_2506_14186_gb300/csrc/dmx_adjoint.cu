@@ -35,7 +35,7 @@ namespace dmx {
 
 constexpr int ADJ_WARPS = 2;          // warps (environments) per block
 constexpr int ADJ_WS = 4096;          // per-lane workspace (derivative scalars)
-constexpr int ADJ_WI = 192;           // per-lane workspace (ints)
+constexpr int ADJ_WI = 512;           // per-lane workspace (ints)
 
 __device__ __forceinline__ double adj_boundary(double T, int NI, int k) { return k >= NI ? T : T * k / NI; }
 __device__ __forceinline__ int adj_interval(double T, int NI, double t) {

@@ -39,11 +39,23 @@ namespace dmx {
 template <int G>
 struct Grp {
   int lane;
+  int base;                          // first warp lane of the group
   unsigned mask;
   __device__ Grp() {
     const int l = threadIdx.x & 31;
     lane = l & (G - 1);
-    mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (l & ~(G - 1)));
+    base = l & ~(G - 1);
+    mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+  }
+  // bit k: predicate of the group's lane k
+  __device__ unsigned ballot(bool p) const {
+    const unsigned b = __ballot_sync(mask, p);
+    return G == 32 ? b : (b >> base) & ((1u << G) - 1u);
+  }
+  __device__ unsigned ior(unsigned x) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x |= __shfl_xor_sync(mask, x, o);
+    return x;
   }
   __device__ void sync() const {
     if (G > 1) __syncwarp(mask);
@@ -192,64 +204,148 @@ struct WsT {
 };
 using Ws = WsT<double>;
 
+// Entry e (row-major) of the rotation of the quaternion x (w, x, y, z) with
+// s = 2 / |x|^2 (the normalisation folded into the products).
+template <class T>
+__device__ __forceinline__ T quat_entry(const T* x, const T& s, int e) {
+  const T w = x[0], a = x[1], b = x[2], c = x[3];
+  switch (e) {
+    case 0: return 1.0 - (s * b * b + s * c * c);
+    case 1: return s * a * b - s * w * c;
+    case 2: return s * a * c + s * w * b;
+    case 3: return s * a * b + s * w * c;
+    case 4: return 1.0 - (s * a * a + s * c * c);
+    case 5: return s * b * c - s * w * a;
+    case 6: return s * a * c - s * w * b;
+    case 7: return s * b * c + s * w * a;
+    default: return 1.0 - (s * a * a + s * b * b);
+  }
+}
+// Entry (i, j) of the hinge rotation about the unit axis a by the angle with
+// sine sn and cosine cs (Rodrigues: I + sin K + (1 - cos) K^2, K = [a]x).
+template <class T>
+__device__ __forceinline__ T hinge_entry(const double* a, const T& sn, const T& cs, int i, int j) {
+  const T c1 = 1.0 - cs;
+  T v = c1 * a[i] * a[j];
+  if (i == j) return cs + v;
+  const int k = 3 - i - j;                       // the third axis
+  const bool pos = (j == nxt3(i));               // K_ij = -a_k for j = i + 1 (cyclic), else +a_k
+  return pos ? v - sn * a[k] : v + sn * a[k];
+}
+
 // Kinematics: body poses, COMs, dof motion vectors, body spatial inertias, geom poses.
-// The per-body work runs for all bodies at once (local joint transforms, then
-// COMs, inertias and motion vectors from the world poses); only the
-// composition of the poses along the tree is sequential over the tree levels
-// (one 3x3 product and one 3-vector per body and level).
+// Work is split into small tasks so that a group's lanes stay busy even for a
+// single body: per-body scalars (hinge sine and cosine, the free joint's
+// quaternion normalisation), then every entry of every local transform, then
+// the composition along the tree level by level (one entry per task), then
+// COMs, geom poses and dof motion vectors, then spatial inertias.
 template <int G, class T>
 __device__ void kinematics(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* q) {
   const Layout& L = *w.L;
   T* R = w.at(L.R); T* P = w.at(L.p); T* C = w.at(L.com);
   T* S = w.at(L.sd); T* Ib = w.at(L.Ib);
-  // local transforms: free joint = world pose; hinge = rotation in the parent frame
-  for (int b = g.lane; b < m.nbody; b += G) {
-    T* Rb = R + 9 * b; T* pb = P + 3 * b;
+  T* X = w.at(L.xl); T* SC = w.at(L.sc);
+  const int nb = m.nbody;
+  for (int b = g.lane; b < nb; b += G) {
+    const T* x = q + m.b_qadr[b];
     if (m.b_jtype[b] == JNT_FREE) {
-      const T* x = q + m.b_qadr[b];
-      pb[0] = x[0]; pb[1] = x[1]; pb[2] = x[2];
-      quat_to_mat(x + 3, Rb);
+      SC[2 * b] = 2.0 / (x[3] * x[3] + x[4] * x[4] + x[5] * x[5] + x[6] * x[6]);
     } else {
       T sn, cs;
-      sincos(q[m.b_qadr[b]], &sn, &cs);
-      const double* a = m.b_axis[b];
-      const T c1 = 1.0 - cs;
-      // Rodrigues: I + sin K + (1 - cos) K^2, K = [a]x
-      T Rj[9];
-      Rj[0] = cs + c1 * a[0] * a[0];           Rj[1] = c1 * a[0] * a[1] - sn * a[2]; Rj[2] = c1 * a[0] * a[2] + sn * a[1];
-      Rj[3] = c1 * a[0] * a[1] + sn * a[2];    Rj[4] = cs + c1 * a[1] * a[1];        Rj[5] = c1 * a[1] * a[2] - sn * a[0];
-      Rj[6] = c1 * a[0] * a[2] - sn * a[1];    Rj[7] = c1 * a[1] * a[2] + sn * a[0]; Rj[8] = cs + c1 * a[2] * a[2];
-      matmul3(m.b_Roff[b], Rj, Rb);
-      pb[0] = m.b_pos[b][0]; pb[1] = m.b_pos[b][1]; pb[2] = m.b_pos[b][2];
+      sincos(x[0], &sn, &cs);
+      SC[2 * b] = sn; SC[2 * b + 1] = cs;
     }
   }
   g.sync();
-  // world poses: R = R_parent R_local, p = p_parent + R_parent b_pos
+  // local transforms: free joint = world pose; hinge = rotation in the parent frame.
+  // Bodies at the root are written straight into the world arrays.
+  for (int t = g.lane; t < 12 * nb; t += G) {
+    const int b = t / 12, e = t - 12 * b;
+    const bool root = m.b_parent[b] < 0;
+    T v;
+    if (m.b_jtype[b] == JNT_FREE) {
+      const T* x = q + m.b_qadr[b];
+      v = e < 9 ? quat_entry(x + 3, SC[2 * b], e) : x[e - 9];
+    } else if (e >= 9) {
+      v = m.b_pos[b][e - 9];
+    } else {
+      const int i = e / 3, j = e - 3 * (e / 3);
+      const T sn = SC[2 * b], cs = SC[2 * b + 1];
+      if (m.b_ident[b]) {
+        v = hinge_entry(m.b_axis[b], sn, cs, i, j);
+      } else {
+        const double* Ro = m.b_Roff[b];
+        v = Ro[3 * i] * hinge_entry(m.b_axis[b], sn, cs, 0, j) + Ro[3 * i + 1] * hinge_entry(m.b_axis[b], sn, cs, 1, j) +
+            Ro[3 * i + 2] * hinge_entry(m.b_axis[b], sn, cs, 2, j);
+      }
+    }
+    if (root) { if (e < 9) R[9 * b + e] = v; else P[3 * b + e - 9] = v; }
+    else X[12 * b + e] = v;
+  }
+  g.sync();
+  // world poses: R = R_parent R_local, p = p_parent + R_parent p_local
   for (int lev = 1; lev < m.nlevel; ++lev) {
-    for (int k = m.level_start[lev] + g.lane; k < m.level_start[lev + 1]; k += G) {
-      const int b = m.level_list[k];
-      const int par = m.b_parent[b];
-      if (par < 0 || m.b_jtype[b] == JNT_FREE) continue;
-      T* Rb = R + 9 * b; T* pb = P + 3 * b;
-      const T* Rp = R + 9 * par;
-      T Rl[9], t[3];
-      for (int i = 0; i < 9; ++i) Rl[i] = Rb[i];
-      matmul3(Rp, Rl, Rb);
-      matvec3(Rp, pb, t);
-      pb[0] = P[3 * par] + t[0]; pb[1] = P[3 * par + 1] + t[1]; pb[2] = P[3 * par + 2] + t[2];
+    for (int t = 12 * m.level_start[lev] + g.lane; t < 12 * m.level_start[lev + 1]; t += G) {
+      const int k = t / 12, e = t - 12 * k;
+      const int b = m.level_list[k], par = m.b_parent[b];
+      const T* Rp = R + 9 * par; const T* xl = X + 12 * b;
+      if (e < 9) {
+        const int i = e / 3, j = e - 3 * (e / 3);
+        R[9 * b + e] = Rp[3 * i] * xl[j] + Rp[3 * i + 1] * xl[3 + j] + Rp[3 * i + 2] * xl[6 + j];
+      } else {
+        const int i = e - 9;
+        P[3 * b + i] = P[3 * par + i] + (Rp[3 * i] * xl[9] + Rp[3 * i + 1] * xl[10] + Rp[3 * i + 2] * xl[11]);
+      }
     }
     g.sync();
   }
-  // COMs
-  for (int b = g.lane; b < m.nbody; b += G) {
-    T c[3];
-    matvec3(R + 9 * b, m.b_com[b], c);
-    C[3 * b] = c[0] + P[3 * b]; C[3 * b + 1] = c[1] + P[3 * b + 1]; C[3 * b + 2] = c[2] + P[3 * b + 2];
+  // COMs (one component per task), geom poses (one entry per task), dof
+  // motion vectors (w; v at the world origin, one dof per task)
+  T* gR = w.at(L.gR); T* gp = w.at(L.gp);
+  const int n1 = 3 * nb, n2 = n1 + 12 * m.ngeom, n3 = n2 + m.nv;
+  for (int t = g.lane; t < n3; t += G) {
+    if (t < n1) {
+      const int b = t / 3, i = t - 3 * b;
+      const T* Rb = R + 9 * b; const double* c = m.b_com[b];
+      C[t] = (Rb[3 * i] * c[0] + Rb[3 * i + 1] * c[1] + Rb[3 * i + 2] * c[2]) + P[t];
+    } else if (t < n2) {
+      const int gi = (t - n1) / 12, e = t - n1 - 12 * gi;
+      const int b = m.g_body[gi];
+      const T* Rb = R + 9 * b;
+      if (e < 9) {
+        const int i = e / 3, j = e - 3 * (e / 3);
+        const double* Ro = m.g_Roff[gi];
+        gR[9 * gi + e] = m.g_ident[gi] ? Rb[e] : Rb[3 * i] * Ro[j] + Rb[3 * i + 1] * Ro[3 + j] + Rb[3 * i + 2] * Ro[6 + j];
+      } else {
+        const int i = e - 9;
+        const double* gpos = m.g_pos[gi];
+        gp[3 * gi + i] = m.g_zpos[gi] ? P[3 * b + i]
+                                      : P[3 * b + i] + (Rb[3 * i] * gpos[0] + Rb[3 * i + 1] * gpos[1] + Rb[3 * i + 2] * gpos[2]);
+      }
+    } else {
+      const int i = t - n2;
+      const int b = m.dof_body[i];
+      const T* Rb = R + 9 * b; const T* pb = P + 3 * b;
+      T* st = S + 6 * i;
+      if (m.b_jtype[b] == JNT_FREE) {
+        const int d = i - m.b_vadr[b];
+        if (d < 3) {
+          st[0] = 0.0; st[1] = 0.0; st[2] = 0.0; st[3] = d == 0 ? 1.0 : 0.0; st[4] = d == 1 ? 1.0 : 0.0;
+          st[5] = d == 2 ? 1.0 : 0.0;
+        } else {
+          st[0] = Rb[d - 3]; st[1] = Rb[d]; st[2] = Rb[d + 3];
+          cross3(pb, st, st + 3);
+        }
+      } else {
+        matvec3(Rb, m.b_axis[b], st);
+        cross3(pb, st, st + 3);
+      }
+    }
   }
   g.sync();
   // spatial inertias about the world origin (m, m c, R diag(I) R^T + m (|c|^2 1 - c c^T)),
   // one entry per task
-  for (int k = g.lane; k < 10 * m.nbody; k += G) {
+  for (int k = g.lane; k < 10 * nb; k += G) {
     const int b = k / 10, e = k - 10 * b;
     const double ms = m.b_mass[b];
     const T* c = C + 3 * b;
@@ -266,33 +362,6 @@ __device__ void kinematics(const Grp<G>& g, const DevModel& m, const WsT<T>& w, 
       v += ms * ((i == j ? cc : T(0.0)) - c[i] * c[j]);
     }
     Ib[10 * b + e] = v;
-  }
-  // dof motion vectors (w; v at the world origin), one dof per task
-  for (int i = g.lane; i < m.nv; i += G) {
-    const int b = m.dof_body[i];
-    const T* Rb = R + 9 * b; const T* pb = P + 3 * b;
-    T* st = S + 6 * i;
-    if (m.b_jtype[b] == JNT_FREE) {
-      const int d = i - m.b_vadr[b];
-      if (d < 3) {
-        st[0] = 0.0; st[1] = 0.0; st[2] = 0.0; st[3] = d == 0 ? 1.0 : 0.0; st[4] = d == 1 ? 1.0 : 0.0;
-        st[5] = d == 2 ? 1.0 : 0.0;
-      } else {
-        st[0] = Rb[d - 3]; st[1] = Rb[d]; st[2] = Rb[d + 3];
-        cross3(pb, st, st + 3);
-      }
-    } else {
-      matvec3(Rb, m.b_axis[b], st);
-      cross3(pb, st, st + 3);
-    }
-  }
-  T* gR = w.at(L.gR); T* gp = w.at(L.gp);
-  for (int gi = g.lane; gi < m.ngeom; gi += G) {
-    const int b = m.g_body[gi];
-    matmul3(R + 9 * b, m.g_Roff[gi], gR + 9 * gi);
-    T t[3];
-    matvec3(R + 9 * b, m.g_pos[gi], t);
-    gp[3 * gi] = P[3 * b] + t[0]; gp[3 * gi + 1] = P[3 * b + 1] + t[1]; gp[3 * gi + 2] = P[3 * b + 2] + t[2];
   }
   g.sync();
 }
@@ -595,7 +664,9 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, boo
       ct[4] = 0.0; ct[5] = 0.0; ct[6] = 1.0; ct[7] = 1.0; ct[8] = 0.0; ct[9] = 0.0; ct[10] = 0.0; ct[11] = 1.0;
       ct[12] = 0.0;
     }
-    if (value(ct[0]) < thr) {
+    const bool inc = value(ct[0]) < thr;
+    w.i[L.sinc + s] = inc ? 1 : 0;
+    if (inc) {
       const T r = ct[0];
       const T d = impedance(m, r, cfd);
       const int pr = m.s_pair[s];
@@ -615,14 +686,20 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const WsT<T>& w, co
   const Layout& L = *w.L;
   const T* CT = w.at(L.ct); const T* S = w.at(L.sd);
   int* slotrow = w.i + L.slotrow; int* rowid = w.i + L.rowid; int* slist = w.i + L.slist;
-  const double thr = cfd ? m.cfd[2] : 0.0;
   const int nv = m.nv;
+  int* rowslot = w.i + L.rowslot;
+  const int* sinc = w.i + L.sinc;
   if (g.lane == 0) {
     int n = 0, ns = 0;
     for (int s = 0; s < m.nslot; ++s) {
-      const bool inc = value(CT[16 * s]) < thr;
+      const bool inc = sinc[s] != 0;
       slotrow[s] = inc ? n : -1;
-      if (inc) { n += (m.p_condim[m.s_pair[s]] == 1) ? 1 : 4; slist[ns++] = s; }
+      if (inc) {
+        const int nrow = (m.p_condim[m.s_pair[s]] == 1) ? 1 : 4;
+        for (int e = 0; e < nrow && n + e < L.rcap; ++e) rowslot[n + e] = s;
+        n += nrow;
+        slist[ns++] = s;
+      }
     }
     slotrow[m.nslot] = n;
     w.i[L.misc] = ns;
@@ -650,7 +727,11 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const WsT<T>& w, co
       cross3(sv, ct + 1, pv);
       pv[0] += sv[3]; pv[1] += sv[4]; pv[2] += sv[5];
       const double sg = mA ? 1.0 : -1.0;
-      jn = sg * dot3(ct + 4, pv); j1 = sg * dot3(ct + 7, pv); j2 = sg * dot3(ct + 10, pv);
+      if (bB < 0) {   // ground plane: the frame is the world's (z, x, y)
+        jn = sg * pv[2]; j1 = sg * pv[0]; j2 = sg * pv[1];
+      } else {
+        jn = sg * dot3(ct + 4, pv); j1 = sg * dot3(ct + 7, pv); j2 = sg * dot3(ct + 10, pv);
+      }
     }
     if (m.p_condim[p] == 1) {
       J[r0 * nv + i] = jn;
@@ -664,22 +745,20 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const WsT<T>& w, co
   }
   g.sync();
   T* aref = w.at(L.aref); T* Dr = w.at(L.Dr);
-  for (int si = g.lane; si < nincl; si += G) {
-    const int s = slist[si];
-    const int r0 = slotrow[s];
+  for (int r = g.lane; r < nr; r += G) {   // one row per task
+    const int s = rowslot[r];
+    const int e = r - slotrow[s];
     const int p = m.s_pair[s];
     const int nrow = m.p_condim[p] == 1 ? 1 : 4;
     const T* ct = CT + 16 * s;
-    for (int e = 0; e < nrow; ++e) {
-      const int r = r0 + e;
-      T jv = 0.0;
-      for (int i = 0; i < nv; ++i) jv += J[r * nv + i] * v[i];
-      aref[r] = -(m.bcoef * jv) + ct[14];
-      Dr[r] = ct[15];
-      rowid[r] = m.p_row0[p] + m.s_idx[s] * nrow + e;
-    }
+    T jv = 0.0;
+    for (int i = 0; i < nv; ++i) jv += J[r * nv + i] * v[i];
+    aref[r] = -(m.bcoef * jv) + ct[14];
+    Dr[r] = ct[15];
+    rowid[r] = m.p_row0[p] + m.s_idx[s] * nrow + e;
   }
   g.sync();
+  (void)nincl;
   return nr;
 }
 
@@ -735,19 +814,37 @@ __device__ bool solve_active(const Grp<G>& g, const DevModel& m, const WsT<T>& w
   const T* J = w.at(L.J); const T* aref = w.at(L.aref); const T* Dr = w.at(L.Dr);
   const T* rhs0 = w.at(L.rhs0); T* an = w.at(L.an);
   const int* rowid = w.i + L.rowid;
-  for (int idx = g.lane; idx < nv * nv; idx += G) {
-    const int i = idx / nv, j = idx - i * nv;
-    if (j > i) continue;
-    T h = M[idx];
-    for (int r = 0; r < nr; ++r)
-      if (mask_has(act, rowid[r])) h += Dr[r] * J[r * nv + i] * J[r * nv + j];
-    H[idx] = h;
+  int* alist = w.i + L.alist;
+  // compacted list of the active rows (in row order)
+  int na = 0;
+  for (int r0 = 0; r0 < nr; r0 += G) {
+    const int r = r0 + g.lane;
+    const bool a = r < nr && mask_has(act, rowid[r]);
+    const unsigned bits = g.ballot(a);
+    if (a) alist[na + __popc(bits & ((1u << g.lane) - 1u))] = r;
+    na += __popc(bits);
   }
-  for (int i = g.lane; i < nv; i += G) {
-    T b = rhs0[i];
-    for (int r = 0; r < nr; ++r)
-      if (mask_has(act, rowid[r])) b += Dr[r] * aref[r] * J[r * nv + i];
-    an[i] = b;
+  g.sync();
+  // lower triangle of H, then b: one entry per task
+  const int ntri = nv * (nv + 1) / 2;
+  for (int t = g.lane; t < ntri + nv; t += G) {
+    if (t < ntri) {
+      const int i = c_tri[t][0], j = c_tri[t][1];
+      T h = M[i * nv + j];
+      for (int k = 0; k < na; ++k) {
+        const int r = alist[k];
+        h += Dr[r] * J[r * nv + i] * J[r * nv + j];
+      }
+      H[i * nv + j] = h;
+    } else {
+      const int i = t - ntri;
+      T b = rhs0[i];
+      for (int k = 0; k < na; ++k) {
+        const int r = alist[k];
+        b += Dr[r] * aref[r] * J[r * nv + i];
+      }
+      an[i] = b;
+    }
   }
   g.sync();
   const bool ok = cholesky(g, H, w.at(L.tmp2), nv);
@@ -763,15 +860,16 @@ __device__ void residual_set(const Grp<G>& g, const DevModel& m, const WsT<T>& w
   const T* J = w.at(L.J); const T* aref = w.at(L.aref);
   T* z = w.at(L.z);
   const int* rowid = w.i + L.rowid;
+  unsigned bits[MASKW] = {0u, 0u, 0u, 0u};
   for (int r = g.lane; r < nr; r += G) {
     T t = 0.0;
     for (int i = 0; i < nv; ++i) t += J[r * nv + i] * a[i];
-    z[r] = t - aref[r];
+    const T zr = t - aref[r];
+    z[r] = zr;
+    if (value(zr) < 0) bits[rowid[r] >> 5] |= 1u << (rowid[r] & 31);
   }
+  for (int k = 0; k < MASKW; ++k) newmask[k] = (int)g.ior(bits[k]);
   g.sync();
-  for (int k = 0; k < MASKW; ++k) newmask[k] = 0;
-  for (int r = 0; r < nr; ++r)
-    if (value(z[r]) < 0) newmask[rowid[r] >> 5] |= 1 << (rowid[r] & 31);
 }
 
 // Exact line search along d = an - a: minimiser over alpha >= 0 of the convex
@@ -906,8 +1004,8 @@ __device__ int solve_constraints(const Grp<G>& g, const DevModel& m, const WsT<T
 
 // v' = F(q, v, u) (or F~ with cfd) into out[nv].  Returns 0 or an ENV_* code.
 template <int G, class T>
-__device__ int rhs(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* q, const T* v, const T* u, bool cfd,
-                   T* out) {
+__device__ int rhs(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T* q, const T* v,
+                                const T* u, bool cfd, T* out) {
   const Layout& L = *w.L;
   kinematics(g, m, w, q);
   crba(g, m, w);

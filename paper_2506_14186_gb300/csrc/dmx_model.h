@@ -41,6 +41,7 @@ struct DevModel {
   unsigned b_anc[MAXB];              // bit j: body j is this body or an ancestor
   double b_pos[MAXB][3], b_Roff[MAXB][9], b_axis[MAXB][3];
   double b_mass[MAXB], b_com[MAXB][3], b_inertia[MAXB][3], b_damping[MAXB];
+  int b_ident[MAXB];                 // 1: b_Roff is exactly the identity
   int child_start[MAXB], child_count[MAXB], child_list[MAXB];
   int level_start[MAXLEV + 1], level_list[MAXB];
   int dof_body[MAXV];
@@ -48,6 +49,7 @@ struct DevModel {
   int g_type[MAXG], g_body[MAXG];
   double g_pos[MAXG][3], g_Roff[MAXG][9], g_size[MAXG][3];
   double g_bound[MAXG];              // bounding-sphere radius about the geom centre
+  int g_ident[MAXG], g_zpos[MAXG];   // 1: g_Roff is exactly the identity / g_pos is exactly zero
   // pairs and slots
   int p_g1[MAXP], p_g2[MAXP], p_condim[MAXP], p_slot0[MAXP], p_nslot[MAXP], p_row0[MAXP];
   double p_mu[MAXP], p_ahat[MAXP], p_ahat_edge[MAXP];
@@ -64,7 +66,9 @@ struct Layout {
   int M, H, rhs0, a, an, tmp, tmp2;
   int ct, J, aref, Dr, z, s, u;
   int nd;                            // doubles per environment (padded to even)
+  int xl, sc;                        // kinematics scratch, aliases of Ab..Fb (12 per body) and iv (2 per body)
   int rowid, slotrow, slist, amask, pmask, misc;
+  int sinc, rowslot, alist;          // slot included (0/1), slot of each row, compacted active rows
   int ni;                            // ints per environment
   int rcap;                          // constraint-row capacity
 };
@@ -79,6 +83,9 @@ DMX_HD inline Layout make_layout(const DevModel& m, int rcap) {
   L.R = take(9 * nb); L.p = take(3 * nb); L.com = take(3 * nb); L.sd = take(6 * nv);
   L.Ib = take(10 * nb); L.Ic = take(10 * nb); L.F = take(6 * nv);
   L.Vb = take(6 * nb); L.Ab = take(6 * nb); L.Fb = take(6 * nb); L.iv = take(6 * nb);
+  // the bias-force arrays are free while the kinematics run: local transforms
+  // (Ab and Fb are contiguous, 12 per body) and per-body scalars (iv)
+  L.xl = L.Ab; L.sc = L.iv;
   L.gR = take(9 * ng); L.gp = take(3 * ng);
   L.M = take(nv * nv); L.H = take(nv * nv);
   L.rhs0 = take(nv); L.a = take(nv); L.an = take(nv); L.tmp = take(nv); L.tmp2 = take(nv);
@@ -91,6 +98,7 @@ DMX_HD inline Layout make_layout(const DevModel& m, int rcap) {
   L.rowid = takei(rcap); L.slotrow = takei(ns + 1); L.slist = takei(ns); L.amask = takei(MASKW);
   L.pmask = takei(MASKW);
   L.misc = takei(8);
+  L.sinc = takei(ns); L.rowslot = takei(rcap); L.alist = takei(rcap);
   L.ni = (i + 3) & ~3;
   L.rcap = rcap;
   return L;

@@ -61,6 +61,12 @@ static void quat_mat(const double* q0, double* R) {
   R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
 }
 
+static int is_identity(const double* R) {
+  for (int i = 0; i < 9; ++i)
+    if (R[i] != ((i % 4 == 0) ? 1.0 : 0.0)) return 0;
+  return 1;
+}
+
 static std::string compile_model(const dmx_model_desc* d, DevModel& m) {
   std::memset(&m, 0, sizeof(m));
   if (d->nbody < 1 || d->nbody > MAXB) return "nbody must be in [1, " + std::to_string(MAXB) + "]";
@@ -83,6 +89,7 @@ static std::string compile_model(const dmx_model_desc* d, DevModel& m) {
     m.nv += m.b_nv[b];
     for (int i = 0; i < 3; ++i) { m.b_pos[b][i] = B.pos[i]; m.b_com[b][i] = B.com[i]; m.b_inertia[b][i] = B.inertia[i]; }
     quat_mat(B.quat, m.b_Roff[b]);
+    m.b_ident[b] = is_identity(m.b_Roff[b]);
     double an = std::sqrt(B.axis[0] * B.axis[0] + B.axis[1] * B.axis[1] + B.axis[2] * B.axis[2]);
     if (B.joint == DMX_JNT_HINGE && !(an > 0)) return "hinge axis must be non-zero";
     for (int i = 0; i < 3; ++i) m.b_axis[b][i] = an > 0 ? B.axis[i] / an : 0.0;
@@ -120,6 +127,8 @@ static std::string compile_model(const dmx_model_desc* d, DevModel& m) {
     m.g_type[g] = G.type; m.g_body[g] = G.body;
     for (int i = 0; i < 3; ++i) { m.g_pos[g][i] = G.pos[i]; m.g_size[g][i] = G.size[i]; }
     quat_mat(G.quat, m.g_Roff[g]);
+    m.g_ident[g] = is_identity(m.g_Roff[g]);
+    m.g_zpos[g] = G.pos[0] == 0.0 && G.pos[1] == 0.0 && G.pos[2] == 0.0;
     if (G.type == DMX_GEOM_SPHERE) m.g_bound[g] = G.size[0];
     else if (G.type == DMX_GEOM_CAPSULE) m.g_bound[g] = G.size[0] + G.size[1];
     else m.g_bound[g] = std::sqrt(G.size[0] * G.size[0] + G.size[1] * G.size[1] + G.size[2] * G.size[2]);
