@@ -64,7 +64,7 @@ enum { DMX_GEOM_SPHERE = 0, DMX_GEOM_CAPSULE = 1, DMX_GEOM_BOX = 2 };
 enum { DMX_ACT_MOTOR = 0, DMX_ACT_POSITION = 1 };
 enum { DMX_FORM_PERSISTENT = 0, DMX_FORM_STEP = 1, DMX_FORM_STEP_GRAPH = 2 };
 /* adjoint kernels of dmx_rollout_grad (dmx_set_adjoint) */
-enum { DMX_ADJ_REVERSE = 0, DMX_ADJ_TANGENT = 1 };
+enum { DMX_ADJ_REVERSE = 0, DMX_ADJ_TANGENT = 1, DMX_ADJ_RECOMPUTE = 2 };
 
 /* ------------------------------------------------------------------ model */
 /* Body of a kinematic tree.  parent < own index (-1 = world).  A free joint
@@ -176,9 +176,16 @@ dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* tape, int32_t cfd, const dou
  *   DMX_ADJ_REVERSE (default): reverse mode, a group of lanes per environment
  *     (lanes from dmx_set_lanes(m, B, 2, G), G in {2, 4, 8, 16, 32}, else a
  *     default that fills the SMs); per accepted step it transposes the
- *     Dormand-Prince stages with one right-hand-side VJP per stage.  An
- *     environment whose right-hand side overflowed the row workspace during
- *     the adjoint gets NaN in x0_bar.
+ *     Dormand-Prince stages with one right-hand-side VJP per stage.  With
+ *     cfd = 0 the workspace of every stage's right-hand side is kept in
+ *     library device memory while a segment between two checkpoints is
+ *     recomputed (K steps x 6 stages per resident environment, used when it
+ *     fits 1/8 of the free device memory and 8 GiB), so each stage is
+ *     evaluated once; otherwise as DMX_ADJ_RECOMPUTE.  An environment whose
+ *     right-hand side overflowed the row workspace during the adjoint gets
+ *     NaN in x0_bar.
+ *   DMX_ADJ_RECOMPUTE: the same reverse mode, evaluating each stage's
+ *     right-hand side again during the reverse sweep (no stage snapshots).
  *   DMX_ADJ_TANGENT: forward-mode derivative scalars, one warp per
  *     environment and one input direction per lane (the Jacobian of every
  *     step, column by column); kept as an independent check.

@@ -28,7 +28,7 @@ c_i32, c_f64, c_p = ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
 DMX_OK, DMX_ERR_INVALID, DMX_ERR_OOM, DMX_ERR_CUDA, DMX_NOT_READY, DMX_ERR_TIMEOUT, DMX_ERR_UNIMPLEMENTED = range(7)
 ENV_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "nonfinite", 4: "solver_noconv", 5: "row_overflow"}
 FORMS = {"persistent": 0, "step": 1, "graph": 2}
-ADJOINT_MODES = {"reverse": 0, "tangent": 1}
+ADJOINT_MODES = {"reverse": 0, "tangent": 1, "recompute": 2}
 _JOINT = {"free": 0, "hinge": 1}
 _GEOM = {"sphere": 0, "capsule": 1, "box": 2}
 _ACT = {"motor": 0, "position": 1}
@@ -190,7 +190,9 @@ class Model:
         _check(lib().dmx_set_lanes(self.h, int(B), int(grad), int(lanes)))
 
     def set_adjoint(self, mode):
-        """Adjoint kernel of rollout_grad: "reverse" (default) or "tangent"."""
+        """Adjoint kernel of rollout_grad: "reverse" (default; stage snapshots in
+        device memory when they fit), "recompute" (reverse mode evaluating each
+        stage's right-hand side again) or "tangent" (forward-mode columns)."""
         _check(lib().dmx_set_adjoint(self.h, ADJOINT_MODES[mode]))
 
 

@@ -21,8 +21,33 @@ struct AdjParams {
   double* x0_bar;         // [nx][B]
   double* ctrl_bar;       // [NI][nu][B] or null
   double* segbuf;         // per warp (tangent) or group (reverse): recomputed steps of a segment
+  double* snapbuf;        // reverse mode: per group, K steps x 6 stage snapshots of SN doubles (or null)
+  int SN;                 // doubles per snapshot
   int* queue;             // next environment
 };
+
+// Offsets (doubles) of one stage snapshot: the part of a right-hand-side
+// workspace that its VJP reads (poses .. geom frames, the Cholesky factor of
+// the final Newton system with the solution, contact records, the used
+// Jacobian rows with D and the residuals, then as ints: status, rows,
+// slot->row map, row ids, final active set).
+struct SnapOff {
+  int n1, o2, n2, o3, o4, o5, o6, oi, size;
+};
+__host__ __device__ inline SnapOff snap_offsets(const DevModel& m, const Layout& L) {
+  SnapOff o{};
+  o.n1 = L.gp + 3 * m.ngeom - L.R;
+  o.o2 = o.n1;
+  o.n2 = L.tmp2 + m.nv - L.H;
+  o.o3 = o.o2 + o.n2;
+  o.o4 = o.o3 + 16 * m.nslot;
+  o.o5 = o.o4 + L.rcap * m.nv;
+  o.o6 = o.o5 + L.rcap;
+  o.oi = o.o6 + L.rcap;
+  const int nints = 3 + m.nslot + L.rcap + MASKW;
+  o.size = (o.oi + (nints + 1) / 2 + 1) & ~1;
+  return o;
+}
 
 cudaError_t launch_adjoint(const AdjParams& P, int blocks, cudaStream_t st);
 // reverse-mode kernel, G lanes per environment (G = 2, 4, 8, 16, 32)

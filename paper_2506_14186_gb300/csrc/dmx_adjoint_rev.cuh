@@ -15,6 +15,16 @@
 // come from a forward recompute of the segment between two checkpoints (the
 // tape holds the state every K accepted steps), stored per step in a
 // per-group buffer: q_n, V_0..V_5 and t_n.
+//
+// Without the CFD right-hand side (cfd = 0) the reverse sweep needs the
+// right-hand sides that the segment recompute already evaluated (same stage
+// states, same inputs).  When P.snapbuf is given, the recompute copies the
+// part of each stage's workspace that the VJP reads to device memory
+// (K steps x 6 stages per group) and the reverse sweep restores it instead of
+// evaluating the right-hand side a second time: device memory traded for
+// FP64 work.  The final active set of a stage does not depend on the
+// warm start of its Newton search, so the restored workspace equals a
+// recomputed one.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -33,12 +43,52 @@ __device__ __forceinline__ int rev_interval(double T, int NI, double t) {
 // Doubles per recomputed step in the segment buffer: q_n, V_0..V_5, t_n.
 __host__ __device__ __forceinline__ int rev_row(const DevModel& m) { return m.nq + 6 * m.nv + 1; }
 
+// Workspace of the right-hand side just evaluated (status st) -> snapshot dst.
+template <int G>
+__device__ void snap_save(const Grp<G>& g, const DevModel& m, const Ws& w, double* dst, int st) {
+  const Layout& L = *w.L;
+  const SnapOff o = snap_offsets(m, L);
+  const int nr = (st == ENV_ROW_OVERFLOW) ? 0 : w.i[L.slotrow + m.nslot];
+  const double* d = w.d;
+  for (int i = g.lane; i < o.n1; i += G) dst[i] = d[L.R + i];
+  for (int i = g.lane; i < o.n2; i += G) dst[o.o2 + i] = d[L.H + i];
+  for (int i = g.lane; i < 16 * m.nslot; i += G) dst[o.o3 + i] = d[L.ct + i];
+  for (int i = g.lane; i < nr * m.nv; i += G) dst[o.o4 + i] = d[L.J + i];
+  for (int i = g.lane; i < nr; i += G) { dst[o.o5 + i] = d[L.Dr + i]; dst[o.o6 + i] = d[L.z + i]; }
+  int* di = reinterpret_cast<int*>(dst + o.oi);
+  if (g.lane == 0) { di[0] = st; di[1] = nr; }
+  for (int i = g.lane; i <= m.nslot; i += G) di[2 + i] = w.i[L.slotrow + i];
+  for (int i = g.lane; i < nr; i += G) di[3 + m.nslot + i] = w.i[L.rowid + i];
+  for (int i = g.lane; i < MASKW; i += G) di[3 + m.nslot + L.rcap + i] = w.i[L.amask + i];
+}
+// Snapshot src -> workspace (the state rhs() leaves for rhs_vjp); returns the status.
+template <int G>
+__device__ int snap_restore(const Grp<G>& g, const DevModel& m, const Ws& w, const double* src) {
+  const Layout& L = *w.L;
+  const SnapOff o = snap_offsets(m, L);
+  const int* si = reinterpret_cast<const int*>(src + o.oi);
+  const int st = si[0], nr = si[1];
+  double* d = w.d;
+  for (int i = g.lane; i < o.n1; i += G) d[L.R + i] = src[i];
+  for (int i = g.lane; i < o.n2; i += G) d[L.H + i] = src[o.o2 + i];
+  for (int i = g.lane; i < 16 * m.nslot; i += G) d[L.ct + i] = src[o.o3 + i];
+  for (int i = g.lane; i < nr * m.nv; i += G) d[L.J + i] = src[o.o4 + i];
+  for (int i = g.lane; i < nr; i += G) { d[L.Dr + i] = src[o.o5 + i]; d[L.z + i] = src[o.o6 + i]; }
+  for (int i = g.lane; i <= m.nslot; i += G) w.i[L.slotrow + i] = si[2 + i];
+  for (int i = g.lane; i < nr; i += G) w.i[L.rowid + i] = si[3 + m.nslot + i];
+  for (int i = g.lane; i < MASKW; i += G) w.i[L.amask + i] = si[3 + m.nslot + L.rcap + i];
+  g.sync();
+  return st;
+}
+
 // (qnb, vnb, ub) = transposed step map applied to (Qb, Vb) = the cotangent of
 // (q_{n+1}, v_{n+1}); reads q_n from b.qn and V_0..V_5 from b.vst.  Qb and Vb
-// are consumed (left zero).  Returns the worst right-hand-side status.
+// are consumed (left zero).  snaps: the step's 6 stage snapshots (SN doubles
+// each), or null to evaluate each stage's right-hand side.  Returns the worst
+// right-hand-side status.
 template <int G>
 __device__ int dopri5_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const WsB& b, const double* u,
-                               double h, bool cfd) {
+                               double h, bool cfd, const double* snaps, int SN) {
   const Layout& L = *w.L;
   const LayoutBar& LB = *b.L;
   const int nv = m.nv;
@@ -72,7 +122,8 @@ __device__ int dopri5_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, 
     }
     if (s <= 5) {
       const double* Vs = vst + s * nv;
-      const int r = rhs(g, m, w, (const double*)Qs, Vs, u, cfd, w.at(L.ka));
+      const int r = snaps ? snap_restore(g, m, w, snaps + (size_t)s * SN)
+                          : rhs(g, m, w, (const double*)Qs, Vs, u, cfd, w.at(L.ka));
       if (r > st) st = r;
       rhs_vjp(g, m, w, b, Qs, Vs, u, cfd, r, kab + s * nv, Qb, Vb, ub);
       for (int i = g.lane; i < nv; i += G) Vb[i] += kvb[s * nv + i];   // K^v_s = V_s
@@ -107,7 +158,7 @@ __device__ int dopri5_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, 
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) k_adjoint_rev(AdjParams P) {
+__global__ void __launch_bounds__(32, 1) k_adjoint_rev(AdjParams P) {
   extern __shared__ double smem[];
   __shared__ Layout sL;
   __shared__ LayoutBar sB;
@@ -122,6 +173,9 @@ __global__ void __launch_bounds__(256) k_adjoint_rev(AdjParams P) {
   const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
   const int RW = rev_row(m);
   double* seg = P.segbuf + (size_t)(blockIdx.x * ngb + gib) * P.K * RW;
+  const bool use_snap = P.snapbuf != nullptr && P.cfd == 0;
+  const int SN = P.SN;
+  double* snb = use_snap ? P.snapbuf + (size_t)(blockIdx.x * ngb + gib) * P.K * 6 * SN : nullptr;
   double* qn = w.at(sL.qn); double* vn = w.at(sL.vn); double* u = w.at(sL.u); double* ka = w.at(sL.ka);
   double* xbar = b.at(sB.xb);
   for (;;) {
@@ -147,12 +201,19 @@ __global__ void __launch_bounds__(256) k_adjoint_rev(AdjParams P) {
       int k = rev_interval(T, P.NI, t);
       for (int a = g.lane; a < nu; a += G) u[a] = P.ctrl[((size_t)k * nu + a) * P.B + env];
       g.sync();
-      rhs(g, m, w, (const double*)qn, (const double*)vn, (const double*)u, false, ka);
+      {
+        const int st0 = rhs(g, m, w, (const double*)qn, (const double*)vn, (const double*)u, false, ka);
+        if (use_snap) snap_save(g, m, w, snb, st0);
+      }
       for (int n = n0; n < n1; ++n) {
         double* row = seg + (size_t)(n - n0) * RW;
         const double h = P.hlog[(size_t)n * P.B + env];
-        int st;
-        dopri5_attempt(g, m, w, (const double*)u, h, 1.0, 1.0, &st);
+        double* sn_step = use_snap ? snb + (size_t)(n - n0) * 6 * SN : nullptr;
+        double* sn_next = (use_snap && n + 1 < n1) ? sn_step + (size_t)6 * SN : nullptr;
+        dopri5_stages(g, m, w, (const double*)u, h, [&](int s, int r) {
+          if (s <= 5) { if (sn_step) snap_save(g, m, w, sn_step + (size_t)s * SN, r); }
+          else if (sn_next) snap_save(g, m, w, sn_next, r);   // stage 6 = stage 0 of the next step
+        });
         const double* kv = w.at(sL.kv);
         for (int i = g.lane; i < nq; i += G) row[i] = qn[i];
         for (int i = g.lane; i < 6 * nv; i += G) row[nq + i] = kv[i];
@@ -170,7 +231,8 @@ __global__ void __launch_bounds__(256) k_adjoint_rev(AdjParams P) {
           ++k;
           for (int a = g.lane; a < nu; a += G) u[a] = P.ctrl[((size_t)k * nu + a) * P.B + env];
           g.sync();
-          rhs(g, m, w, (const double*)qn, (const double*)vn, (const double*)u, false, ka);
+          const int stb = rhs(g, m, w, (const double*)qn, (const double*)vn, (const double*)u, false, ka);
+          if (sn_next) snap_save(g, m, w, sn_next, stb);   // the new control's stage 0
         }
       }
       __threadfence_block();
@@ -194,7 +256,8 @@ __global__ void __launch_bounds__(256) k_adjoint_rev(AdjParams P) {
         for (int i = g.lane; i < nq; i += G) Qb[i] = xbar[i];
         for (int i = g.lane; i < nv; i += G) Vb[i] = xbar[nq + i];
         g.sync();
-        const int st = dopri5_step_vjp(g, m, w, b, (const double*)u, h, P.cfd != 0);
+        const int st = dopri5_step_vjp(g, m, w, b, (const double*)u, h, P.cfd != 0,
+                                       use_snap ? snb + (size_t)(n - n0) * 6 * SN : nullptr, SN);
         if (st > worst) worst = st;
         const double* qnb = b.at(sB.qnb); const double* vnb = b.at(sB.vnb); const double* ub = b.at(sB.ub);
         for (int i = g.lane; i < nq; i += G) xbar[i] = qnb[i];
@@ -219,7 +282,7 @@ __global__ void __launch_bounds__(256) k_adjoint_rev(AdjParams P) {
 // u [nu][B], abar [nv][B]) into qbar [nq][B], vbar [nv][B], ubar [nu][B]
 // (ubar only when nu > 0); status [B] = rhs status.
 template <int G>
-__global__ void __launch_bounds__(256) k_eval_rhs_vjp(AdjParams P, const double* q, const double* v, const double* u,
+__global__ void __launch_bounds__(32) k_eval_rhs_vjp(AdjParams P, const double* q, const double* v, const double* u,
                                                       const double* abar, double* qbar, double* vbar, double* ubar,
                                                       int* status) {
   extern __shared__ double smem[];

@@ -1080,12 +1080,13 @@ __device__ __forceinline__ double pos_mag(const DevModel& m, const double* q, in
   return d < 3 ? fabs(q[m.b_qadr[b] + d]) : 1.0;
 }
 
-// One DOPRI5 attempt of size h from (qn, vn) with ka[0] = F(qn, vn).  Leaves
-// the 5th-order solution in (qs, vs) and its derivative in ka[6]; returns the
-// RMS error norm (NaN-safe: non-finite -> +inf) and the worst stage status.
-template <int G>
-__device__ double dopri5_attempt(const Grp<G>& g, const DevModel& m, const Ws& w, const double* u, double h,
-                                 double rtol, double atol, int* st_out) {
+// The six new stages of a DOPRI5 step of size h from (qn, vn) with
+// ka[0] = F(qn, vn): stage velocities kv[s], derivatives ka[s], the
+// 5th-order solution in (qs, vs) and its derivative in ka[6].  hook(s, status)
+// runs after the right-hand side of stage s (the workspace then holds that
+// evaluation).  Returns the worst stage status.
+template <int G, class Hook>
+__device__ int dopri5_stages(const Grp<G>& g, const DevModel& m, const Ws& w, const double* u, double h, Hook&& hook) {
   const Layout& L = *w.L;
   const int nv = m.nv;
   const double* qn = w.at(L.qn); const double* vn = w.at(L.vn);
@@ -1112,7 +1113,23 @@ __device__ double dopri5_attempt(const Grp<G>& g, const DevModel& m, const Ws& w
     integrate_pos(g, m, qn, dq, qs);
     const int r = rhs(g, m, w, qs, vs, u, false, ka + s * nv);
     if (r > st) st = r;
+    hook(s, r);
   }
+  return st;
+}
+
+// One DOPRI5 attempt of size h from (qn, vn) with ka[0] = F(qn, vn).  Leaves
+// the 5th-order solution in (qs, vs) and its derivative in ka[6]; returns the
+// RMS error norm (NaN-safe: non-finite -> +inf) and the worst stage status.
+template <int G>
+__device__ double dopri5_attempt(const Grp<G>& g, const DevModel& m, const Ws& w, const double* u, double h,
+                                 double rtol, double atol, int* st_out) {
+  const Layout& L = *w.L;
+  const int nv = m.nv;
+  const double* qn = w.at(L.qn); const double* vn = w.at(L.vn);
+  const double* qs = w.at(L.qs); const double* vs = w.at(L.vs);
+  const double* kv = w.at(L.kv); const double* ka = w.at(L.ka);
+  const int st = dopri5_stages(g, m, w, u, h, [](int, int) {});
   double acc = 0;
   for (int i = g.lane; i < nv; i += G) {
     double ep = 0, ev = 0;

@@ -489,6 +489,9 @@ extern "C" dmx_status dmx_set_lanes(dmx_model* m, int32_t B, int32_t grad, int32
 
 static bool valid_adj_lanes(int G) { return G == 2 || G == 4 || G == 8 || G == 16 || G == 32; }
 
+// Upper bound of the reverse adjoint's stage-snapshot buffer per call.
+constexpr size_t kSnapMaxBytes = size_t(8) << 30;
+
 // Threads and shared memory of the reverse-mode adjoint kernel for G lanes.
 // (one warp per block, as for the forward kernels)
 static bool adj_launch_config(const dmx_model* m, const dmx::LayoutBar& LB, int G, int* threads, size_t* smem) {
@@ -519,7 +522,8 @@ static int adjoint_lanes(dmx_model* m, int B) {
 }
 
 extern "C" dmx_status dmx_set_adjoint(dmx_model* m, int32_t mode) {
-  if (!m || (mode != DMX_ADJ_REVERSE && mode != DMX_ADJ_TANGENT)) return dmx_fail(DMX_ERR_INVALID, "bad argument");
+  if (!m || (mode != DMX_ADJ_REVERSE && mode != DMX_ADJ_TANGENT && mode != DMX_ADJ_RECOMPUTE))
+    return dmx_fail(DMX_ERR_INVALID, "bad argument");
   std::lock_guard<std::mutex> lk(m->mu);
   m->adj_mode = mode;
   return DMX_OK;
@@ -570,10 +574,21 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
   blocks = std::min(blocks, m->nsm * occ);
   const int RW = m->host.nq + 6 * m->host.nv + 1;
   const size_t seg_bytes = sizeof(double) * (size_t)blocks * gpb * t->K * RW;
+  // stage snapshots (forward right-hand side only): used when they fit a
+  // share of the free device memory, else each stage is evaluated again
+  size_t snap_bytes = 0;
+  if (mode == DMX_ADJ_REVERSE && !cfd) {
+    P.SN = dmx::snap_offsets(m->host, m->L).size;
+    snap_bytes = sizeof(double) * (size_t)blocks * gpb * t->K * 6 * (size_t)P.SN;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || snap_bytes > free_b / 8 || snap_bytes > kSnapMaxBytes)
+      snap_bytes = 0;
+  }
   void* scratch = nullptr;
-  CK(cudaMallocAsync(&scratch, seg_bytes + 256, st));
+  CK(cudaMallocAsync(&scratch, seg_bytes + snap_bytes + 256, st));
   P.segbuf = static_cast<double*>(scratch);
-  P.queue = reinterpret_cast<int*>(static_cast<char*>(scratch) + seg_bytes);
+  P.snapbuf = snap_bytes ? reinterpret_cast<double*>(static_cast<char*>(scratch) + seg_bytes) : nullptr;
+  P.queue = reinterpret_cast<int*>(static_cast<char*>(scratch) + seg_bytes + snap_bytes);
   CK(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
   CK(dmx::launch_adjoint_rev(G, P, blocks, threads, smem, st));
   CK(cudaFreeAsync(scratch, st));

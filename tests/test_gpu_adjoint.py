@@ -72,7 +72,7 @@ def assert_grad(g, o, key="x0_bar"):
     return err
 
 
-MODES = ["reverse", "tangent"]
+MODES = ["reverse", "recompute", "tangent"]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -261,3 +261,7 @@ def test_reverse_kernel_equals_tangent_kernel(dmx, name):
         b = res["tangent"][k].cpu().numpy().reshape(-1, len(inp["T"])).T
         err = max(rel_err(a[e], b[e]) for e in range(len(a)))
         assert err < 0.1 * TOL, err
+        # stage snapshots restore exactly what a second evaluation computes
+        # (the final active set, hence the Newton system, is the same)
+        c = res["recompute"][k].cpu().numpy().reshape(-1, len(inp["T"])).T
+        np.testing.assert_array_equal(a, c)
