@@ -53,7 +53,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the plain-form and CPU-baseline legs")
     p.add_argument("--serving", action="store_true", help="served-request latency benchmark instead of the rollout bench")
     p.add_argument("--grad-only", action="store_true", help="only the fwd+adjoint leg (one JSON line)")
-    p.add_argument("--grad-envs", type=int, default=2048, help="environments of the fwd+adjoint leg")
+    p.add_argument("--grad-envs", type=int, default=16384, help="environments of the fwd+adjoint leg")
+    p.add_argument("--all", action="store_true", help="every workload (forward, fwd+adjoint, CPU oracle samples)")
     p.add_argument("--adj-lanes", type=int, default=0, help="lanes per environment of the adjoint (0 = autotuned)")
     p.add_argument("--requests", type=int, default=40)
     p.add_argument("--warmup-requests", type=int, default=5)
@@ -299,11 +300,11 @@ def run_ours(args):
     return result
 
 
-def grad_leg(dmx, dev, B=2048, adj_lanes=0):
+def grad_leg(dmx, dev, B=16384, adj_lanes=0):
     """Forward (taped) + discrete adjoint (reverse-mode kernel, autotuned lanes)
     of the arm-pushes-cube workload (7 hinges + free cube, 50 torque intervals
-    over 2 s, K = 32), loss = squared cube-to-goal distance, on a bounded
-    sample (the first B) of the 16384 environments."""
+    over 2 s, K = 32), loss = squared cube-to-goal distance, on the first B of
+    the 16384 environments (all of them by default)."""
     import torch
     from paper_2506_14186_gb300 import autotune
     from paper_2506_14186_gb300 import workloads as W
@@ -334,11 +335,161 @@ def grad_leg(dmx, dev, B=2048, adj_lanes=0):
     e2.synchronize()
     t_f, t_all = e0.elapsed_time(e1) * 1e-3, e0.elapsed_time(e2) * 1e-3
     steps = int(out["nsteps"].sum().item())
-    return {"workload": "chain_cube (7 hinges + cube, NI=50, T=2 s, K=32)", "sample_envs": B,
+    return {"workload": "chain_cube (7 hinges + cube, NI=50, T=2 s, K=32)", "envs": B,
             "grad_rollouts_per_s": B / t_all, "env_steps_per_s": steps / t_all, "forward_s": t_f,
             "adjoint_s": t_all - t_f, "env_steps": steps, "adjoint_kernel": "reverse",
             "lanes": {"forward": fwd_lanes, "adjoint": adj_lanes, "adjoint_tuning_ms": adj_ms},
             "finite": bool(torch.isfinite(gu).all().item())}
+
+
+# ------------------------------------------------------------------ every workload
+def _events_time(fn):
+    import torch
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    r = fn()
+    e1.record(st)
+    e1.synchronize()
+    return r, e0.elapsed_time(e1) * 1e-3
+
+
+def _oracle_fwd(scene, inp, n):
+    """Oracle batch rollout of the first n environments on all host cores: (env-steps/s, seconds)."""
+    import oracle
+    m = oracle.OracleModel(scene)
+    ctrl = None if inp["ctrl"] is None else inp["ctrl"][:n]
+    t0 = time.perf_counter()
+    r = m.batch_rollout(inp["x0"][:n], inp["T"][:n], ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"], atol=inp["atol"],
+                        h0=inp["h0"], max_steps=inp["max_steps"])
+    dt = time.perf_counter() - t0
+    return float(r["nsteps"].sum()) / dt, dt
+
+
+def _oracle_grad(scene, inp, n, xT_bar):
+    """Oracle forward + discrete adjoint of the first n environments: (grad-rollouts/s, seconds)."""
+    import oracle
+    m = oracle.OracleModel(scene)
+    ctrl = None if inp["ctrl"] is None else inp["ctrl"][:n]
+    t0 = time.perf_counter()
+    m.batch_grad(inp["x0"][:n], inp["T"][:n], xT_bar[:n], ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"], atol=inp["atol"],
+                 h0=inp["h0"], max_steps=inp["max_steps"])
+    dt = time.perf_counter() - t0
+    return n / dt, dt
+
+
+def run_all(args):
+    """Forward and fwd+adjoint rates of the four rollout workloads at their
+    stated batch sizes (the quadruped adjoint on its first 2048 environments),
+    with the CPU oracle timed on bounded samples."""
+    import torch
+
+    import paper_2506_14186_gb300 as dmx
+    from paper_2506_14186_gb300 import _build, autotune
+    from paper_2506_14186_gb300 import workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cores = os.cpu_count() or 1
+
+    def d(a):
+        return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    def tensors(inp, n):
+        ctrl = None if inp["ctrl"] is None else d(np.transpose(inp["ctrl"][:n], (1, 2, 0)))
+        return d(inp["x0"][:n].T), d(inp["T"][:n]), ctrl
+
+    def forward(m, inp, n, reps=3):
+        x0, T, ctrl = tensors(inp, n)
+        kw = dict(ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"], atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"])
+        lanes, tuned = autotune.tune_forward(m, x0, torch.clamp(T, max=0.25), **kw)
+        best, out = 1e30, None
+        for _ in range(reps):
+            out, t = _events_time(lambda: dmx.rollout(m, x0, T, lanes=lanes, **kw))
+            best = min(best, t)
+        steps = int(out["nsteps"].sum().item())
+        assert int((out["status"] != 0).sum().item()) == 0
+        return {"envs": n, "env_steps": steps, "s": best, "env_steps_per_s": steps / best, "lanes": lanes}
+
+    def gradient(m, inp, n, xT_bar_fn, K=None):
+        x0, T, ctrl = tensors(inp, n)
+        kw = dict(ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"], atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"])
+        fl, _ = autotune.tune_forward(m, x0, torch.clamp(T, max=0.25), **kw)
+        al, _ = autotune.tune_adjoint(m, x0, T, K=K or 32, **kw)
+        tuned_k = None
+        if K is None:
+            K, tuned_k = autotune.tune_checkpoint(m, x0, T, **kw)
+        m.set_lanes(n, fl)
+
+        def fwd_adj():
+            out = dmx.rollout(m, x0, T, K=K, tape=True, **kw)
+            return out, dmx.rollout_grad(out["tape"], xT_bar_fn(out))
+        if n <= 4096:
+            _events_time(fwd_adj)                        # warm-up (large batches are warm from the tuning)
+        (out, (gx, gu)), t = _events_time(fwd_adj)
+        steps = int(out["nsteps"].sum().item())
+        return {"envs": n, "env_steps": steps, "s": t, "grad_rollouts_per_s": n / t, "env_steps_per_s": steps / t,
+                "K": K, "K_tuning_ms": tuned_k, "lanes": {"forward": fl, "adjoint": al},
+                "finite": bool(torch.isfinite(gx).all().item())}
+
+    res = {}
+    rng = np.random.default_rng(0)
+    # 1. bouncing balls, B = 16: forward; gradient of the final height w.r.t. the state (v0 entries)
+    sc, inp = W.ball_scene(), W.ball_inputs(16)
+    m = dmx.Model(sc)
+
+    def height_bar(out):
+        b = torch.zeros_like(out["xT"])
+        b[2] = 1.0
+        return b
+    xb = np.zeros((16, 13)); xb[:, 2] = 1.0
+    r = {"forward": forward(m, inp, 16), "fwd_adjoint": gradient(m, inp, 16, height_bar, K=32)}
+    rate, sec = _oracle_fwd(sc, inp, 16)
+    grate, gsec = _oracle_grad(sc, inp, 16, xb)
+    r["cpu_oracle"] = {"env_steps_per_s": rate, "grad_rollouts_per_s": grate, "cores": cores, "sample": "all 16"}
+    res["ball_B16"] = r
+    # 2. box pushes, B = 4096: forward in the three launch forms
+    sc, inp = W.box_scene(), W.box_push_inputs(4096)
+    m = dmx.Model(sc)
+    r = {"forward": forward(m, inp, 4096)}
+    x0, T, _ = tensors(inp, 4096)
+    for form in ("graph", "step"):
+        out, t = _events_time(lambda: dmx.rollout(m, x0, T, lanes=r["forward"]["lanes"], form=form, rtol=inp["rtol"],
+                                                  atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"]))
+        r[f"forward_{form}"] = {"s": t, "env_steps_per_s": int(out["nsteps"].sum().item()) / t}
+    rate, sec = _oracle_fwd(sc, inp, 512)
+    r["cpu_oracle"] = {"env_steps_per_s": rate, "cores": cores, "sample": "first 512 of 4096"}
+    res["box_push_B4096"] = r
+    # 3. arm pushes cube, B = 16384: forward; forward + adjoint of the squared cube-to-goal distance (K = 32)
+    sc, inp = W.chain_cube_scene(), W.chain_inputs(16384)
+    m = dmx.Model(sc)
+    goal = torch.tensor(W.chain_goal(), device=dev)[:, None]
+
+    def goal_bar(out):
+        b = torch.zeros_like(out["xT"])
+        b[7:10] = 2 * (out["xT"][7:10] - goal)
+        return b
+    r = {"forward": forward(m, inp, 16384, reps=1), "fwd_adjoint": gradient(m, inp, 16384, goal_bar, K=32)}
+    rate, sec = _oracle_fwd(sc, inp, 64)
+    gb = np.zeros((4, 27)); gb[:, 7:10] = 1.0
+    grate, gsec = _oracle_grad(sc, inp, 4, gb)
+    r["cpu_oracle"] = {"env_steps_per_s": rate, "grad_rollouts_per_s": grate, "cores": cores,
+                       "sample": "forward: first 64 of 16384; gradient: first 4"}
+    res["chain_cube_B16384"] = r
+    # 4. quadruped, B = 8192: forward; forward + adjoint (autotuned lanes and K) on the first 2048
+    sc, inp = W.quadruped_scene(), W.quadruped_inputs(8192)
+    m = dmx.Model(sc)
+
+    def torso_bar(out):
+        b = torch.zeros_like(out["xT"])
+        b[0:3] = 1.0
+        return b
+    r = {"forward": forward(m, inp, 8192, reps=1), "fwd_adjoint": gradient(m, inp, 2048, torso_bar)}
+    rate, sec = _oracle_fwd(sc, inp, 64)
+    r["cpu_oracle"] = {"env_steps_per_s": rate, "cores": cores, "sample": "forward: first 64 of 8192"}
+    res["quadruped_B8192"] = r
+    return {"metric": METRIC, "impl": "ours", "dtype": "f64", "data": "synthetic (seeded)", "all": res}
 
 
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
@@ -478,6 +629,9 @@ def main():
     args = parse()
     if args.serving:
         print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.all:
+        print(json.dumps(run_all(args)), flush=True)
         return
     if args.grad_only:
         import torch

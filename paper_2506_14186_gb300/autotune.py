@@ -5,7 +5,9 @@ caller's own inputs (CUDA events, after one warm-up run); the fastest is
 recorded in the library (dmx_set_lanes) so that later calls with lanes = 0 use
 it.  Results are cached per process by (scene name, B, kind).  The adjoint
 kernel is timed on the caller's batch over a short horizon (its lane choice
-depends on the batch size and the model, not on the step count).
+depends on the batch size and the model, not on the step count).  The
+checkpoint interval K of the tape is chosen the same way: taped forward plus
+adjoint timed for each candidate K.
 """
 
 from __future__ import annotations
@@ -78,5 +80,40 @@ def tune_adjoint(model, x0, T, ctrl=None, NI=1, horizon=0.1, candidates=ADJ_LANE
         times[G] = e0.elapsed_time(e1)
     best = min(times, key=times.get)
     model.set_lanes(B, best, grad=2)
+    _cache[key] = (best, times)
+    return best, times
+
+
+K_CANDIDATES = (8, 16, 32, 64)
+
+
+def tune_checkpoint(model, x0, T, ctrl=None, NI=1, horizon=0.2, candidates=K_CANDIDATES, **kw):
+    """Times a taped forward rollout plus its adjoint (current lane choices)
+    for each candidate checkpoint interval K on the caller's batch with
+    horizons capped at `horizon` seconds; returns (best_K, {K: ms}).  A K
+    whose tape or adjoint scratch does not fit is skipped."""
+    import torch
+    B = x0.shape[1]
+    key = (model.scene.get("name"), B, "K")
+    if key in _cache:
+        return _cache[key]
+    Tc = torch.clamp(T, max=horizon)
+    times = {}
+    for K in candidates:
+        try:
+            out = dmx.rollout(model, x0, Tc, ctrl=ctrl, NI=NI, K=K, tape=True, **kw)   # warm-up (and fit check)
+            dmx.rollout_grad(out["tape"], torch.ones_like(out["xT"]))
+        except dmx.DmxError:
+            continue
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        out = dmx.rollout(model, x0, Tc, ctrl=ctrl, NI=NI, K=K, tape=True, **kw)
+        dmx.rollout_grad(out["tape"], torch.ones_like(out["xT"]))
+        e1.record(st)
+        e1.synchronize()
+        times[K] = e0.elapsed_time(e1)
+    best = min(times, key=times.get)
     _cache[key] = (best, times)
     return best, times

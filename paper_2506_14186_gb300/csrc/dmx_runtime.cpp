@@ -521,6 +521,20 @@ static int adjoint_lanes(dmx_model* m, int B) {
   return G;
 }
 
+size_t adjoint_scratch_bound(dmx_model* m, int B, int K, int cfd) {
+  int mode;
+  {
+    std::lock_guard<std::mutex> lk(m->mu);
+    mode = m->adj_mode;
+  }
+  const size_t groups = (size_t)std::max(B, 1), k = (size_t)std::max(K, 1);
+  const size_t nx = m->host.nq + m->host.nv;
+  size_t b = sizeof(double) * groups * k * std::max<size_t>(m->host.nq + 6 * m->host.nv + 1, nx + 1);
+  if (mode == DMX_ADJ_REVERSE && !cfd)
+    b += std::min(kSnapMaxBytes, sizeof(double) * groups * k * 6 * (size_t)dmx::snap_offsets(m->host, m->L).size);
+  return b + 256;
+}
+
 extern "C" dmx_status dmx_set_adjoint(dmx_model* m, int32_t mode) {
   if (!m || (mode != DMX_ADJ_REVERSE && mode != DMX_ADJ_TANGENT && mode != DMX_ADJ_RECOMPUTE))
     return dmx_fail(DMX_ERR_INVALID, "bad argument");

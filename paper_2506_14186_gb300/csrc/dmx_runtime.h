@@ -49,6 +49,10 @@ int default_lanes(const dmx_model* m, int B);
 int tuned_lanes(dmx_model* m, int B, int grad);
 dmx_status run_rollout(dmx_model* m, const dmx::RolloutParams& P, int form, int G, cudaStream_t st);
 int model_smem_bytes(const dmx_model* m, int groups);
+// Upper bound of the device scratch that dmx_rollout_grad allocates for B
+// environments with checkpoint interval K (segment buffers and, for the
+// reverse kernel without CFD, the stage snapshots).
+size_t adjoint_scratch_bound(dmx_model* m, int B, int K, int cfd);
 
 namespace dmx {
 int persistent_occupancy(int G, int threads, size_t smem);

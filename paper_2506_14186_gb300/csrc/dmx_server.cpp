@@ -75,9 +75,10 @@ static size_t request_bytes(const dmx_request& r) {
     const size_t K = r.K > 0 ? r.K : 32;
     d += B * nx * 2 + (size_t)r.NI * nu * B;             // xT_bar, x0_bar, ctrl_bar
     d += (size_t)(r.max_steps / K + 2) * (nx + 1) * B + (size_t)r.max_steps * B + (size_t)r.NI * nu * B + B;  // tape
-    d += 2 * 152 * 8 * K * (nx + 1);                     // adjoint segment buffers (upper bound)
   }
-  return d * sizeof(double) + 2 * B * sizeof(int) + 4096;
+  size_t extra = 0;
+  if (r.grad) extra = adjoint_scratch_bound(r.model, r.B, r.K > 0 ? r.K : 32, r.cfd);   // segment buffers, snapshots
+  return d * sizeof(double) + extra + 2 * B * sizeof(int) + 4096;
 }
 
 static void CUDART_CB on_done(void* p) {
