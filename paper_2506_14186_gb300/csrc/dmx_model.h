@@ -109,6 +109,8 @@ DMX_HD inline Layout make_layout(const DevModel& m, int rcap) {
 // the stage data and cotangents of one Dormand-Prince step.
 struct LayoutBar {
   int R, p, cR, cp, S, F, Ib, Ic, V, A, Fb, slot, y, jy, cz, cj, q, v, u;   // right-hand side
+  int gb, iv, ivb;                   // geom pose cotangents, I V and its cotangent per body
+  int sc, tk;                        // hinge sine and cosine, theta-cotangent terms per body
   int qn, vst, dq, dqb, Qs, kab, kvb, Qb, Vb, qnb, vnb, ub, xb;            // one step
   int nd;                            // doubles per environment (padded to even)
 };
@@ -125,6 +127,8 @@ DMX_HD inline LayoutBar make_bar_layout(const DevModel& m, int rcap) {
   B.slot = take(SLOTBAR * ns);
   B.y = take(nv); B.jy = take(rcap); B.cz = take(rcap); B.cj = take(rcap);
   B.q = take(nq); B.v = take(nv); B.u = take(nu);
+  B.gb = take(12 * (m.ngeom > 0 ? m.ngeom : 1)); B.iv = take(6 * nb); B.ivb = take(6 * nb);
+  B.sc = take(2 * nb); B.tk = take(9 * nb);
   B.qn = take(nq); B.vst = take(6 * nv); B.dq = take(nv); B.dqb = take(nv); B.Qs = take(nq);
   B.kab = take(6 * nv); B.kvb = take(6 * nv); B.Qb = take(nq); B.Vb = take(nv);
   B.qnb = take(nq); B.vnb = take(nv); B.ub = take(nu); B.xb = take(nq + nv);

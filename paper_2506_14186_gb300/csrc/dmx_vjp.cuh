@@ -53,6 +53,22 @@ __device__ __forceinline__ void inertia_grad(const double* yb, const double* x, 
   Ibar[4] += yb[0] * w0; Ibar[5] += yb[1] * w1; Ibar[6] += yb[2] * w2;
   Ibar[7] += yb[0] * w1 + yb[1] * w0; Ibar[8] += yb[0] * w2 + yb[2] * w0; Ibar[9] += yb[1] * w2 + yb[2] * w1;
 }
+// Component e of d/dI (ybar . inertia_apply(I, x)) (the terms inertia_grad adds).
+__device__ __forceinline__ double inertia_grad_comp(const double* yb, const double* x, int e) {
+  const double w0 = x[0], w1 = x[1], w2 = x[2], v0 = x[3], v1 = x[4], v2 = x[5];
+  switch (e) {
+    case 0: return yb[3] * v0 + yb[4] * v1 + yb[5] * v2;
+    case 1: return (v1 * yb[2] - v2 * yb[1]) - (w1 * yb[5] - w2 * yb[4]);
+    case 2: return (v2 * yb[0] - v0 * yb[2]) - (w2 * yb[3] - w0 * yb[5]);
+    case 3: return (v0 * yb[1] - v1 * yb[0]) - (w0 * yb[4] - w1 * yb[3]);
+    case 4: return yb[0] * w0;
+    case 5: return yb[1] * w1;
+    case 6: return yb[2] * w2;
+    case 7: return yb[0] * w1 + yb[1] * w0;
+    case 8: return yb[0] * w2 + yb[2] * w0;
+    default: return yb[1] * w2 + yb[2] * w1;
+  }
+}
 // c = a x b (motion): abar, bbar += from cbar.  a = (w; v), b = (w2; v2).
 __device__ __forceinline__ void crm6_vjp(const double* a, const double* b, const double* cb, double* ab, double* bb) {
   acc_cross(b, cb, ab);            // w2 x cw
@@ -439,41 +455,59 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     }
   }
   g.sync();
-  // ---- per body: geom poses -> body pose; bias-force and CRBA cotangents of its dofs
-  for (int bb = g.lane; bb < nb; bb += G) {
-    double* rb = Rb + 9 * bb; double* pbb = pb + 3 * bb;
-    for (int gi = 0; gi < m.ngeom; ++gi) {
-      if (m.g_body[gi] != bb) continue;
-      double gRb[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gpb[3] = {0, 0, 0};
-      for (int s = 0; s < m.nslot; ++s) {
-        if (slotrow[s] < 0) continue;
-        const int p = m.s_pair[s];
-        const double* src = nullptr;
-        if (m.p_g1[p] == gi) src = SB + SLOTBAR * s;
-        else if (m.p_g2[p] == gi) src = SB + SLOTBAR * s + 12;
-        if (!src) continue;
-        for (int k = 0; k < 9; ++k) gRb[k] += src[k];
-        for (int k = 0; k < 3; ++k) gpb[k] += src[9 + k];
-      }
-      // gR = R_b Roff, gp = p_b + R_b gpos
-      const double* Ro = m.g_Roff[gi]; const double* gpos = m.g_pos[gi];
-      for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j)
-          rb[3 * i + j] += gRb[3 * i] * Ro[3 * j] + gRb[3 * i + 1] * Ro[3 * j + 1] + gRb[3 * i + 2] * Ro[3 * j + 2] +
-                           gpb[i] * gpos[j];
-        pbb[i] += gpb[i];
-      }
+  // ---- per geom: pose cotangents gathered from its slots (one component per task)
+  double* GB = b.at(LB.gb);
+  for (int t = g.lane; t < 12 * m.ngeom; t += G) {
+    const int gi = t / 12, c = t - 12 * gi;
+    double acc = 0.0;
+    for (int s = 0; s < m.nslot; ++s) {
+      if (slotrow[s] < 0) continue;
+      const int p = m.s_pair[s];
+      if (m.p_g1[p] == gi) acc += SB[SLOTBAR * s + c];
+      else if (m.p_g2[p] == gi) acc += SB[SLOTBAR * s + 12 + c];
     }
-    const int va = m.b_vadr[bb], nd = m.b_nv[bb];
-    const double* I = Ic + 10 * bb;
-    double* fbb = Fbb + 6 * bb; double* icb = Icb + 10 * bb;
-    for (int d = 0; d < nd; ++d) {
-      const int i = va + d;
-      for (int e = 0; e < 6; ++e) fbb[e] -= y[i] * S[6 * i + e];   // c_i = S_i . Fb
-      inertia_grad(Fd + 6 * i, S + 6 * i, icb);                     // F_i = Ic S_i
-      double t[6];
-      inertia_apply(I, Fd + 6 * i, t);
-      for (int e = 0; e < 6; ++e) Sb[6 * i + e] += t[e];
+    GB[t] = acc;
+  }
+  g.sync();
+  // ---- per body: geom poses -> body pose (gR = R_b Roff, gp = p_b + R_b gpos), one
+  // entry per task; per dof and body component: bias-force (c_i = S_i . Fb) and
+  // CRBA (F_i = Ic S_i) cotangents
+  {
+    const int n1 = 12 * nb, n2 = n1 + 6 * nv, n3 = n2 + 6 * nb, n4 = n3 + 10 * nb;
+    for (int t = g.lane; t < n4; t += G) {
+      if (t < n1) {
+        const int bb = t / 12, c = t - 12 * bb;
+        double acc = 0.0;
+        for (int gi = 0; gi < m.ngeom; ++gi) {
+          if (m.g_body[gi] != bb) continue;
+          const double* gb = GB + 12 * gi;
+          if (c < 9) {
+            const int i = c / 3, j = c - 3 * (c / 3);
+            const double* Ro = m.g_Roff[gi];
+            acc += gb[3 * i] * Ro[3 * j] + gb[3 * i + 1] * Ro[3 * j + 1] + gb[3 * i + 2] * Ro[3 * j + 2] +
+                   gb[9 + i] * m.g_pos[gi][j];
+          } else {
+            acc += gb[c];
+          }
+        }
+        if (c < 9) Rb[9 * bb + c] += acc; else pb[3 * bb + c - 9] += acc;
+      } else if (t < n2) {
+        const int k = t - n1, i = k / 6, e = k - 6 * (k / 6);
+        Sb[6 * i + e] += inertia_comp(Ic + 10 * m.dof_body[i], Fd + 6 * i, e);
+      } else if (t < n3) {
+        const int k = t - n2, bb = k / 6, e = k - 6 * (k / 6);
+        double acc = 0.0;
+        for (int d = 0; d < m.b_nv[bb]; ++d) { const int i = m.b_vadr[bb] + d; acc += y[i] * S[6 * i + e]; }
+        Fbb[6 * bb + e] -= acc;
+      } else {
+        const int k = t - n3, bb = k / 10, e = k - 10 * (k / 10);
+        double acc = 0.0;
+        for (int d = 0; d < m.b_nv[bb]; ++d) {
+          const int i = m.b_vadr[bb] + d;
+          acc += inertia_grad_comp(Fd + 6 * i, S + 6 * i, e);
+        }
+        Icb[10 * bb + e] += acc;
+      }
     }
   }
   g.sync();
@@ -493,19 +527,43 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
   // ---- recursive Newton-Euler (forward: V = V_parent + S v, A = A_parent + (V x S) v,
   // F = I A + V x* (I V)), reversed with the same split: per-body work for all
   // bodies at once, sums along the tree level by level
-  for (int bb = g.lane; bb < nb; bb += G) {      // F's cotangent -> A, V (own terms)
-    const double* vbv = V + 6 * bb; const double* abv = A + 6 * bb; const double* I = Ib + 10 * bb;
-    const double* fbar = Fbb + 6 * bb;
-    double* ibb = Ibb + 10 * bb;
-    double abar6[6], vbar6[6] = {0, 0, 0, 0, 0, 0}, ivb[6] = {0, 0, 0, 0, 0, 0}, iv[6], t[6];
-    inertia_apply(I, fbar, abar6);               // f1 = I ab
-    inertia_grad(fbar, abv, ibb);
-    inertia_apply(I, vbv, iv);                   // f2 = vb x* (I vb)
-    crf6_vjp(vbv, iv, fbar, vbar6, ivb);
-    inertia_apply(I, ivb, t);
-    for (int e = 0; e < 6; ++e) vbar6[e] += t[e];
-    inertia_grad(ivb, vbv, ibb);
-    for (int e = 0; e < 6; ++e) { Vbb[6 * bb + e] = vbar6[e]; Abb[6 * bb + e] = abar6[e]; }
+  // F's cotangent -> A, V (own terms), one body component per task:
+  //   f1 = I A:          Abar = I fbar,  Ibar += grad(fbar, A)
+  //   f2 = V x* (I V):   Vbar and (I V)bar from the force cross product, then
+  //                      Vbar += I (I V)bar,  Ibar += grad((I V)bar, V)
+  double* IV = b.at(LB.iv); double* IVB = b.at(LB.ivb);
+  for (int t = g.lane; t < 6 * nb; t += G) {
+    const int bb = t / 6, e = t - 6 * (t / 6);
+    const double* I = Ib + 10 * bb;
+    Abb[t] = inertia_comp(I, Fbb + 6 * bb, e);
+    IV[t] = inertia_comp(I, V + 6 * bb, e);
+  }
+  g.sync();
+  for (int t = g.lane; t < 6 * nb; t += G) {
+    const int bb = t / 6, e = t - 6 * (t / 6);
+    const double* a = V + 6 * bb; const double* iv = IV + 6 * bb; const double* fbar = Fbb + 6 * bb;
+    const int k = e < 3 ? e : e - 3, k1 = nxt3(k), k2 = prv3(k);
+    // c = a x* iv with a = (w; v), iv = (n; f): c_n = w x n + v x f, c_f = w x f
+    double vb_e, ivb_e;
+    if (e < 3) {
+      vb_e = (iv[k1] * fbar[k2] - iv[k2] * fbar[k1]) + (iv[3 + k1] * fbar[3 + k2] - iv[3 + k2] * fbar[3 + k1]);
+      ivb_e = fbar[k1] * a[k2] - fbar[k2] * a[k1];
+    } else {
+      vb_e = iv[3 + k1] * fbar[k2] - iv[3 + k2] * fbar[k1];
+      ivb_e = (fbar[k1] * a[3 + k2] - fbar[k2] * a[3 + k1]) + (fbar[3 + k1] * a[k2] - fbar[3 + k2] * a[k1]);
+    }
+    Vbb[t] = vb_e;
+    IVB[t] = ivb_e;
+  }
+  g.sync();
+  for (int t = g.lane; t < 16 * nb; t += G) {
+    if (t < 6 * nb) {
+      const int bb = t / 6, e = t - 6 * (t / 6);
+      Vbb[t] += inertia_comp(Ib + 10 * bb, IVB + 6 * bb, e);
+    } else {
+      const int k = t - 6 * nb, bb = k / 10, e = k - 10 * (k / 10);
+      Ibb[10 * bb + e] += inertia_grad_comp(Fbb + 6 * bb, A + 6 * bb, e) + inertia_grad_comp(IVB + 6 * bb, V + 6 * bb, e);
+    }
   }
   g.sync();
   for (int lev = m.nlevel - 1; lev >= 1; --lev) {   // A_child = A_parent + ...: gather into parents
@@ -518,18 +576,48 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     }
     g.sync();
   }
-  for (int bb = g.lane; bb < nb; bb += G) {      // A's own term (V x S_d) v_d
-    const double* vbv = V + 6 * bb; const double* abar6 = Abb + 6 * bb;
-    const int va = m.b_vadr[bb], nd = m.b_nv[bb];
-    const int d0 = (m.b_jtype[bb] == JNT_FREE) ? 3 : 0;
-    for (int d = d0; d < nd; ++d) {
-      const double* sd = S + 6 * (va + d);
-      double cm[6];
-      crm6(vbv, sd, cm);
-      double s1 = 0.0, cb6[6];
-      for (int e = 0; e < 6; ++e) { s1 += abar6[e] * cm[e]; cb6[e] = abar6[e] * v[va + d]; }
-      vb[va + d] += s1;
-      crm6_vjp(vbv, sd, cb6, Vbb + 6 * bb, Sb + 6 * (va + d));
+  // A's own term (V x S_d) v_d (d past the free joint's translations):
+  //   vbar_d += Abar . (V x S_d);  with cb = Abar v_d:  Vbar_w += S_w x cb_w + S_v x cb_v,
+  //   Vbar_v += S_w x cb_v;  Sbar_w += cb_w x V_w + cb_v x V_v,  Sbar_v += cb_v x V_w
+  {
+    const int n1 = nv, n2 = n1 + 6 * nv, n3 = n2 + 6 * nb;
+    for (int t = g.lane; t < n3; t += G) {
+      if (t < n1) {
+        const int i = t, bb = m.dof_body[i];
+        if (m.b_jtype[bb] == JNT_FREE && i - m.b_vadr[bb] < 3) continue;
+        const double* vbv = V + 6 * bb; const double* sd = S + 6 * i; const double* ab6 = Abb + 6 * bb;
+        double s1 = 0.0;
+        for (int e = 0; e < 6; ++e) s1 += ab6[e] * crm_comp(vbv, sd, e);
+        vb[i] += s1;
+      } else if (t < n2) {
+        const int k = t - n1, i = k / 6, e = k - 6 * (k / 6), bb = m.dof_body[i];
+        if (m.b_jtype[bb] == JNT_FREE && i - m.b_vadr[bb] < 3) continue;
+        const double* a = V + 6 * bb; const double* ab6 = Abb + 6 * bb;
+        const double vd = v[i];
+        const int c = e < 3 ? e : e - 3, c1 = nxt3(c), c2 = prv3(c);
+        double r;
+        if (e < 3)
+          r = vd * ((ab6[c1] * a[c2] - ab6[c2] * a[c1]) + (ab6[3 + c1] * a[3 + c2] - ab6[3 + c2] * a[3 + c1]));
+        else
+          r = vd * (ab6[3 + c1] * a[c2] - ab6[3 + c2] * a[c1]);
+        Sb[6 * i + e] += r;
+      } else {
+        const int k = t - n2, bb = k / 6, e = k - 6 * (k / 6);
+        const double* ab6 = Abb + 6 * bb;
+        const int c = e < 3 ? e : e - 3, c1 = nxt3(c), c2 = prv3(c);
+        const int va = m.b_vadr[bb], nd = m.b_nv[bb];
+        const int d0 = (m.b_jtype[bb] == JNT_FREE) ? 3 : 0;
+        double acc = 0.0;
+        for (int d = d0; d < nd; ++d) {
+          const double* sd = S + 6 * (va + d);
+          const double vd = v[va + d];
+          if (e < 3)
+            acc += vd * ((sd[c1] * ab6[c2] - sd[c2] * ab6[c1]) + (sd[3 + c1] * ab6[3 + c2] - sd[3 + c2] * ab6[3 + c1]));
+          else
+            acc += vd * (sd[c1] * ab6[3 + c2] - sd[c2] * ab6[3 + c1]);
+        }
+        Vbb[6 * bb + e] += acc;
+      }
     }
   }
   g.sync();
@@ -543,17 +631,21 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     }
     g.sync();
   }
-  for (int bb = g.lane; bb < nb; bb += G) {      // V's own term S_d v_d
-    const double* vbar6 = Vbb + 6 * bb;
-    const int va = m.b_vadr[bb], nd = m.b_nv[bb];
-    for (int d = 0; d < nd; ++d) {
-      const double* sd = S + 6 * (va + d);
+  // V's own term S_d v_d: vbar_d += Vbar . S_d, Sbar_d += Vbar v_d (per dof, per dof component)
+  for (int t = g.lane; t < 7 * nv; t += G) {
+    if (t < nv) {
+      const int i = t;
+      const double* vbar6 = Vbb + 6 * m.dof_body[i]; const double* sd = S + 6 * i;
       double s1 = 0.0;
-      for (int e = 0; e < 6; ++e) { s1 += vbar6[e] * sd[e]; Sb[6 * (va + d) + e] += vbar6[e] * v[va + d]; }
-      vb[va + d] += s1;
+      for (int e = 0; e < 6; ++e) s1 += vbar6[e] * sd[e];
+      vb[i] += s1;
+    } else {
+      const int k = t - nv, i = k / 6, e = k - 6 * (k / 6);
+      Sb[6 * i + e] += Vbb[6 * m.dof_body[i] + e] * v[i];
     }
   }
   g.sync();
+  // actuators: motor tau += gear u; position servo tau += kp (u - q) - kd v
   if (g.lane == 0) {
     for (int a = 0; a < m.nact; ++a) {
       const int vi = m.a_vadr[a];
@@ -563,109 +655,145 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
   }
   // ---- kinematics (forward: local rotation Rl = Roff Rj(theta) or the free joint's
   // pose; R = R_parent Rl, p = p_parent + R_parent b_pos; then COMs, inertias,
-  // motion vectors and geoms from (R, p)).  Own terms of every body first.
-  for (int bb = g.lane; bb < nb; bb += G) {
-    double* rb = Rb + 9 * bb; double* pbv = pb + 3 * bb;   // geom terms are already in
-    const double* Rv = R + 9 * bb; const double* pv = P + 3 * bb; const double* c = C + 3 * bb;
-    // spatial inertia about the origin: (m, m c, R diag(In) R^T + m (|c|^2 - c c^T))
-    const double ms = m.b_mass[bb];
-    const double* In = m.b_inertia[bb];
-    const double* ib = Ibb + 10 * bb;
-    double cb3[3] = {ms * ib[1], ms * ib[2], ms * ib[3]};
-    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
-    for (int e = 0; e < 6; ++e) {
-      const int i = ii[e], j = jj[e];
-      const double be = ib[4 + e];
-      for (int kk = 0; kk < 3; ++kk) {
-        rb[3 * i + kk] += be * Rv[3 * j + kk] * In[kk];
-        rb[3 * j + kk] += be * Rv[3 * i + kk] * In[kk];
-      }
-      if (i == j) for (int kk = 0; kk < 3; ++kk) cb3[kk] += be * ms * 2.0 * c[kk];
-      cb3[i] -= be * ms * c[j];
-      cb3[j] -= be * ms * c[i];
+  // motion vectors and geoms from (R, p)).  Own terms of every body first, split
+  // into tasks: per body the hinge's sine and cosine and the COM cotangent
+  // (spatial inertia (m, m c, R diag(In) R^T + m (|c|^2 - c c^T)) -> c); then
+  // one pose entry per task (inertia, COM and motion-vector terms) and one
+  // local-rotation entry per task for the composition.
+  double* SCb = b.at(LB.sc); double* TK = b.at(LB.tk);
+  for (int t = g.lane; t < 4 * nb; t += G) {
+    if (t < nb) {
+      if (m.b_jtype[t] == JNT_HINGE) ::sincos(q[m.b_qadr[t]], &SCb[2 * t], &SCb[2 * t + 1]);
+    } else {
+      const int k = t - nb, bb = k / 3, r = k - 3 * (k / 3);
+      const double ms = m.b_mass[bb];
+      const double* ib = Ibb + 10 * bb; const double* c = C + 3 * bb;
+      // Ibar as a symmetric matrix B (diagonal ib[4..6], (0,1) ib[7], (0,2) ib[8], (1,2) ib[9])
+      const double Br[3] = {r == 0 ? 2.0 * ib[4] : (r == 1 ? ib[7] : ib[8]),
+                            r == 0 ? ib[7] : (r == 1 ? 2.0 * ib[5] : ib[9]),
+                            r == 0 ? ib[8] : (r == 1 ? ib[9] : 2.0 * ib[6])};
+      const double tr = ib[4] + ib[5] + ib[6];
+      cp[k] = ms * (ib[1 + r] + 2.0 * c[r] * tr - (Br[0] * c[0] + Br[1] * c[1] + Br[2] * c[2]));
     }
-    // c = R com + p
-    for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) rb[3 * i + j] += cb3[i] * m.b_com[bb][j];
-      pbv[i] += cb3[i];
-    }
-    // dof motion vectors
-    const int va = m.b_vadr[bb];
-    if (m.b_jtype[bb] == JNT_FREE) {
-      for (int d = 0; d < 3; ++d) {
-        const double* sbd = Sb + 6 * (va + 3 + d);
-        const double sr[3] = {Rv[d], Rv[3 + d], Rv[6 + d]};
-        double srb[3] = {sbd[0], sbd[1], sbd[2]};
-        acc_cross(sbd + 3, pv, srb);           // lin = p x sr
-        acc_cross(sr, sbd + 3, pbv);
-        rb[d] += srb[0]; rb[3 + d] += srb[1]; rb[6 + d] += srb[2];
+  }
+  g.sync();
+  for (int t = g.lane; t < 21 * nb; t += G) {
+    if (t < 12 * nb) {
+      const int bb = t / 12, comp = t - 12 * (t / 12);
+      const double* Rv = R + 9 * bb; const double* pv = P + 3 * bb;
+      const double* cb3 = cp + 3 * bb;
+      const int va = m.b_vadr[bb];
+      const bool fr = m.b_jtype[bb] == JNT_FREE;
+      if (comp < 9) {
+        const int r = comp / 3, kk = comp - 3 * (comp / 3);
+        const double* ib = Ibb + 10 * bb;
+        const double Br[3] = {r == 0 ? 2.0 * ib[4] : (r == 1 ? ib[7] : ib[8]),
+                              r == 0 ? ib[7] : (r == 1 ? 2.0 * ib[5] : ib[9]),
+                              r == 0 ? ib[8] : (r == 1 ? ib[9] : 2.0 * ib[6])};
+        double val = m.b_inertia[bb][kk] * (Br[0] * Rv[kk] + Br[1] * Rv[3 + kk] + Br[2] * Rv[6 + kk]);
+        val += cb3[r] * m.b_com[bb][kk];
+        // motion vectors: free angular dof kk = column kk of R (lin = p x col);
+        // hinge: sh = R axis (lin = p x sh)
+        const double* sbd = Sb + 6 * (fr ? va + 3 + kk : va);
+        const int r1 = nxt3(r), r2 = prv3(r);
+        const double wb = sbd[r] + (sbd[3 + r1] * pv[r2] - sbd[3 + r2] * pv[r1]);
+        val += fr ? wb : wb * m.b_axis[bb][kk];
+        Rb[9 * bb + comp] += val;
+      } else {
+        const int r = comp - 9, r1 = nxt3(r), r2 = prv3(r);
+        double val = cb3[r];
+        if (fr) {
+          for (int d = 0; d < 3; ++d) {
+            const double* sv = Sb + 6 * (va + 3 + d) + 3;
+            val += Rv[3 * r1 + d] * sv[r2] - Rv[3 * r2 + d] * sv[r1];
+          }
+        } else {
+          const double* sv = Sb + 6 * va + 3;
+          const double* ax = m.b_axis[bb];
+          const double sh1 = Rv[3 * r1] * ax[0] + Rv[3 * r1 + 1] * ax[1] + Rv[3 * r1 + 2] * ax[2];
+          const double sh2 = Rv[3 * r2] * ax[0] + Rv[3 * r2 + 1] * ax[1] + Rv[3 * r2 + 2] * ax[2];
+          val += sh1 * sv[r2] - sh2 * sv[r1];
+        }
+        pb[3 * bb + r] += val;
       }
     } else {
-      const double* sbd = Sb + 6 * va;
+      const int k = t - 12 * nb, bb = k / 9, e = k - 9 * (k / 9);
+      if (m.b_jtype[bb] != JNT_HINGE) continue;
+      const int i = e / 3, j = e - 3 * (e / 3);
+      const double sn = SCb[2 * bb], cs = SCb[2 * bb + 1];
       const double* ax = m.b_axis[bb];
-      double sh[3];
-      matvec3(Rv, ax, sh);
-      double shb[3] = {sbd[0], sbd[1], sbd[2]};
-      acc_cross(sbd + 3, pv, shb);             // lin = p x sh
-      acc_cross(sh, sbd + 3, pbv);
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) rb[3 * i + j] += shb[i] * ax[j];
-      // the local rotation, for the composition below
-      double Rj[9], dRj[9], sn, cs;
-      ::sincos(q[m.b_qadr[bb]], &sn, &cs);
-      rodrigues(ax, sn, cs, Rj, dRj);
-      matmul3(m.b_Roff[bb], Rj, cR + 9 * bb);
+      double val;
+      if (m.b_ident[bb]) {
+        val = hinge_entry(ax, sn, cs, i, j);
+      } else {
+        const double* Ro = m.b_Roff[bb];
+        val = Ro[3 * i] * hinge_entry(ax, sn, cs, 0, j) + Ro[3 * i + 1] * hinge_entry(ax, sn, cs, 1, j) +
+              Ro[3 * i + 2] * hinge_entry(ax, sn, cs, 2, j);
+      }
+      cR[9 * bb + e] = val;
     }
   }
   g.sync();
   // composition, leaves to root: R_parent gets Rbar Rl^T + pbar b_pos^T, p_parent gets pbar
+  // (one parent entry per task)
   for (int lev = m.nlevel - 1; lev >= 1; --lev) {
-    for (int k = m.level_start[lev - 1] + g.lane; k < m.level_start[lev]; k += G) {
-      const int bb = m.level_list[k];
-      double* rb = Rb + 9 * bb; double* pbv = pb + 3 * bb;
+    for (int t = 12 * m.level_start[lev - 1] + g.lane; t < 12 * m.level_start[lev]; t += G) {
+      const int kb = t / 12, comp = t - 12 * (t / 12);
+      const int bb = m.level_list[kb];
+      double acc = 0.0;
       for (int c = 0; c < m.child_count[bb]; ++c) {
         const int ch = m.child_list[m.child_start[bb] + c];
         if (m.b_jtype[ch] == JNT_FREE) continue;
         const double* rc = Rb + 9 * ch; const double* pc = pb + 3 * ch;
-        const double* Rl = cR + 9 * ch; const double* bp = m.b_pos[ch];
-        for (int i = 0; i < 3; ++i) {
-          for (int j = 0; j < 3; ++j)
-            rb[3 * i + j] += rc[3 * i] * Rl[3 * j] + rc[3 * i + 1] * Rl[3 * j + 1] + rc[3 * i + 2] * Rl[3 * j + 2] +
-                             pc[i] * bp[j];
-          pbv[i] += pc[i];
+        if (comp < 9) {
+          const int i = comp / 3, j = comp - 3 * (comp / 3);
+          const double* Rl = cR + 9 * ch;
+          acc += rc[3 * i] * Rl[3 * j] + rc[3 * i + 1] * Rl[3 * j + 1] + rc[3 * i + 2] * Rl[3 * j + 2] +
+                 pc[i] * m.b_pos[ch][j];
+        } else {
+          acc += pc[comp - 9];
         }
       }
+      if (comp < 9) Rb[9 * bb + comp] += acc; else pb[3 * bb + comp - 9] += acc;
     }
     g.sync();
   }
-  // joint coordinates
-  for (int bb = g.lane; bb < nb; bb += G) {
-    const double* rb = Rb + 9 * bb; const double* pbv = pb + 3 * bb;
-    const int qa = m.b_qadr[bb];
-    if (m.b_jtype[bb] == JNT_FREE) {
+  // joint coordinates: free joints (translation, quaternion), one task per body;
+  // hinges: theta bar = <Roff^T R_parent^T Rbar, dRj/dtheta>, one entry per task
+  for (int t = g.lane; t < 10 * nb; t += G) {
+    if (t < nb) {
+      const int bb = t;
+      if (m.b_jtype[bb] != JNT_FREE) continue;
+      const double* rb = Rb + 9 * bb; const double* pbv = pb + 3 * bb;
+      const int qa = m.b_qadr[bb];
       qb[qa] += pbv[0]; qb[qa + 1] += pbv[1]; qb[qa + 2] += pbv[2];
       quat_to_mat_vjp(q + qa + 3, rb, qb + qa + 3);
-      continue;
-    }
-    // Rl bar = R_parent^T Rbar; Rj bar = Roff^T Rl bar; theta bar = <Rj bar, dRj/dtheta>
-    const int par = m.b_parent[bb];
-    double rl[9];
-    if (par >= 0) {
-      const double* Rp = R + 9 * par;
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) rl[3 * i + j] = Rp[i] * rb[j] + Rp[3 + i] * rb[3 + j] + Rp[6 + i] * rb[6 + j];
     } else {
-      for (int e = 0; e < 9; ++e) rl[e] = rb[e];
+      const int k = t - nb, bb = k / 9, e = k - 9 * (k / 9);
+      if (m.b_jtype[bb] != JNT_HINGE) continue;
+      const int i = e / 3, j = e - 3 * (e / 3);
+      const double* rb = Rb + 9 * bb;
+      const int par = m.b_parent[bb];
+      double rl[3];   // column j of R_parent^T Rbar
+      for (int kk = 0; kk < 3; ++kk)
+        rl[kk] = par >= 0 ? R[9 * par + kk] * rb[j] + R[9 * par + 3 + kk] * rb[3 + j] + R[9 * par + 6 + kk] * rb[6 + j]
+                          : rb[3 * kk + j];
+      const double* Ro = m.b_Roff[bb];
+      const double rjb = Ro[i] * rl[0] + Ro[3 + i] * rl[1] + Ro[6 + i] * rl[2];
+      // dRj/dtheta (i, j) = sin (a_i a_j - delta_ij) + cos K_ij, K = [a]x
+      const double* ax = m.b_axis[bb];
+      const double sn = SCb[2 * bb], cs = SCb[2 * bb + 1];
+      double dr = sn * ax[i] * ax[j];
+      if (i == j) dr -= sn;
+      else dr += (j == nxt3(i)) ? -cs * ax[3 - i - j] : cs * ax[3 - i - j];
+      TK[k] = rjb * dr;
     }
-    double Rj[9], dRj[9], sn, cs;
-    ::sincos(q[qa], &sn, &cs);
-    rodrigues(m.b_axis[bb], sn, cs, Rj, dRj);
-    const double* Ro = m.b_Roff[bb];
-    double th = 0.0;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j)
-        th += (Ro[i] * rl[j] + Ro[3 + i] * rl[3 + j] + Ro[6 + i] * rl[6 + j]) * dRj[3 * i + j];
-    qb[qa] += th;
+  }
+  g.sync();
+  for (int bb = g.lane; bb < nb; bb += G) {
+    if (m.b_jtype[bb] != JNT_HINGE) continue;
+    const double* tk = TK + 9 * bb;
+    qb[m.b_qadr[bb]] += (((tk[0] + tk[1]) + (tk[2] + tk[3])) + ((tk[4] + tk[5]) + (tk[6] + tk[7]))) + tk[8];
   }
   g.sync();
   for (int i = g.lane; i < nq; i += G) qbar[i] += qb[i];
