@@ -40,7 +40,7 @@ __host__ __device__ inline SnapOff snap_offsets(const DevModel& m, const Layout&
   o.o2 = o.n1;
   o.n2 = L.tmp2 + m.nv - L.H;
   o.o3 = o.o2 + o.n2;
-  o.o4 = o.o3 + 16 * m.nslot;
+  o.o4 = o.o3 + 17 * m.nslot;          // contact records, then the capsule-box minimisers
   o.o5 = o.o4 + L.rcap * m.nv;
   o.o6 = o.o5 + L.rcap;
   o.oi = o.o6 + L.rcap;

@@ -512,10 +512,24 @@ __device__ __forceinline__ T box_sdf(const T* y, const double* h, T* grad) {
   grad[k] = value(y[k]) < 0 ? -1.0 : 1.0;
   return qd[k];
 }
+// A number with the sign of the slope of the box distance field along
+// y0 + s wv: outside the box the gradient is (sgn y_i max(|y_i| - h_i, 0))_i
+// divided by the (positive) distance, so the division and the square root
+// are left out; inside it is sgn(y_k) e_k for the axis k of the largest
+// |y_k| - h_k (the same tie rule as box_sdf).
 __device__ __forceinline__ double box_sdf_slope(const double* y0, const double* wv, double s, const double* h) {
-  double y[3] = {y0[0] + s * wv[0], y0[1] + s * wv[1], y0[2] + s * wv[2]}, gr[3];
-  box_sdf(y, h, gr);
-  return gr[0] * wv[0] + gr[1] * wv[1] + gr[2] * wv[2];
+  const double y[3] = {y0[0] + s * wv[0], y0[1] + s * wv[1], y0[2] + s * wv[2]};
+  const double qd[3] = {fabs(y[0]) - h[0], fabs(y[1]) - h[1], fabs(y[2]) - h[2]};
+  if (qd[0] > 0 || qd[1] > 0 || qd[2] > 0) {
+    double num = 0.0;
+    for (int i = 0; i < 3; ++i)
+      if (qd[i] > 0) num += (y[i] < 0 ? -qd[i] : qd[i]) * wv[i];
+    return num;
+  }
+  int k = 0;
+  if (qd[1] > qd[k]) k = 1;
+  if (qd[2] > qd[k]) k = 2;
+  return y[k] < 0 ? -wv[k] : wv[k];
 }
 
 // Minimiser over the capsule axis s in [-Lh, Lh] of the box distance field
@@ -555,7 +569,8 @@ __device__ __forceinline__ double capsule_box_curv(const double* y0v, const doub
 // implicit function theorem (slope = 0 at an interior minimum of the smooth
 // outside field: ds = -d(slope) / (d slope / ds)); elsewhere s is constant.
 template <class T>
-__device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1, int g2, double thr, T* ct) {
+__device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1, int g2, double thr, T* ct,
+                            T* s_out) {
   const double rc = m.g_size[g1][0], Lh = m.g_size[g1][1];
   const double* h = m.g_size[g2];
   const T* R1 = gR + 9 * g1; const T* R2 = gR + 9 * g2;
@@ -570,6 +585,7 @@ __device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1,
   matTvec3(R2, u, wv);
   const double y0v[3] = {value(y0[0]), value(y0[1]), value(y0[2])}, wvv[3] = {value(wv[0]), value(wv[1]), value(wv[2])};
   const double sv = capsule_box_s(y0v, wvv, Lh, h);
+  *s_out = T(sv);
   T s = sv;
   if constexpr (!std::is_same<T, double>::value) {
     const double phi2 = capsule_box_curv(y0v, wvv, sv, Lh, h);
@@ -640,7 +656,7 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, boo
     T* ct = CT + 16 * s;
     const int p = m.s_pair[s], j = m.s_idx[s], g1 = m.p_g1[p];
     if (m.p_g2[p] >= 0) {
-      capsule_box(m, gR, gp, g1, m.p_g2[p], thr, ct);
+      capsule_box(m, gR, gp, g1, m.p_g2[p], thr, ct, w.at(L.csv) + s);
     } else {
       const T* Rg = gR + 9 * g1; const T* cg = gp + 3 * g1;
       T pt[3];

@@ -219,8 +219,9 @@ __device__ __forceinline__ void box_sdf_vjp(const double* y, const double* h, do
 // Capsule-box contact record VJP.  cb: cotangents of (r, pos, n, t1, t2) in
 // cb[0..12] (cb[0] already holds the impedance part of rbar).  Accumulates the
 // pose cotangents of g1 (R1bar 9, c1bar 3) and g2 (R2bar 9, c2bar 3).
+// sv: the minimiser over the capsule axis that the forward evaluation found.
 static __device__ void capsule_box_vjp(const DevModel& m, const double* gR, const double* gp, int g1, int g2,
-                                const double* cb, double* b1, double* b2) {
+                                       double sv, const double* cb, double* b1, double* b2) {
   const double rc = m.g_size[g1][0], Lh = m.g_size[g1][1];
   const double* h = m.g_size[g2];
   const double* R1 = gR + 9 * g1; const double* R2 = gR + 9 * g2;
@@ -230,7 +231,6 @@ static __device__ void capsule_box_vjp(const DevModel& m, const double* gR, cons
   double y0[3], wv[3];
   matTvec3(R2, dc, y0);
   matTvec3(R2, u, wv);
-  const double sv = capsule_box_s(y0, wv, Lh, h);
   const double phi2 = capsule_box_curv(y0, wv, sv, Lh, h);
   const double y[3] = {y0[0] + sv * wv[0], y0[1] + sv * wv[1], y0[2] + sv * wv[2]};
   double gr[3], n[3];
@@ -436,7 +436,7 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     double* b1 = sb; double* b2 = sb + 12;
     const int g1 = m.p_g1[p];
     if (m.p_g2[p] >= 0) {
-      capsule_box_vjp(m, gR, gp, g1, m.p_g2[p], cb, b1, b2);
+      capsule_box_vjp(m, gR, gp, g1, m.p_g2[p], w.at(L.csv)[s], cb, b1, b2);
     } else {
       // r = pt_z - rad, pos = (pt_x, pt_y, pt_z - rad - r / 2); fixed frame
       const double ptb[3] = {cb[1], cb[2], cb[0] + 0.5 * cb[3]};
