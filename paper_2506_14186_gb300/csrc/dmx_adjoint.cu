@@ -64,8 +64,8 @@ __device__ int dual_step(const Grp<1>& g, const DevModel& m, const WsT<Dual>& w,
       for (int i = 0; i < nv; ++i) {
         Dual sq = 0.0, sv = 0.0;
         for (int j = 0; j < s; ++j) {
+          if (!((c_tab.nz[s] >> j) & 1u)) continue;
           const double c = c_tab.a[s][j];
-          if (c == 0.0) continue;
           sq += c * kv[j * nv + i];
           sv += c * ka[j * nv + i];
         }

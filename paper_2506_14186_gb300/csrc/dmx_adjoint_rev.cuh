@@ -110,8 +110,8 @@ __device__ int dopri5_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, 
       for (int i = g.lane; i < nv; i += G) {
         double sq = 0;
         for (int j = 0; j < s; ++j) {
+          if (!((c_tab.nz[s] >> j) & 1u)) continue;
           const double c = c_tab.a[s][j];
-          if (c == 0.0) continue;
           sq += c * vst[j * nv + i];
         }
         dq[i] = h * sq;
@@ -135,16 +135,16 @@ __device__ int dopri5_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, 
       for (int i = g.lane; i < nv; i += G) {
         vnb[i] += Vb[i];
         for (int j = 0; j < s; ++j) {
+          if (!((c_tab.nz[s] >> j) & 1u)) continue;
           const double c = c_tab.a[s][j];
-          if (c == 0.0) continue;
           kab[j * nv + i] += h * c * Vb[i];
         }
       }
       integrate_pos_vjp(g, m, qn, dq, Qb, qnb, dqb);
       for (int i = g.lane; i < nv; i += G)
         for (int j = 0; j < s; ++j) {
+          if (!((c_tab.nz[s] >> j) & 1u)) continue;
           const double c = c_tab.a[s][j];
-          if (c == 0.0) continue;
           kvb[j * nv + i] += h * c * dqb[i];
         }
     } else {

@@ -1039,20 +1039,33 @@ __device__ int rhs(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T*
 // ------------------------------------------------------------------ integrator
 // Dormand & Prince (1980) 5(4) coefficients: a (row 7 = the 5th-order weights
 // b, first same as last) and e = b - bhat (bhat: embedded 4th-order weights).
+// nz[s] / enz: bit j set where a[s][j] / e[j] is non-zero, so that the stage
+// sums skip the zero coefficients with an integer test.
 struct Tab {
   double a[7][7];
   double e[7];
+  unsigned nz[7], enz;
 };
-static __constant__ Tab c_tab = {
-    {{0, 0, 0, 0, 0, 0, 0},
-     {1.0 / 5.0, 0, 0, 0, 0, 0, 0},
-     {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0, 0},
-     {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0, 0},
-     {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0, 0},
-     {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0, 0},
-     {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0}},
-    {35.0 / 384.0 - 5179.0 / 57600.0, 0.0, 500.0 / 1113.0 - 7571.0 / 16695.0, 125.0 / 192.0 - 393.0 / 640.0,
-     -2187.0 / 6784.0 + 92097.0 / 339200.0, 11.0 / 84.0 - 187.0 / 2100.0, -1.0 / 40.0}};
+__host__ __device__ constexpr Tab make_tab() {
+  Tab t{{{0, 0, 0, 0, 0, 0, 0},
+         {1.0 / 5.0, 0, 0, 0, 0, 0, 0},
+         {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0, 0},
+         {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0, 0},
+         {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0, 0},
+         {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0, 0},
+         {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0}},
+        {35.0 / 384.0 - 5179.0 / 57600.0, 0.0, 500.0 / 1113.0 - 7571.0 / 16695.0, 125.0 / 192.0 - 393.0 / 640.0,
+         -2187.0 / 6784.0 + 92097.0 / 339200.0, 11.0 / 84.0 - 187.0 / 2100.0, -1.0 / 40.0},
+        {0, 0, 0, 0, 0, 0, 0},
+        0u};
+  for (int s = 0; s < 7; ++s)
+    for (int j = 0; j < 7; ++j)
+      if (t.a[s][j] != 0.0) t.nz[s] |= 1u << j;
+  for (int j = 0; j < 7; ++j)
+    if (t.e[j] != 0.0) t.enz |= 1u << j;
+  return t;
+}
+static __constant__ Tab c_tab = make_tab();
 
 // q (+) dq for every joint (free: translation + body-frame rotation exponential).
 template <int G, class T>
@@ -1115,8 +1128,8 @@ __device__ int dopri5_stages(const Grp<G>& g, const DevModel& m, const Ws& w, co
     for (int i = g.lane; i < nv; i += G) {
       double sq = 0, sv = 0;
       for (int j = 0; j < s; ++j) {
+        if (!((c_tab.nz[s] >> j) & 1u)) continue;
         const double c = c_tab.a[s][j];
-        if (c == 0.0) continue;
         sq += c * kv[j * nv + i];
         sv += c * ka[j * nv + i];
       }
@@ -1150,8 +1163,8 @@ __device__ double dopri5_attempt(const Grp<G>& g, const DevModel& m, const Ws& w
   for (int i = g.lane; i < nv; i += G) {
     double ep = 0, ev = 0;
     for (int j = 0; j < 7; ++j) {
+      if (!((c_tab.enz >> j) & 1u)) continue;
       const double c = c_tab.e[j];
-      if (c == 0.0) continue;
       ep += c * kv[j * nv + i];
       ev += c * ka[j * nv + i];
     }

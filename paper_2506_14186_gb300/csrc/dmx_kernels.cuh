@@ -19,7 +19,7 @@ namespace dmx {
 __device__ __forceinline__ double boundary_time(double T, int NI, int k) { return k >= NI ? T : T * k / NI; }
 
 struct EnvState {
-  double t, h, errp, T;
+  double t, h, lerrp, T;   // lerrp: log of the previous accepted step's error norm
   int k, nacc, nrej, att, st, done;
 };
 
@@ -60,7 +60,7 @@ __device__ void env_start(const Grp<G>& g, const DevModel& m, const Ws& w, const
   bad = g.isum(bad);
   if (g.lane == 0) for (int k = 0; k < MASKW; ++k) w.i[L.pmask + k] = 0;
   g.sync();
-  s.t = 0.0; s.h = P.h0; s.errp = 1.0; s.T = P.T[env];
+  s.t = 0.0; s.h = P.h0; s.lerrp = 0.0; s.T = P.T[env];
   s.k = 0; s.nacc = 0; s.nrej = 0; s.att = 0; s.st = ENV_OK; s.done = 0;
   if (P.xb) store_state(g, m, w, P, env, P.xb);
   if (P.ckpt) write_checkpoint(g, m, w, P, env, 0, 0.0);
@@ -98,9 +98,12 @@ __device__ void env_attempt(const Grp<G>& g, const DevModel& m, const Ws& w, con
     g.sync();
     ++s.nacc;
     const double errf = fmax(err, 1e-10);
-    double fac = 0.9 * pow(errf, -0.6 / 5.0) * pow(s.errp, 0.2 / 5.0);
+    // 0.9 err^-(P+I)/5 err_prev^(P/5) as one exponential of the logs (the
+    // previous log is carried over)
+    const double lerr = log(errf);
+    double fac = 0.9 * exp(-(0.6 / 5.0) * lerr + (0.2 / 5.0) * s.lerrp);
     fac = fmin(10.0, fmax(0.2, fac));
-    s.errp = errf;
+    s.lerrp = lerr;
     s.h = ht * fac;
     if (P.ckpt && (s.nacc % P.K) == 0) write_checkpoint(g, m, w, P, env, s.nacc / P.K, s.t);
     if (reached) {
@@ -142,7 +145,7 @@ __device__ void load_step_state(const Grp<G>& g, const DevModel& m, const Ws& w,
   for (int i = g.lane; i < m.nv; i += G) { vn[i] = S.v[(size_t)i * P.B + env]; ka[i] = S.ka0[(size_t)i * P.B + env]; }
   if (g.lane == 0)
     for (int k = 0; k < MASKW; ++k) w.i[L.pmask + k] = S.pmask[(size_t)k * P.B + env];
-  s.t = S.t[env]; s.h = S.h[env]; s.errp = S.errp[env]; s.T = P.T[env];
+  s.t = S.t[env]; s.h = S.h[env]; s.lerrp = S.lerrp[env]; s.T = P.T[env];
   s.k = S.k[env]; s.nacc = S.nacc[env]; s.nrej = S.nrej[env]; s.att = S.att[env]; s.st = S.st[env];
   s.done = S.done[env];
   g.sync();
@@ -157,7 +160,7 @@ __device__ void save_step_state(const Grp<G>& g, const DevModel& m, const Ws& w,
   for (int i = g.lane; i < m.nv; i += G) { S.v[(size_t)i * P.B + env] = vn[i]; S.ka0[(size_t)i * P.B + env] = ka[i]; }
   if (g.lane == 0) {
     for (int k = 0; k < MASKW; ++k) S.pmask[(size_t)k * P.B + env] = w.i[L.pmask + k];
-    S.t[env] = s.t; S.h[env] = s.h; S.errp[env] = s.errp;
+    S.t[env] = s.t; S.h[env] = s.h; S.lerrp[env] = s.lerrp;
     S.k[env] = s.k; S.nacc[env] = s.nacc; S.nrej[env] = s.nrej; S.att[env] = s.att; S.st[env] = s.st;
     S.done[env] = s.done;
   }

@@ -32,7 +32,7 @@ struct StepState {
   double* ka0;          // [nv][B] derivative at the step start (first same as last)
   double* t;
   double* h;
-  double* errp;
+  double* lerrp;        // log of the previous accepted error norm (step-size controller)
   int* k;
   int* nacc;
   int* nrej;

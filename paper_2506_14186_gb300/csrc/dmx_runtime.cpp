@@ -313,7 +313,7 @@ dmx_status run_rollout(dmx_model* m, const RolloutParams& P0, int form, int G, c
   size_t off = 0;
   auto takeD = [&](size_t n) { double* r = reinterpret_cast<double*>(base + off); off += n * sizeof(double); return r; };
   auto takeI = [&](size_t n) { int* r = reinterpret_cast<int*>(base + off); off += n * sizeof(int); return r; };
-  S.q = takeD(B * nq); S.v = takeD(B * nv); S.ka0 = takeD(B * nv); S.t = takeD(B); S.h = takeD(B); S.errp = takeD(B);
+  S.q = takeD(B * nq); S.v = takeD(B * nv); S.ka0 = takeD(B * nv); S.t = takeD(B); S.h = takeD(B); S.lerrp = takeD(B);
   S.k = takeI(B); S.nacc = takeI(B); S.nrej = takeI(B); S.att = takeI(B); S.st = takeI(B); S.done = takeI(B);
   S.pmask = takeI(B * MASKW);
   S.active = takeI(1);
