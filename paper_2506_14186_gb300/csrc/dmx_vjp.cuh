@@ -298,6 +298,22 @@ static __device__ void capsule_box_vjp(const DevModel& m, const double* gR, cons
 // i moves the first geom's body, -1 the second's.  Returns false when the dof
 // moves neither or both (no Jacobian entry).  With ya_i = an_i + bcoef v_i:
 //   Jbar_r,i = -(D_r z_r y_i + D_r (J_r y) ya_i)   (active rows, else 0).
+__device__ __forceinline__ void slot_rows_bar(const DevModel& m, const WsB& b, int p, int r0, double yi, double yai,
+                                              double* jb) {
+  const LayoutBar& LB = *b.L;
+  const double* cz = b.at(LB.cz); const double* cj = b.at(LB.cj);
+  if (m.p_condim[p] == 1) {
+    jb[0] = -(cz[r0] * yi + cj[r0] * yai);
+    jb[1] = 0.0; jb[2] = 0.0;
+  } else {
+    double e[4];
+    for (int k = 0; k < 4; ++k) e[k] = -(cz[r0 + k] * yi + cj[r0 + k] * yai);
+    const double mu = m.p_mu[p];
+    jb[0] = (e[0] + e[1]) + (e[2] + e[3]);
+    jb[1] = mu * (e[0] - e[1]);
+    jb[2] = mu * (e[2] - e[3]);
+  }
+}
 __device__ __forceinline__ bool slot_jbar(const DevModel& m, const Ws& w, const WsB& b, int s, int r0, int i,
                                           double yi, double yai, double* jb, double* pv, double* sg) {
   const Layout& L = *w.L;
@@ -395,11 +411,20 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     for (int s = 0; s < m.nslot; ++s) {
       const int r0 = slotrow[s];
       if (r0 < 0) continue;
-      double jb[3], pv[3], sg;
-      if (!slot_jbar(m, w, b, s, r0, i, y[i], yai, jb, pv, &sg)) continue;
+      const int p = m.s_pair[s];
       const double* ct = CT + 16 * s;
       double pvb[3];
-      for (int k = 0; k < 3; ++k) pvb[k] = sg * (jb[0] * ct[4 + k] + jb[1] * ct[7 + k] + jb[2] * ct[10 + k]);
+      if (m.p_g2[p] < 0) {
+        // ground plane: frame (z, x, y) of the world, the dof moves the geom's body or nothing
+        if (!((m.b_anc[m.g_body[m.p_g1[p]]] >> bi) & 1u)) continue;
+        double jb[3];
+        slot_rows_bar(m, b, p, r0, y[i], yai, jb);
+        pvb[0] = jb[1]; pvb[1] = jb[2]; pvb[2] = jb[0];
+      } else {
+        double jb[3], pv[3], sg;
+        if (!slot_jbar(m, w, b, s, r0, i, y[i], yai, jb, pv, &sg)) continue;
+        for (int k = 0; k < 3; ++k) pvb[k] = sg * (jb[0] * ct[4 + k] + jb[1] * ct[7 + k] + jb[2] * ct[10 + k]);
+      }
       acc_cross(ct + 1, pvb, sbi);      // pv = S_ang x pos + S_lin
       sbi[3] += pvb[0]; sbi[4] += pvb[1]; sbi[5] += pvb[2];
     }
@@ -413,18 +438,30 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     const int p = m.s_pair[s];
     const int nrow = m.p_condim[p] == 1 ? 1 : 4;
     double cb[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < nv; ++i) {
-      double jb[3], pv[3], sg;
-      if (!slot_jbar(m, w, b, s, r0, i, y[i], an[i] + m.bcoef * v[i], jb, pv, &sg)) continue;
-      const double* sv = S + 6 * i;
-      double pvb[3];
-      for (int k = 0; k < 3; ++k) {
-        cb[4 + k] += sg * jb[0] * pv[k];
-        cb[7 + k] += sg * jb[1] * pv[k];
-        cb[10 + k] += sg * jb[2] * pv[k];
-        pvb[k] = sg * (jb[0] * ct[4 + k] + jb[1] * ct[7 + k] + jb[2] * ct[10 + k]);
+    if (m.p_g2[p] < 0) {
+      // ground plane: the frame is fixed (no frame cotangents), pvb in the world frame
+      const unsigned anc = m.b_anc[m.g_body[m.p_g1[p]]];
+      for (int i = 0; i < nv; ++i) {
+        if (!((anc >> m.dof_body[i]) & 1u)) continue;
+        double jb[3];
+        slot_rows_bar(m, b, p, r0, y[i], an[i] + m.bcoef * v[i], jb);
+        const double pvb[3] = {jb[1], jb[2], jb[0]};
+        acc_cross(pvb, S + 6 * i, cb + 1);   // pos cotangent from S_ang x pos
       }
-      acc_cross(pvb, sv, cb + 1);       // pos cotangent from S_ang x pos
+    } else {
+      for (int i = 0; i < nv; ++i) {
+        double jb[3], pv[3], sg;
+        if (!slot_jbar(m, w, b, s, r0, i, y[i], an[i] + m.bcoef * v[i], jb, pv, &sg)) continue;
+        const double* sv = S + 6 * i;
+        double pvb[3];
+        for (int k = 0; k < 3; ++k) {
+          cb[4 + k] += sg * jb[0] * pv[k];
+          cb[7 + k] += sg * jb[1] * pv[k];
+          cb[10 + k] += sg * jb[2] * pv[k];
+          pvb[k] = sg * (jb[0] * ct[4 + k] + jb[1] * ct[7 + k] + jb[2] * ct[10 + k]);
+        }
+        acc_cross(pvb, sv, cb + 1);       // pos cotangent from S_ang x pos
+      }
     }
     double b14 = 0.0, b15 = 0.0;
     for (int e = 0; e < nrow; ++e) { b14 += cj[r0 + e]; b15 -= jy[r0 + e] * z[r0 + e]; }
