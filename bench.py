@@ -157,18 +157,41 @@ FORWARD_SOURCES = ("dmx_device.cuh", "dmx_dual.cuh", "dmx_kernels.cuh", "dmx_ker
                    "dmx_inst_g32.cu")
 
 
+# sources of the reverse adjoint kernel (its FP64 counter record is valid while they are unchanged)
+ADJOINT_SOURCES = FORWARD_SOURCES + ("dmx_adjoint.h", "dmx_adjoint_rev.cuh", "dmx_vjp.cuh", "dmx_adj_g2.cu",
+                                     "dmx_adj_g4.cu", "dmx_adj_g8.cu", "dmx_adj_g16.cu", "dmx_adj_g32.cu")
+
+
+def _sources_sha(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2506_14186_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def _adjoint_flops_per_env(lanes):
+    """FP64 flops per environment of the reverse adjoint of the arm workload
+    (T = 2 s, 50 intervals, K = 32) from the committed ncu counter record
+    (2 DFMA + DMUL + DADD thread operations), if it was taken on the current
+    kernel sources with the same lane count (else None)."""
+    path = os.path.join(ROOT, "profiles", "adjoint_rev_chain_cube.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if rec.get("source_sha256") != _sources_sha(ADJOINT_SOURCES) or rec.get("lanes") != lanes:
+        return None
+    return rec["fp64_flops_per_launch"] / rec["envs"]
+
+
 def _traffic(kernel_lanes):
     """DRAM bytes per launch of the persistent kernel from the committed ncu
     summary, if it was taken on the current kernel sources (else None)."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "rollout_persistent_box_push.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = hashlib.sha256()
-    for f in FORWARD_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2506_14186_gb300", "csrc", f), "rb").read())
-    if rec.get("source_sha256") != h.hexdigest() or rec.get("lanes") != kernel_lanes:
+    if rec.get("source_sha256") != _sources_sha(FORWARD_SOURCES) or rec.get("lanes") != kernel_lanes:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -323,6 +346,11 @@ def grad_leg(dmx, dev, B=16384, adj_lanes=0):
     else:
         adj_lanes, adj_ms = autotune.tune_adjoint(m, x0, T, ctrl=ctrl, NI=50, K=32)
     m.set_lanes(B, fwd_lanes)
+    # warm-up on a short horizon: the stream-ordered pool then holds the tape
+    # and adjoint scratch sizes the timed call needs
+    w = dmx.rollout(m, x0, torch.clamp(T, max=0.05), ctrl=ctrl, NI=50, K=32, tape=True)
+    dmx.rollout_grad(w["tape"], torch.zeros_like(w["xT"]))
+    del w
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record(st)
@@ -335,7 +363,16 @@ def grad_leg(dmx, dev, B=16384, adj_lanes=0):
     e2.synchronize()
     t_f, t_all = e0.elapsed_time(e1) * 1e-3, e0.elapsed_time(e2) * 1e-3
     steps = int(out["nsteps"].sum().item())
-    return {"workload": "chain_cube (7 hinges + cube, NI=50, T=2 s, K=32)", "envs": B,
+    fpe = _adjoint_flops_per_env(adj_lanes)
+    adj_roof = None
+    if fpe is not None:
+        achieved = fpe * B / (t_all - t_f) / 1e12
+        peak = FP64_PEAK_GFLOPS / 1e3
+        adj_roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "kernel": f"k_adjoint_rev<{adj_lanes}>",
+                    "work": "FP64 thread operations counted by ncu (2 DFMA + DMUL + DADD) per environment, "
+                            "profiles/adjoint_rev_chain_cube.json"}
+    return {"workload": "chain_cube (7 hinges + cube, NI=50, T=2 s, K=32)", "envs": B, "adjoint_roofline": adj_roof,
             "grad_rollouts_per_s": B / t_all, "env_steps_per_s": steps / t_all, "forward_s": t_f,
             "adjoint_s": t_all - t_f, "env_steps": steps, "adjoint_kernel": "reverse",
             "lanes": {"forward": fwd_lanes, "adjoint": adj_lanes, "adjoint_tuning_ms": adj_ms},
