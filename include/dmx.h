@@ -56,7 +56,8 @@ enum {
   DMX_ENV_H_UNDERFLOW = 2,    /* step size fell below 1e-12 s */
   DMX_ENV_NONFINITE = 3,      /* non-finite initial state */
   DMX_ENV_SOLVER_NOCONV = 4,  /* constraint Newton solve exceeded 50 iterations */
-  DMX_ENV_ROW_OVERFLOW = 5    /* more active constraint rows than the workspace holds */
+  DMX_ENV_ROW_OVERFLOW = 5    /* more included constraint rows than the workspace holds (row capacity =
+                                 min(rows of all contact slots, 64), dmx_model_info) */
 };
 
 enum { DMX_JNT_FREE = 0, DMX_JNT_HINGE = 1 };
@@ -213,7 +214,8 @@ dmx_status dmx_set_lanes(dmx_model* m, int32_t B, int32_t grad, int32_t lanes);
 /* Model facts for tests and tools: invw[nbody] (host, may be NULL) receives the
  * translational inverse weight of every body at qpos0 (the A_hat of Sec. 2.1,
  * model constant); info[8] (host, may be NULL) receives nslot, nrowid,
- * row capacity, workspace doubles, workspace ints, nbody. */
+ * row capacity of the forward right-hand side (the CFD right-hand side holds
+ * every row id up to 128), workspace doubles, workspace ints, nbody. */
 dmx_status dmx_model_info(const dmx_model* m, double* invw, int32_t* info);
 
 /* ------------------------------------------------------------------ serving */

@@ -20,6 +20,12 @@ constexpr int MAXP = 24;      // contact pairs
 constexpr int MAXS = 32;      // contact slots
 constexpr int MAXU = 16;      // actuators
 constexpr int MAXROWID = 128; // constraint rows over all slots (stable row ids)
+// Constraint rows one right-hand side can hold (the included contacts' rows,
+// compacted): the Jacobian and row arrays of the per-environment workspace
+// are sized min(row ids, ROWCAP), which keeps shared memory per environment,
+// hence warps per SM, independent of how many slots a model declares; a state
+// with more included rows reports ENV_ROW_OVERFLOW.
+constexpr int ROWCAP = 64;
 constexpr int MAXLEV = 12;    // depth of the body tree
 constexpr int MASKW = MAXROWID / 32;
 

@@ -179,8 +179,10 @@ extern "C" dmx_status dmx_create_model(const dmx_model_desc* desc, dmx_model** o
   dmx_model* m = new dmx_model();
   std::string err = compile_model(desc, m->host);
   if (!err.empty()) { delete m; return dmx_fail(DMX_ERR_INVALID, err); }
-  m->rcap = std::max(1, std::min(m->host.nrowid, dmx::MAXROWID));
+  m->rcap = std::max(1, std::min(m->host.nrowid, dmx::ROWCAP));
   m->L = make_layout(m->host, m->rcap);
+  m->rcap_c = std::max(1, std::min(m->host.nrowid, dmx::MAXROWID));
+  m->Lc = make_layout(m->host, m->rcap_c);
   CK(cudaGetDevice(&m->device));
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, m->device));
@@ -258,7 +260,10 @@ static bool valid_lanes(int G) { return G == 1 || G == 2 || G == 4 || G == 8 || 
 // SM (with larger blocks a batch of a few thousand environments filled only
 // some of the SMs), and a block needs only one warp's workspace.
 bool launch_config(const dmx_model* m, int G, int* threads, size_t* smem) {
-  const int per = m->L.nd * 8 + m->L.ni * 4;
+  return launch_config_layout(m, m->L, G, threads, smem);
+}
+bool launch_config_layout(const dmx_model* m, const dmx::Layout& L, int G, int* threads, size_t* smem) {
+  const int per = L.nd * 8 + L.ni * 4;
   if (G < 1 || G > 32) return false;
   const size_t s = (size_t)(32 / G) * per;
   if ((int)s > m->smem_max - 1024) return false;
@@ -494,8 +499,9 @@ constexpr size_t kSnapMaxBytes = size_t(8) << 30;
 
 // Threads and shared memory of the reverse-mode adjoint kernel for G lanes.
 // (one warp per block, as for the forward kernels)
-static bool adj_launch_config(const dmx_model* m, const dmx::LayoutBar& LB, int G, int* threads, size_t* smem) {
-  const int per = (m->L.nd + LB.nd) * 8 + m->L.ni * 4;
+static bool adj_launch_config(const dmx_model* m, const dmx::Layout& L, const dmx::LayoutBar& LB, int G, int* threads,
+                              size_t* smem) {
+  const int per = (L.nd + LB.nd) * 8 + L.ni * 4;
   if (G < 1 || G > 32) return false;
   const size_t s = (size_t)(32 / G) * per;
   if ((int)s > m->smem_max - 2048) return false;
@@ -506,18 +512,19 @@ static bool adj_launch_config(const dmx_model* m, const dmx::LayoutBar& LB, int 
 
 // Lanes of the reverse-mode adjoint: the recorded choice, else enough lanes
 // to give every SM sub-partition a warp (at least 2), within shared memory.
-static int adjoint_lanes(dmx_model* m, int B) {
+static int adjoint_lanes(dmx_model* m, int B, const dmx::Layout& L) {
+  const dmx::LayoutBar LB = dmx::make_bar_layout(m->host, L.rcap);
+  int t; size_t s;
   {
     std::lock_guard<std::mutex> lk(m->mu);
     auto it = m->tuned.find({B, 2});
-    if (it != m->tuned.end() && valid_adj_lanes(it->second)) return it->second;
+    if (it != m->tuned.end() && valid_adj_lanes(it->second) && adj_launch_config(m, L, LB, it->second, &t, &s))
+      return it->second;
   }
-  const dmx::LayoutBar LB = dmx::make_bar_layout(m->host, m->rcap);
   const int want = 4 * 32 * m->nsm;
   int G = 2;
   while (G < 32 && (long long)B * G < want) G <<= 1;
-  int t; size_t s;
-  while (G < 32 && !adj_launch_config(m, LB, G, &t, &s)) G <<= 1;
+  while (G < 32 && !adj_launch_config(m, L, LB, G, &t, &s)) G <<= 1;
   return G;
 }
 
@@ -532,6 +539,7 @@ size_t adjoint_scratch_bound(dmx_model* m, int B, int K, int cfd) {
   size_t b = sizeof(double) * groups * k * std::max<size_t>(m->host.nq + 6 * m->host.nv + 1, nx + 1);
   if (mode == DMX_ADJ_REVERSE && !cfd)
     b += std::min(kSnapMaxBytes, sizeof(double) * groups * k * 6 * (size_t)dmx::snap_offsets(m->host, m->L).size);
+  (void)cfd;
   return b + 256;
 }
 
@@ -558,11 +566,12 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
     mode = m->adj_mode;
   }
   dmx::AdjParams P{};
-  P.model = m->dev; P.L = m->L; P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd;
+  const dmx::Layout& L = layout_for(m, cfd);
+  P.model = m->dev; P.L = L; P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd;
   P.ckpt = t->ckpt; P.hlog = t->hlog; P.tape_n = t->n; P.ctrl = t->ctrl; P.T = t->T;
   P.xT_bar = xT_bar; P.xb_bar = xb_bar; P.x0_bar = x0_bar; P.ctrl_bar = m->host.nu ? ctrl_bar : nullptr;
   if (mode == DMX_ADJ_TANGENT) {
-    if (m->L.nd > dmx::adjoint_workspace_limit() || m->L.ni > dmx::adjoint_int_limit())
+    if (L.nd > dmx::adjoint_workspace_limit() || L.ni > dmx::adjoint_int_limit())
       return dmx_fail(DMX_ERR_INVALID, "model workspace exceeds the tangent adjoint kernel's per-lane limit");
     const int wpb = dmx::adjoint_warps_per_block();
     int blocks = (t->B + wpb - 1) / wpb;
@@ -577,10 +586,10 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
     CK(cudaFreeAsync(scratch, st));
     return DMX_OK;
   }
-  const int G = adjoint_lanes(m, t->B);
-  P.LB = dmx::make_bar_layout(m->host, m->rcap);
+  const int G = adjoint_lanes(m, t->B, L);
+  P.LB = dmx::make_bar_layout(m->host, L.rcap);
   int threads; size_t smem;
-  if (!adj_launch_config(m, P.LB, G, &threads, &smem))
+  if (!adj_launch_config(m, L, P.LB, G, &threads, &smem))
     return dmx_fail(DMX_ERR_INVALID, "adjoint workspace of " + std::to_string(G) + " lanes/env does not fit shared memory");
   const int gpb = threads / G;
   const int occ = std::max(1, dmx::adjoint_rev_occupancy(G, threads, smem));
@@ -592,7 +601,7 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
   // share of the free device memory, else each stage is evaluated again
   size_t snap_bytes = 0;
   if (mode == DMX_ADJ_REVERSE && !cfd) {
-    P.SN = dmx::snap_offsets(m->host, m->L).size;
+    P.SN = dmx::snap_offsets(m->host, L).size;
     snap_bytes = sizeof(double) * (size_t)blocks * gpb * t->K * 6 * (size_t)P.SN;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || snap_bytes > free_b / 8 || snap_bytes > kSnapMaxBytes)
@@ -616,12 +625,13 @@ extern "C" dmx_status dmx_eval_rhs_vjp(dmx_model* m, int32_t B, const double* q,
   if (B == 0) return DMX_OK;
   const bool act = m->host.nu > 0;
   if (!q || !v || !abar || !qbar || !vbar || !status || (act && (!u || !ubar))) return dmx_fail(DMX_ERR_INVALID, "null array");
-  const int G = lanes ? lanes : adjoint_lanes(m, B);
+  const dmx::Layout& L = layout_for(m, cfd);
+  const int G = lanes ? lanes : adjoint_lanes(m, B, L);
   if (!valid_adj_lanes(G)) return dmx_fail(DMX_ERR_INVALID, "lanes must be 0, 2, 4, 8, 16 or 32");
   dmx::AdjParams P{};
-  P.model = m->dev; P.L = m->L; P.LB = dmx::make_bar_layout(m->host, m->rcap); P.B = B; P.cfd = cfd;
+  P.model = m->dev; P.L = L; P.LB = dmx::make_bar_layout(m->host, L.rcap); P.B = B; P.cfd = cfd;
   int threads; size_t smem;
-  if (!adj_launch_config(m, P.LB, G, &threads, &smem)) return dmx_fail(DMX_ERR_INVALID, "workspace does not fit");
+  if (!adj_launch_config(m, L, P.LB, G, &threads, &smem)) return dmx_fail(DMX_ERR_INVALID, "workspace does not fit");
   CK(dmx::launch_eval_rhs_vjp(G, P, q, v, act ? u : q, abar, qbar, vbar, act ? ubar : nullptr, status, threads, smem,
                               static_cast<cudaStream_t>(stream)));
   return DMX_OK;
@@ -635,9 +645,10 @@ extern "C" dmx_status dmx_eval_rhs(dmx_model* m, int32_t B, const double* q, con
   const int G = lanes ? lanes : default_lanes(m, B);
   if (!valid_lanes(G)) return dmx_fail(DMX_ERR_INVALID, "lanes must be 0, 1, 2, 4, 8, 16 or 32");
   int threads; size_t smem;
-  if (!launch_config(m, G, &threads, &smem)) return dmx_fail(DMX_ERR_INVALID, "workspace does not fit");
+  const dmx::Layout& L = layout_for(m, cfd);
+  if (!launch_config_layout(m, L, G, &threads, &smem)) return dmx_fail(DMX_ERR_INVALID, "workspace does not fit");
   RolloutParams P{};
-  P.model = m->dev; P.L = m->L; P.B = B;
+  P.model = m->dev; P.L = L; P.B = B;
   CK(launch_eval_rhs(G, P, q, v, m->host.nu ? u : q, cfd, a, info, threads, smem, static_cast<cudaStream_t>(stream)));
   return DMX_OK;
 }

@@ -21,8 +21,9 @@ struct DevBuf {
 struct dmx_model {
   dmx::DevModel host;
   dmx::DevModel* dev = nullptr;
-  dmx::Layout L;
-  int device = 0, nsm = 0, smem_max = 0, rcap = 0;
+  dmx::Layout L;                              // workspace of the forward right-hand side (rows: rcap)
+  dmx::Layout Lc;                             // workspace of the CFD right-hand side F~ (rows: rcap_c)
+  int device = 0, nsm = 0, smem_max = 0, rcap = 0, rcap_c = 0;
   double invw[dmx::MAXB];
   std::mutex mu;
   std::map<std::pair<int, int>, int> tuned;   // (B, kind) -> lanes per environment
@@ -45,6 +46,10 @@ struct dmx_tape {
 
 dmx_status dmx_fail(dmx_status s, const std::string& msg);
 bool launch_config(const dmx_model* m, int G, int* threads, size_t* smem);
+bool launch_config_layout(const dmx_model* m, const dmx::Layout& L, int G, int* threads, size_t* smem);
+// Workspace layout of a right-hand side with (cfd = 1) or without the CFD
+// contacts: F~ includes every slot within w_c, so it may need more rows.
+inline const dmx::Layout& layout_for(const dmx_model* m, int cfd) { return cfd ? m->Lc : m->L; }
 int default_lanes(const dmx_model* m, int B);
 int tuned_lanes(dmx_model* m, int B, int grad);
 dmx_status run_rollout(dmx_model* m, const dmx::RolloutParams& P, int form, int G, cudaStream_t st);
