@@ -312,3 +312,29 @@ def test_integrate_pos_group_properties(orc):
         ew, ev = np.cos(th / 2), np.sin(th / 2) * ax
         ref = np.concatenate([[w * ew - v @ ev], w * ev + ew * v + np.cross(v, ev)])
         np.testing.assert_allclose(got, ref / np.linalg.norm(ref), atol=2e-16)
+
+
+@pytest.mark.parametrize("kind", ["motor", "position"])
+def test_actuated_hinge_closed_form(orc, kind):
+    """One hinge about the world z axis (COM at distance l on the link, gravity
+    along the axis, so the bias force vanishes): the applied generalised force
+    is gear u for a motor and kp (u - q) - kd v for a position servo, plus the
+    joint damping -d v, and the acceleration is that force over the moment of
+    inertia about the axis, Izz + m l^2."""
+    m_, l, d, gear, kp, kd = 2.0, 0.3, 0.15, 1.7, 40.0, 1.3
+    inertia = [0.01, 0.02, 0.03]
+    scene = {"name": "hinge", "bodies": [{"parent": -1, "joint": "hinge", "pos": [0.0, 0.0, 0.0],
+                                          "quat": [1.0, 0.0, 0.0, 0.0], "axis": [0.0, 0.0, 1.0], "mass": m_,
+                                          "com": [l, 0.0, 0.0], "inertia": inertia, "damping": d}],
+             "geoms": [], "pairs": [],
+             "actuators": [{"type": kind, "body": 0, "gear": gear, "kp": kp, "kd": kd}],
+             "options": W._options(), "qpos0": [0.0]}
+    om = orc.OracleModel(scene)
+    Jz = inertia[2] + m_ * l * l
+    g = np.random.default_rng(21)
+    for _ in range(5):
+        q, v, u = g.uniform(-2, 2, 1), g.uniform(-3, 3, 1), g.uniform(-1, 1, 1)
+        tau = gear * u[0] if kind == "motor" else kp * (u[0] - q[0]) - kd * v[0]
+        tau -= d * v[0]
+        np.testing.assert_allclose(om.applied(q, v, u), [tau], rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(om.rhs(q, v, u), [tau / Jz], rtol=1e-12, atol=1e-13)
