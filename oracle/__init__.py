@@ -13,8 +13,10 @@ flat record layout (``oracle/model.h``).
 Functions whose results are pinned by tests against closed forms, invariants,
 brute force or finite differences (see ``tests/test_oracle_*.py``):
 kinematics, mass matrix, bias force, contacts, impedance, constraint solve,
-right-hand side and its Jacobian, DOPRI5 tableau, rollout, replay, step
-Jacobian and rollout gradient.
+right-hand side and its Jacobian, DOPRI5 tableau, error norm and PID
+step-size controller (fixed point, gains, rejection, clips and floor;
+``tests/test_oracle_step_control.py``), rollout, replay, step Jacobian and
+rollout gradient.
 """
 
 from __future__ import annotations
@@ -62,6 +64,7 @@ def lib():
         L.orc_impedance.restype = ctypes.c_double
         L.orc_count_flops.restype = ctypes.c_longlong
         L.orc_step_error.restype = ctypes.c_double
+        L.orc_error_norm.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -196,6 +199,12 @@ class OracleModel:
         u = _f64(u if u is not None else np.zeros(max(self.nu, 1)))
         return lib().orc_step_error(self.h, _p(_f64(x)), _p(u), ctypes.c_double(h), ctypes.c_double(rtol),
                                     ctypes.c_double(atol))
+
+    def error_norm(self, q0, v0, q1, v1, e, rtol=1e-6, atol=1e-8):
+        """The controller's error norm of an embedded difference e (2 nv tangent
+        components) between the states (q0, v0) and (q1, v1)."""
+        return lib().orc_error_norm(self.h, _p(_f64(q0)), _p(_f64(v0)), _p(_f64(q1)), _p(_f64(v1)), _p(_f64(e)),
+                                    ctypes.c_double(rtol), ctypes.c_double(atol))
 
     def step_jacobian(self, q, v, u, h, cfd=False):
         Jx = np.zeros((self.nx, self.nx)); Ju = np.zeros((self.nx, max(self.nu, 1)))

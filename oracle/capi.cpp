@@ -190,6 +190,13 @@ int orc_replay(void* h, const double* x0, const double* ctrl, double T, int NI, 
   Result r = rollout<double>(M(h), x0, ctrl, make_opts(T, NI, 0, 0, 0, 0), xT, xb, nullptr, nullptr, hlog, n);
   return r.nsteps;
 }
+// Error norm of a given embedded difference e (2 nv tangent components)
+// between the states (q0, v0) and (q1, v1): the scalar the step controller
+// compares with 1.
+double orc_error_norm(void* h, const double* q0, const double* v0, const double* q1, const double* v1,
+                      const double* e, double rtol, double atol) {
+  return error_norm<double>(M(h), q0, v0, q1, v1, e, rtol, atol);
+}
 // Error norm of one DOPRI5 attempt of size hs from x = [q; v] (controls u):
 // the value the adaptive controller compares with 1.
 double orc_step_error(void* h, const double* x, const double* u, double hs, double rtol, double atol) {

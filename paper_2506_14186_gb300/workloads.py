@@ -37,6 +37,12 @@ GRAVITY = (0.0, 0.0, -9.81)
 SOLREF = (0.002, 1.0)
 SOLIMP = (0.0, 0.95, 0.001, 0.5, 2.0)
 SOLIMP_CFD = (0.0, 0.0, 0.05, 1.0, 4.0)
+# Contacts from distance (Sec. 4, App. D.3): contact impedance starting at
+# d_o = 0.1 and the CFD spline (d_c, d_0, w_c, m_c, p_c) that continues it
+# from r = 0 up to the taper width w_c (0.05 m for the 0.1 m cubes here).
+CFD_SOLIMP = (0.1, 0.95, 0.001, 0.5, 2.0)
+CFD_SOLIMP_CFD = (0.0, 0.1, 0.05, 1.0, 4.0)
+CFD_OPTIONS = {"solimp": CFD_SOLIMP, "solimp_cfd": CFD_SOLIMP_CFD}
 SOFTPLUS = 1e-3
 IDQ = (1.0, 0.0, 0.0, 0.0)
 

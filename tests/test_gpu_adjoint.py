@@ -14,10 +14,10 @@ from tests.conftest import rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-6
-CFD_OPT = dict(solimp=(0.1, 0.95, 0.001, 0.5, 2.0), solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+CFD_OPT = dict(W.CFD_OPTIONS)
 # CFD continuation only (the forward right-hand side keeps d(0) = 0, so contact
 # forces stay continuous and the box pushes integrate with ordinary step sizes)
-CFD_ONLY = dict(solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+CFD_ONLY = dict(solimp_cfd=W.CFD_SOLIMP_CFD)
 
 
 @pytest.fixture(scope="module")

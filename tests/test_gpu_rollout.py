@@ -35,7 +35,7 @@ TOL_RHS = 1e-11
 TOL_REPLAY = 1e-9
 TOL_FREE = 1e-4
 TOL_STEP = 1e-11
-CFD_OPT = dict(solimp=(0.1, 0.95, 0.001, 0.5, 2.0), solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+CFD_OPT = dict(W.CFD_OPTIONS)
 
 
 @pytest.fixture(scope="module")
@@ -370,3 +370,26 @@ def test_model_inverse_weights_match_oracle(dmx, orc_mod):
         g = dmx.Model(sc).info()["invw"]
         o = orc_mod.OracleModel(sc)
         np.testing.assert_allclose(g, [o.body_invw(b) for b in range(o.nbody)], rtol=1e-12)
+
+
+# ---------------------------------------------------------------- step-size control
+def test_step_size_sequence_equals_oracle(dmx, orc_mod):
+    """The GPU's controller against the oracle's pinned one: on the torque-free
+    symmetric top (error norm a function of h alone, absolute tolerance only;
+    tests/test_oracle_step_control.py) both take the same accepted step sizes,
+    through the PID transient, the rejections (one retry, and two when the
+    first retry is clipped at 0.2), the growth clip at 10 and the fixed point."""
+    sc = W.box_scene(gravity=(0.0, 0.0, 0.0))
+    sc["bodies"][0]["inertia"] = [0.1, 0.1, 0.3]
+    sc["pairs"] = []
+    om = orc_mod.OracleModel(sc)
+    gm = dmx.Model(sc)
+    x0 = np.array([0, 0, 1.0, 1, 0, 0, 0, 0, 0, 0, 1.0, 0.5, 4.0])
+    for h0 in (1e-6, 5e-3, 0.03, 0.1):
+        inp = {"x0": x0[None, :], "ctrl": None, "T": np.array([1.0]), "NI": 1, "rtol": 0.0, "atol": 1e-8,
+               "h0": h0, "max_steps": 20000}
+        g = gpu_rollout(dmx, gm, inp, tape=True)
+        o = om.rollout(x0, T=1.0, rtol=0.0, atol=1e-8, h0=h0)
+        n = int(g["tape_n"][0])
+        assert n == o["nsteps"] and g["nrej"][0] == o["nrej"]
+        np.testing.assert_allclose(g["hlog"][0, :n], o["hlog"], rtol=1e-9)

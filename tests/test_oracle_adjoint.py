@@ -9,7 +9,7 @@ import pytest
 from paper_2506_14186_gb300 import workloads as W
 from tests.conftest import rel_err
 
-CFD_OPT = dict(solimp=(0.1, 0.95, 0.001, 0.5, 2.0), solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+CFD_OPT = dict(W.CFD_OPTIONS)
 
 
 def test_ballistic_gradient_closed_form(orc):

@@ -274,7 +274,7 @@ def test_impedance_spline_points(orc):
     """solimp (0, 0.95, 0.001, 0.5, 2): d(0) = d_o, d(-w) = d_w, d(-mid w) =
     d_o + mid (d_w - d_o), x^p / mid^(p-1) below the midpoint; CFD continuation
     (d_c, d_0, w_c, m_c, p_c) = (0, 0.1, 0.05, 1, 4) meets d_0 at r = 0 and d_c at w_c."""
-    sc = W.ball_scene(solimp=(0.1, 0.95, 0.001, 0.5, 2.0), solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+    sc = W.ball_scene(**W.CFD_OPTIONS)
     m = orc.OracleModel(sc)
     assert abs(m.impedance(0.0) - 0.1) < 1e-15
     assert abs(m.impedance(-0.001) - 0.95) < 1e-15

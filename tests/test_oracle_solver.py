@@ -124,7 +124,7 @@ def _fd_rhs(m, q, v, u, cfd, eps=1e-7):
     return Jq, Jv, Ju
 
 
-CFD_OPT = dict(solimp=(0.1, 0.95, 0.001, 0.5, 2.0), solimp_cfd=(0.0, 0.1, 0.05, 1.0, 4.0))
+CFD_OPT = dict(W.CFD_OPTIONS)
 
 
 @pytest.mark.parametrize("cfd", [False, True])
