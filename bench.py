@@ -32,13 +32,22 @@ METRIC = "env-steps/s fwd and fwd+adjoint; p50/p99 MPC-request latency, 1 GB300"
 UNIT = "env-steps/s"
 WORKLOAD = {"workload": "box_push", "B": 4096, "T_s": 1.0, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3, "mu": 1.0,
             "contacts": "8 box vertices vs plane, pyramidal 4-edge cone", "solref": [0.002, 1.0]}
-# Algorithmic FP64 work of one accepted step of this workload: 41,112 flop,
-# counted by the oracle's instrumented scalar over 64 seeded environments
-# (python -m oracle.count_flops box).
-FLOP_PER_STEP = 41112.0
-# FP64 peak derived from the unit counts and clock: 152 SMs x 4 FP64 flop/clk
-# (2 DFMA lanes) x 2070 MHz.
-FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+# Algorithmic FP64 work of one accepted step, counted by the oracle's
+# instrumented scalar over seeded environments (python -m oracle.count_flops):
+# each constraint solve counted as started at its final active set (one Newton
+# system and one residual check per right-hand side; the CUDA path starts the
+# search at the previous right-hand side's active set).  Box pushes: 28,910
+# (41,112 with the oracle's own search from the unconstrained acceleration).
+FLOP_PER_STEP = 28910.0
+FLOP_PER_STEP_SEARCH = 41112.0
+# Arm pushing the cube (T = 2 s, 50 intervals): forward 148,516 per accepted
+# step; adjoint 489,196 per accepted step (every step once with one tangent in
+# the counting derivative scalar: primal recompute + linearised step).
+ARM_FLOP_PER_STEP = 148516.0
+ARM_ADJ_FLOP_PER_STEP = 489196.0
+# FP64 peak derived from the unit counts and clock (152 SMs x 4 FP64 flop/clk
+# x 2070 MHz), reported beside the peak measured in the run.
+FP64_PEAK_DERIVED_GFLOPS = 152 * 4 * 2.070
 L2_BYTES = 126 * 2 ** 20
 
 
@@ -56,8 +65,9 @@ def parse():
     p.add_argument("--grad-envs", type=int, default=16384, help="environments of the fwd+adjoint leg")
     p.add_argument("--all", action="store_true", help="every workload (forward, fwd+adjoint, CPU oracle samples)")
     p.add_argument("--adj-lanes", type=int, default=0, help="lanes per environment of the adjoint (0 = autotuned)")
-    p.add_argument("--requests", type=int, default=40)
-    p.add_argument("--warmup-requests", type=int, default=5)
+    p.add_argument("--requests", type=int, default=24, help="served requests timed (after the warm-up ones)")
+    p.add_argument("--warmup-requests", type=int, default=4)
+    p.add_argument("--grad-reps", type=int, default=3, help="timed repeats of the fwd+adjoint leg")
     p.add_argument("--rate", type=float, default=200.0, help="Poisson arrival rate (requests/s)")
     return p.parse_args()
 
@@ -184,16 +194,42 @@ def _adjoint_flops_per_env(lanes):
     return rec["fp64_flops_per_launch"] / rec["envs"]
 
 
-def _traffic(kernel_lanes):
-    """DRAM bytes per launch of the persistent kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
+def _forward_record(kernel_lanes):
+    """The committed ncu record of the persistent kernel (DRAM bytes and FP64
+    thread operations per launch), if it was taken on the current kernel
+    sources with the same lane count (else None)."""
     path = os.path.join(ROOT, "profiles", "rollout_persistent_box_push.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     if rec.get("source_sha256") != _sources_sha(FORWARD_SOURCES) or rec.get("lanes") != kernel_lanes:
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
+
+
+def cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def stats_ms(times):
+    """Median and p90 (ms) of a list of per-step times (ms)."""
+    a = np.asarray(times, dtype=np.float64)
+    return float(np.median(a)), float(np.percentile(a, 90))
 
 
 # ------------------------------------------------------------------ CPU (oracle) timing
@@ -265,7 +301,7 @@ def run_ours(args):
             assert int((out["status"] != 0).sum().item()) == 0, "environment failed"
     torch.cuda.synchronize()
     barrier(world)
-    ms = float(np.mean(times))
+    ms, ms_p90 = stats_ms(times)
     ms_max = reduce_max(ms, world, dev)
     steps_all = reduce_sum(nsteps, world, dev)
     value = steps_all / (ms_max * 1e-3)
@@ -281,22 +317,32 @@ def run_ours(args):
         r = dmx.rollout_host(model, x0_h, T_h, lanes=lanes, xT=xT_h, **kw)
         e2e_t.append(time.perf_counter() - t0)
         e2e_steps = int(r["nsteps"].sum())
-    e2e_s = reduce_max(float(np.mean(e2e_t)), world, dev)
+    e2e_s = reduce_max(float(np.median(e2e_t)), world, dev)
     e2e = {"value": reduce_sum(e2e_steps, world, dev) / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(x0_h.numel() * 8 + T_h.numel() * 8),
            "d2h_bytes_per_step": int(xT_h.numel() * 8 + 4096 * 4 * 2)}
 
     result = None
     if rank == 0:
+        peak, peak_shapes = dmx.fp64_peak()
         achieved = nsteps * FLOP_PER_STEP / (ms * 1e-3) / 1e12
-        peak = FP64_PEAK_GFLOPS / 1e3
+        rec = _forward_record(lanes)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": _traffic(lanes), "peak_note": "FP64: 152 SMs x 4 flop/clk x 2070 MHz (derived); "
-                    "1.203 TFLOP/s measured with a DFMA microbenchmark", "kernel": f"k_rollout_persistent<{lanes}>",
-                    "flop_per_env_step": FLOP_PER_STEP}
+                    "traffic": rec.get("dram_bytes_per_launch") if rec else None,
+                    "peak_source": "measured in this run: FP64 FMA probe kernel (dmx_fp64_peak), best launch shape "
+                                   "of " + ", ".join(f"{k} {v:.3f}" for k, v in peak_shapes.items()) + " TFLOP/s; "
+                                   f"derived 152 SMs x 4 flop/clk x 2.07 GHz = {FP64_PEAK_DERIVED_GFLOPS / 1e3:.3f}",
+                    "kernel": f"k_rollout_persistent<{lanes}>", "flop_per_env_step": FLOP_PER_STEP,
+                    "flop_per_env_step_with_cold_search": FLOP_PER_STEP_SEARCH}
+        if rec and rec.get("fp64_flops_per_launch"):
+            ex = rec["fp64_flops_per_launch"] / (ms * 1e-3) / 1e12
+            roofline["executed"] = {"achieved": ex, "frac": ex / peak, "flop_per_env_step":
+                                    rec["fp64_flops_per_launch"] / max(1, rec.get("env_steps", nsteps)),
+                                    "source": "ncu FP64 thread operations (2 DFMA + DMUL + DADD), "
+                                              "profiles/rollout_persistent_box_push.json"}
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                  "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                  "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded box pushes)",
+                  "warmup": args.warmup, "ms_per_step": ms_max, "ms_p90": ms_p90, "higher_is_better": True,
+                  "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded box pushes)",
                   "config": dict(WORKLOAD, form=args.form, lanes=lanes, parallelism=f"env shards x{world}",
                                  l2="flushed (256 MB write) between timed steps",
                                  env_steps_per_batch=nsteps, autotune_ms=tuned or None),
@@ -314,20 +360,27 @@ def run_ours(args):
                 t = e0.elapsed_time(e1)
                 extra[form] = {"value": int(out["nsteps"].sum().item()) / (t * 1e-3), "ms_per_step": t}
             result["plain_forms"] = extra
-            result["fwd_adjoint"] = grad_leg(dmx, dev, B=args.grad_envs, adj_lanes=args.adj_lanes)
+            result["fwd_adjoint"] = grad_leg(dmx, dev, B=args.grad_envs, adj_lanes=args.adj_lanes,
+                                             reps=args.grad_reps, peak=peak)
+            result["serving"] = serving_leg(dmx, W, requests=args.requests, warmup=args.warmup_requests,
+                                            rate=args.rate)
             rate, sample, cores, _ = oracle_rate(inp)
-            result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+            rate1, sample1, _, _ = oracle_rate(inp, budget_s=0.0, first=32, max_envs=32, nthreads=1)
+            result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                                      "cpu": cpu_model(), "one_thread": {"value": rate1, "sample": sample1}}
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return result
 
 
-def grad_leg(dmx, dev, B=16384, adj_lanes=0):
+def grad_leg(dmx, dev, B=16384, adj_lanes=0, reps=3, peak=None, parity_envs=(0, 5)):
     """Forward (taped) + discrete adjoint (reverse-mode kernel, autotuned lanes)
     of the arm-pushes-cube workload (7 hinges + free cube, 50 torque intervals
     over 2 s, K = 32), loss = squared cube-to-goal distance, on the first B of
-    the 16384 environments (all of them by default)."""
+    the 16384 environments (all of them by default): `reps` timed repeats
+    (median and p90), and the gradient of `parity_envs` against the CPU
+    oracle's discrete adjoint along the GPU's step sizes."""
     import torch
     from paper_2506_14186_gb300 import autotune
     from paper_2506_14186_gb300 import workloads as W
@@ -351,32 +404,71 @@ def grad_leg(dmx, dev, B=16384, adj_lanes=0):
     w = dmx.rollout(m, x0, torch.clamp(T, max=0.05), ctrl=ctrl, NI=50, K=32, tape=True)
     dmx.rollout_grad(w["tape"], torch.zeros_like(w["xT"]))
     del w
-    torch.cuda.synchronize()
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    e0.record(st)
-    out = dmx.rollout(m, x0, T, ctrl=ctrl, NI=50, K=32, tape=True)
-    e1.record(st)
-    xT_bar = torch.zeros_like(out["xT"])
-    xT_bar[7:10] = 2 * (out["xT"][7:10] - goal)
-    gx, gu = dmx.rollout_grad(out["tape"], xT_bar)
-    e2.record(st)
-    e2.synchronize()
-    t_f, t_all = e0.elapsed_time(e1) * 1e-3, e0.elapsed_time(e2) * 1e-3
+    t_fwd, t_adj, t_tot = [], [], []
+    for _ in range(max(1, reps)):
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        out = dmx.rollout(m, x0, T, ctrl=ctrl, NI=50, K=32, tape=True)
+        e1.record(st)
+        xT_bar = torch.zeros_like(out["xT"])
+        xT_bar[7:10] = 2 * (out["xT"][7:10] - goal)
+        gx, gu = dmx.rollout_grad(out["tape"], xT_bar)
+        e2.record(st)
+        e2.synchronize()
+        t_fwd.append(e0.elapsed_time(e1))
+        t_tot.append(e0.elapsed_time(e2))
+        t_adj.append(t_tot[-1] - t_fwd[-1])
     steps = int(out["nsteps"].sum().item())
-    fpe = _adjoint_flops_per_env(adj_lanes)
+    t_all = float(np.median(t_tot)) * 1e-3
+    t_f = float(np.median(t_fwd)) * 1e-3
+    t_a = float(np.median(t_adj)) * 1e-3
     adj_roof = None
-    if fpe is not None:
-        achieved = fpe * B / (t_all - t_f) / 1e12
-        peak = FP64_PEAK_GFLOPS / 1e3
+    if peak:
+        achieved = ARM_ADJ_FLOP_PER_STEP * steps / t_a / 1e12
         adj_roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "kernel": f"k_adjoint_rev<{adj_lanes}>",
-                    "work": "FP64 thread operations counted by ncu (2 DFMA + DMUL + DADD) per environment, "
-                            "profiles/adjoint_rev_chain_cube.json"}
+                    "kernel": f"k_adjoint_rev<{adj_lanes}>", "flop_per_env_step": ARM_ADJ_FLOP_PER_STEP,
+                    "work": "oracle count: every accepted step once in the counting derivative scalar "
+                            "(recompute + linearised step), python -m oracle.count_flops chain_cube"}
+        fpe = _adjoint_flops_per_env(adj_lanes)
+        if fpe is not None:
+            ex = fpe * B / t_a / 1e12
+            adj_roof["executed"] = {"achieved": ex, "frac": ex / peak,
+                                    "source": "ncu FP64 thread operations, profiles/adjoint_rev_chain_cube.json"}
+    parity = None
+    if parity_envs:
+        parity = _grad_parity(m, out, xT_bar, gx, gu, inp, sc, list(parity_envs))
     return {"workload": "chain_cube (7 hinges + cube, NI=50, T=2 s, K=32)", "envs": B, "adjoint_roofline": adj_roof,
             "grad_rollouts_per_s": B / t_all, "env_steps_per_s": steps / t_all, "forward_s": t_f,
-            "adjoint_s": t_all - t_f, "env_steps": steps, "adjoint_kernel": "reverse",
+            "adjoint_s": t_a, "total_s_median": t_all, "total_s_p90": float(np.percentile(t_tot, 90)) * 1e-3,
+            "reps": len(t_tot), "env_steps": steps, "adjoint_kernel": "reverse",
+            "forward_frac": (ARM_FLOP_PER_STEP * steps / t_f / 1e12 / peak) if peak else None,
             "lanes": {"forward": fwd_lanes, "adjoint": adj_lanes, "adjoint_tuning_ms": adj_ms},
-            "finite": bool(torch.isfinite(gu).all().item())}
+            "finite": bool(torch.isfinite(gu).all().item()), "parity_vs_oracle": parity}
+
+
+def _grad_parity(m, out, xT_bar, gx, gu, inp, scene, envs):
+    """Largest relative gradient error of the sampled environments against the
+    CPU oracle's discrete adjoint along the GPU's accepted step sizes
+    (componentwise |g - o| / max(|o|, ||o||_inf))."""
+    import torch
+
+    import oracle
+    hlog, n = out["tape"].read()
+    idx = torch.tensor(envs, device=hlog.device)
+    n = n[idx].cpu().numpy()
+    hl = hlog[: int(n.max()), idx].cpu().numpy().T
+    om = oracle.OracleModel(scene)
+    o = om.batch_replay_grad(inp["x0"][envs], inp["T"][envs], hl, n, xT_bar.cpu().numpy().T[envs],
+                             ctrl=inp["ctrl"][envs], NI=inp["NI"])
+    g_x = gx.cpu().numpy().T[envs]
+    g_u = np.transpose(gu.cpu().numpy(), (2, 0, 1))[envs]
+
+    def rel(a, b):
+        a, b = a.reshape(len(envs), -1), b.reshape(len(envs), -1)
+        scale = np.maximum(np.maximum(np.abs(b), np.abs(b).max(axis=1, keepdims=True)), 1e-300)
+        return float(np.max(np.abs(a - b) / scale))
+    return {"envs": envs, "x0_bar": rel(g_x, o["x0_bar"]), "ctrl_bar": rel(g_u, o["ctrl_bar"]), "bar": 1e-6}
 
 
 # ------------------------------------------------------------------ every workload
@@ -576,19 +668,24 @@ def make_requests(n, seed=5005):
     return reqs
 
 
-def run_serving(args):
+def serving_leg(dmx, W, requests=40, warmup=5, rate=200.0, seed=5005):
+    """Served MPC requests (seeded mix, Poisson arrivals at `rate`): latency
+    (submit -> outputs in the caller's host buffers) and rollouts/s of three
+    arms on the same requests and arrival times:
+      continuous_batching  -- the request server (dmx_submit / dmx_poll): requests
+                              admitted as slots and memory free up, kernels of
+                              concurrent requests overlap on the device;
+      sequential_persistent -- no server: one request at a time in arrival order,
+                              the same fused persistent kernels;
+      plain_per_request    -- one request at a time, forward pass by one launch
+                              per step attempt (plain form).
+    Latency of the sequential arms is counted from the arrival time."""
     import torch
-
-    import paper_2506_14186_gb300 as dmx
-    from paper_2506_14186_gb300 import _build
-    from paper_2506_14186_gb300 import workloads as W
-    _build.build()
-    torch.cuda.set_device(0)
     models = {n: dmx.Model(W.SCENES[n]()) for n in ("ball", "box", "chain_cube")}
-    total = args.warmup_requests + args.requests
-    reqs = make_requests(total)
-    g = np.random.default_rng(77)
-    arrivals = np.cumsum(g.exponential(1.0 / args.rate, total))
+    total = warmup + requests
+    reqs = make_requests(total, seed=seed)
+    g = np.random.default_rng(seed + 72)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, total))
     host = []
     for r in reqs:
         m = models[r["name"]]
@@ -625,41 +722,53 @@ def run_serving(args):
         srv.close()
         return lat, makespan
 
-    def plain():
-        """One request at a time in arrival order, forward pass by per-attempt
-        launches (plain form); latency counted from the arrival time."""
-        dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
-        t0 = time.perf_counter()
-        lat = {}
-        for j in range(total):
-            while time.perf_counter() - t0 < arrivals[j]:
-                time.sleep(1e-4)
-            m, x0, T, ctrl, xb = host[j]
-            r = reqs[j]
-            out = dmx.rollout(m, dev(x0), dev(T), ctrl=None if ctrl is None else dev(ctrl), NI=r["NI"], form="step",
-                              tape=r["grad"])
-            if r["grad"]:
-                gx, gu = dmx.rollout_grad(out["tape"], dev(xb))
-                gx.cpu()
-            out["xT"].cpu()
-            lat[j] = time.perf_counter() - t0 - arrivals[j]
-        return lat, time.perf_counter() - t0
+    def sequential(form):
+        def run():
+            dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+            t0 = time.perf_counter()
+            lat = {}
+            for j in range(total):
+                while time.perf_counter() - t0 < arrivals[j]:
+                    time.sleep(1e-4)
+                m, x0, T, ctrl, xb = host[j]
+                r = reqs[j]
+                out = dmx.rollout(m, dev(x0), dev(T), ctrl=None if ctrl is None else dev(ctrl), NI=r["NI"], form=form,
+                                  tape=r["grad"])
+                if r["grad"]:
+                    gx, gu = dmx.rollout_grad(out["tape"], dev(xb))
+                    gx.cpu()
+                out["xT"].cpu()
+                lat[j] = time.perf_counter() - t0 - arrivals[j]
+            return lat, time.perf_counter() - t0
+        return run
 
     res = {}
-    for name, fn in (("continuous_batching", served), ("plain_per_request", plain)):
+    for name, fn in (("continuous_batching", served), ("sequential_persistent", sequential("persistent")),
+                     ("plain_per_request", sequential("step"))):
         lat, makespan = fn()
-        vals = np.array([lat[j] for j in range(args.warmup_requests, total)])
+        vals = np.array([lat[j] for j in range(warmup, total)])
         rollouts = sum(reqs[j]["B"] for j in range(total))
         res[name] = {"p50_s": float(np.percentile(vals, 50)), "p99_s": float(np.percentile(vals, 99)),
                      "mean_s": float(vals.mean()), "rollouts_per_s": rollouts / makespan, "makespan_s": makespan}
+    res["config"] = {"arrivals": f"Poisson {rate}/s", "requests": requests, "warmup_requests": warmup,
+                     "mix": "ball/box/chain_cube uniform, B~U{64..1024}, T~U[0.2,2] s, 50% fwd+adjoint"}
+    return res
+
+
+def run_serving(args):
+    import torch
+
+    import paper_2506_14186_gb300 as dmx
+    from paper_2506_14186_gb300 import _build
+    from paper_2506_14186_gb300 import workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    res = serving_leg(dmx, W, requests=args.requests, warmup=args.warmup_requests, rate=args.rate)
     head = res["continuous_batching"]
     return {"metric": METRIC, "value": head["p50_s"], "unit": "s (p50 request latency)", "n_gpus": 1,
             "higher_is_better": False, "steps": args.requests, "warmup": args.warmup_requests,
             "dtype": "f64", "data": "synthetic (seeded request mix)", "vs_baseline": None,
-            "config": {"workload": "served MPC requests", "arrivals": f"Poisson {args.rate}/s",
-                       "mix": "ball/box/chain_cube uniform, B~U{64..1024}, T~U[0.2,2] s, 50% fwd+adjoint",
-                       "requests": args.requests, "warmup_requests": args.warmup_requests},
-            "serving": res}
+            "config": {"workload": "served MPC requests", **res["config"]}, "serving": res}
 
 
 def main():

@@ -223,10 +223,15 @@ typedef struct {
   int64_t device_bytes;       /* admission budget for request state (tapes, staging) */
   int32_t max_inflight;       /* concurrent requests on the device */
   int32_t nstreams;           /* CUDA streams the server overlaps requests on */
+  int64_t host_stage_bytes;   /* page-locked host staging, split into max_inflight equal blocks (one per
+                                 in-flight request); 0 = 32 MiB per in-flight request */
 } dmx_server_cfg;
 
 /* A request owns its host buffers until dmx_poll reports it done.  Host
- * pointers (pinned memory recommended); layouts as in dmx_rollout_args. */
+ * pointers, pageable or pinned; layouts as in dmx_rollout_args.  The server
+ * copies the inputs into its own page-locked block when it admits the
+ * request and the outputs out of it when the device work has finished, so
+ * no copy of one request waits for the device work of another. */
 typedef struct {
   dmx_model* model;
   int32_t B, NI, max_steps, K;
@@ -243,9 +248,15 @@ typedef struct {
   int32_t* status;            /* out [B] or NULL */
 } dmx_request;
 
+/* Continuous batching (served MPC requests): dmx_submit queues a request and
+ * returns at once; a worker thread admits queued requests in arrival order as
+ * soon as an in-flight slot and enough of the device budget are free (also
+ * while others run) and issues each on one of the server's streams, where its
+ * kernels overlap with those of the requests already on the device. */
 dmx_status dmx_server_create(const dmx_server_cfg* cfg, dmx_server** out);
 /* Queues the request (non-blocking).  Admitted to the device once its memory
- * fits the budget and a slot is free.  DMX_ERR_INVALID if it can never fit. */
+ * fits the budget and a slot is free.  DMX_ERR_INVALID if it can never fit
+ * (device budget, or the host staging block of one in-flight request). */
 dmx_status dmx_submit(dmx_server* s, const dmx_request* r, uint64_t* ticket);
 /* DMX_OK when the request's outputs are in its host buffers, DMX_NOT_READY
  * while it runs; non-blocking.  latency_s (optional) = submit -> completion. */
@@ -297,6 +308,16 @@ dmx_status dmx_eval_rhs(dmx_model* m, int32_t B, const double* q, const double* 
 dmx_status dmx_eval_rhs_vjp(dmx_model* m, int32_t B, const double* q, const double* v, const double* u,
                             const double* abar, int32_t cfd, int32_t lanes, double* qbar, double* vbar, double* ubar,
                             int32_t* status, void* stream);
+
+/* FP64 throughput probe (the paper has no counterpart: it measures the
+ * machine).  Launches blocks x threads threads on `stream`, each running
+ * eight independent FP64 fused multiply-add chains of `iters` links: one
+ * launch performs 16 * blocks * threads * iters FP64 flops.  The caller
+ * times it (CUDA events on `stream`) to obtain the FP64 peak that the
+ * rollout and adjoint kernels are reported against.  sink: a device double
+ * the kernel may write (it never does for these inputs).  threads must be a
+ * multiple of 32 in [32, 1024]; DMX_ERR_INVALID otherwise. */
+dmx_status dmx_fp64_peak(int32_t blocks, int32_t threads, int32_t iters, double* sink, void* stream);
 
 const char* dmx_last_error(void);
 

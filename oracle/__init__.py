@@ -63,6 +63,7 @@ def lib():
         L.orc_pair_invw.restype = ctypes.c_double
         L.orc_impedance.restype = ctypes.c_double
         L.orc_count_flops.restype = ctypes.c_longlong
+        L.orc_count_adjoint_flops.restype = ctypes.c_longlong
         L.orc_step_error.restype = ctypes.c_double
         L.orc_error_norm.restype = ctypes.c_double
         _lib = L
@@ -240,11 +241,24 @@ class OracleModel:
         return {"xT": xT, "x0_bar": gx, "ctrl_bar": gu[:NI * self.nu].reshape(NI, self.nu), "status": int(st[0]),
                 "nsteps": int(st[1])}
 
-    def count_flops(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000):
+    def count_flops(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, search=True):
+        """FP64 operations of one adaptive rollout (counting scalar).  search=False
+        counts each constraint solve as started at its final active set (one
+        Newton system plus one residual check) instead of the oracle's search
+        from the unconstrained acceleration."""
         st = np.zeros(4, dtype=np.int32)
         c = _f64(ctrl) if ctrl is not None else _f64(np.zeros(max(NI * self.nu, 1)))
         n = lib().orc_count_flops(self.h, _p(_f64(x0)), _p(c), ctypes.c_double(T), NI, ctypes.c_double(rtol),
-                                  ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(st))
+                                  ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(st), int(bool(search)))
+        return int(n), {"status": int(st[0]), "nsteps": int(st[1]), "nrej": int(st[2]), "nrhs": int(st[3])}
+
+    def count_adjoint_flops(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000):
+        """FP64 operations of the discrete adjoint of one rollout: every accepted
+        step evaluated once with one tangent (primal recompute + linearised step)."""
+        st = np.zeros(4, dtype=np.int32)
+        c = _f64(ctrl) if ctrl is not None else _f64(np.zeros(max(NI * self.nu, 1)))
+        n = lib().orc_count_adjoint_flops(self.h, _p(_f64(x0)), _p(c), ctypes.c_double(T), NI, ctypes.c_double(rtol),
+                                          ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(st))
         return int(n), {"status": int(st[0]), "nsteps": int(st[1]), "nrej": int(st[2]), "nrhs": int(st[3])}
 
     # ---------------------------------------------------------------- batched (env-major arrays)

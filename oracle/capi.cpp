@@ -266,17 +266,51 @@ int orc_batch_grad(void* h, int B, const double* x0, const double* ctrl, const d
 }
 
 // Floating-point operations of one adaptive rollout (counted scalar type).
+// search = 1: the constraint solver's active-set search from the unconstrained
+// acceleration is counted; 0: the solve is counted as started at its final
+// active set (one Newton system and one residual check per right-hand side).
 long long orc_count_flops(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol, double atol,
-                          double h0, int max_steps, int* stats) {
+                          double h0, int max_steps, int* stats, int search) {
   Model& m = M(h);
   const int nx = m.nq + m.nv, nu = m.nu;
   std::vector<Cnt> xc(nx), uc((size_t)std::max(1, NI * nu)), xTc(nx);
   for (int i = 0; i < nx; ++i) xc[i] = Cnt(x0[i]);
   for (int i = 0; i < NI * nu; ++i) uc[i] = Cnt(ctrl[i]);
   g_flops = 0;
+  g_count_search = search;
   Result r = rollout<Cnt>(m, xc.data(), uc.data(), make_opts(T, NI, rtol, atol, h0, max_steps), xTc.data(), nullptr,
                           nullptr, nullptr, nullptr, 0);
   put_stats(r, stats);
+  return (long long)g_flops;
+}
+
+// Algorithmic work of the discrete adjoint of one rollout: for every accepted
+// step, the step evaluated once in the counting derivative scalar (value and
+// one tangent: the primal recompute plus the linearised step; by the
+// transposition principle the reverse sweep of a linear map costs the same
+// multiply-adds as the forward one).  The active-set searches are not counted
+// (the derivative type searches in plain doubles).
+long long orc_count_adjoint_flops(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol,
+                                  double atol, double h0, int max_steps, int* stats) {
+  using D = Dual<Cnt>;
+  Model& m = M(h);
+  const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
+  std::vector<StepRec> rec;
+  std::vector<double> xT(nx);
+  Result r = rollout<double>(m, x0, ctrl, make_opts(T, NI, rtol, atol, h0, max_steps), xT.data(), nullptr, &rec,
+                             nullptr, nullptr, 0);
+  put_stats(r, stats);
+  std::vector<D> qd(nq), vd(nv), ud(std::max(nu, 1)), a1(nv), q7(nq), v7(nv), a7(nv), e(2 * nv);
+  g_flops = 0;
+  g_count_search = 0;
+  for (const StepRec& s : rec) {
+    for (int i = 0; i < nq; ++i) qd[i] = D(Cnt(s.q[i]), Cnt(1.0));
+    for (int i = 0; i < nv; ++i) vd[i] = D(Cnt(s.v[i]), Cnt(1.0));
+    for (int i = 0; i < nu; ++i) ud[i] = D(Cnt(ctrl[(size_t)s.k * nu + i]), Cnt(1.0));
+    StageRhs<D> f{m, false};
+    f(qd.data(), vd.data(), ud.data(), a1.data());
+    dopri5_step(m, f, qd.data(), vd.data(), a1.data(), ud.data(), s.h, q7.data(), v7.data(), a7.data(), e.data());
+  }
   return (long long)g_flops;
 }
 

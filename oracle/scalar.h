@@ -18,23 +18,28 @@ namespace orc {
 
 // ---------------------------------------------------------------- Cnt
 extern thread_local std::int64_t g_flops;
+// While > 0, operations are not counted (used to leave the constraint solver's
+// active-set search out of the algorithmic count; see solve_constraints).
+extern thread_local int g_flops_paused;
+// 1: count the active-set search from the unconstrained acceleration too.
+extern thread_local int g_count_search;
 
 struct Cnt {
   double v;
   Cnt() : v(0) {}
   Cnt(double x) : v(x) {}
 };
-inline Cnt operator+(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v + b.v); }
-inline Cnt operator-(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v - b.v); }
-inline Cnt operator*(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v * b.v); }
-inline Cnt operator/(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v / b.v); }
+inline Cnt operator+(Cnt a, Cnt b) { g_flops += !g_flops_paused; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { g_flops += !g_flops_paused; return Cnt(a.v - b.v); }
+inline Cnt operator*(Cnt a, Cnt b) { g_flops += !g_flops_paused; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { g_flops += !g_flops_paused; return Cnt(a.v / b.v); }
 inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
-inline Cnt sqrt(Cnt a) { ++g_flops; return Cnt(std::sqrt(a.v)); }
-inline Cnt sin(Cnt a) { ++g_flops; return Cnt(std::sin(a.v)); }
-inline Cnt cos(Cnt a) { ++g_flops; return Cnt(std::cos(a.v)); }
-inline Cnt exp(Cnt a) { ++g_flops; return Cnt(std::exp(a.v)); }
-inline Cnt log1p(Cnt a) { ++g_flops; return Cnt(std::log1p(a.v)); }
-inline Cnt pow(Cnt a, double p) { ++g_flops; return Cnt(std::pow(a.v, p)); }
+inline Cnt sqrt(Cnt a) { g_flops += !g_flops_paused; return Cnt(std::sqrt(a.v)); }
+inline Cnt sin(Cnt a) { g_flops += !g_flops_paused; return Cnt(std::sin(a.v)); }
+inline Cnt cos(Cnt a) { g_flops += !g_flops_paused; return Cnt(std::cos(a.v)); }
+inline Cnt exp(Cnt a) { g_flops += !g_flops_paused; return Cnt(std::exp(a.v)); }
+inline Cnt log1p(Cnt a) { g_flops += !g_flops_paused; return Cnt(std::log1p(a.v)); }
+inline Cnt pow(Cnt a, double p) { g_flops += !g_flops_paused; return Cnt(std::pow(a.v, p)); }
 inline Cnt fabs(Cnt a) { return Cnt(std::fabs(a.v)); }
 
 // ---------------------------------------------------------------- Dual

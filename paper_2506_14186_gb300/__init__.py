@@ -37,7 +37,7 @@ _ACT = {"motor": 0, "position": 1}
 ABI_SYMBOLS = ("dmx_create_model", "dmx_destroy_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad",
                "dmx_tape_free", "dmx_tape_read", "dmx_autotune", "dmx_set_lanes", "dmx_model_info", "dmx_server_create", "dmx_submit", "dmx_poll",
                "dmx_server_destroy", "dmx_eval_rhs", "dmx_rollout_static", "dmx_set_adjoint", "dmx_eval_rhs_vjp",
-               "dmx_last_error")
+               "dmx_fp64_peak", "dmx_last_error")
 
 
 class BodyDesc(ctypes.Structure):
@@ -73,7 +73,8 @@ class RolloutArgs(ctypes.Structure):
 
 
 class ServerCfg(ctypes.Structure):
-    _fields_ = [("device_bytes", ctypes.c_int64), ("max_inflight", c_i32), ("nstreams", c_i32)]
+    _fields_ = [("device_bytes", ctypes.c_int64), ("max_inflight", c_i32), ("nstreams", c_i32),
+                ("host_stage_bytes", ctypes.c_int64)]
 
 
 class Request(ctypes.Structure):
@@ -101,7 +102,7 @@ def lib():
         for name in ("dmx_create_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad", "dmx_autotune",
                      "dmx_server_create", "dmx_submit", "dmx_poll", "dmx_server_destroy", "dmx_model_info",
                      "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read", "dmx_rollout_static", "dmx_set_adjoint",
-                     "dmx_eval_rhs_vjp"):
+                     "dmx_eval_rhs_vjp", "dmx_fp64_peak"):
             getattr(L, name).restype = c_i32
         L.dmx_destroy_model.restype = None
         L.dmx_tape_free.restype = None
@@ -353,6 +354,32 @@ def rollout_static(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3,
     return xT, nsteps, status
 
 
+def fp64_peak(configs=((4, 512), (8, 256), (2, 1024), (16, 128)), iters=8192, reps=3, stream=None):
+    """Measured FP64 throughput of this GPU (TFLOP/s): the DFMA probe kernel
+    timed with CUDA events on the stream, best over launch shapes (blocks per
+    SM, threads) and repetitions.  Returns (tflops, {shape: tflops})."""
+    import torch
+    dev = torch.cuda.current_device()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    h = _stream_handle(st)
+    res = {}
+    for per_sm, threads in configs:
+        blocks = per_sm * nsm
+        _check(lib().dmx_fp64_peak(blocks, threads, iters, _ptr(sink), h))      # warm-up
+        best = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _check(lib().dmx_fp64_peak(blocks, threads, iters, _ptr(sink), h))
+            e1.record(st)
+            e1.synchronize()
+            best = max(best, 16.0 * blocks * threads * iters / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        res[f"{per_sm}x{threads}"] = best
+    return max(res.values()), res
+
+
 def _rollout_fn_class():
     import torch
 
@@ -401,8 +428,8 @@ class Server:
     device as slots and memory free up; poll() returns the outputs (host
     arrays) and the submit-to-completion latency once a request is done."""
 
-    def __init__(self, device_bytes=8 << 30, max_inflight=8, nstreams=8):
-        cfg = ServerCfg(int(device_bytes), int(max_inflight), int(nstreams))
+    def __init__(self, device_bytes=8 << 30, max_inflight=8, nstreams=8, host_stage_bytes=0):
+        cfg = ServerCfg(int(device_bytes), int(max_inflight), int(nstreams), int(host_stage_bytes))
         h = c_p()
         _check(lib().dmx_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h

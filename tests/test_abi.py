@@ -38,3 +38,4 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(dmx.PairDesc) == 16 + 8
     assert ctypes.sizeof(dmx.ActDesc) == 8 + 24
     assert ctypes.sizeof(dmx.RolloutArgs) % 8 == 0
+    assert ctypes.sizeof(dmx.ServerCfg) == 8 + 4 + 4 + 8

@@ -267,3 +267,80 @@ def test_reverse_kernel_equals_tangent_kernel(dmx, name):
         # (the final active set, hence the Newton system, is the same)
         c = res["recompute"][k].cpu().numpy().reshape(-1, len(inp["T"])).T
         np.testing.assert_array_equal(a, c)
+
+
+def _oracle_along(orc_mod, scene, inp, idx, hlog, n, xT_bar, NI):
+    m = orc_mod.OracleModel(scene)
+    ctrl = None if inp["ctrl"] is None else inp["ctrl"][idx]
+    return m.batch_replay_grad(inp["x0"][idx], inp["T"][idx], hlog, n, xT_bar, ctrl=ctrl, NI=NI)
+
+
+def test_arm_gradient_at_the_benchmark_configuration(dmx, orc_mod):
+    """The fwd+adjoint benchmark as it is timed: arm + cube, all 16384
+    environments, T = 2 s, 50 torque intervals, K = 32, persistent forward and
+    reverse adjoint with autotuned lanes; cotangent = gradient of the squared
+    cube-to-goal distance plus a random cotangent on every final coordinate.
+    Six sampled environments (four where the arm reaches the cube) against
+    the oracle's discrete adjoint along the GPU's step sizes: 1e-6 on x0_bar
+    and on all 350 control gradients.  (The oracle's own conditioning floor at
+    this horizon is below 1e-7: tests/test_oracle_adjoint.py.)"""
+    import torch
+    from paper_2506_14186_gb300 import autotune
+    sc, inp = W.chain_cube_scene(), W.chain_inputs(16384)
+    B = 16384
+    m = dmx.Model(sc)
+    x0, T = _dev(inp["x0"].T), _dev(inp["T"])
+    ctrl = _dev(np.transpose(inp["ctrl"], (1, 2, 0)))
+    fl, _ = autotune.tune_forward(m, x0, torch.clamp(T, max=0.2), ctrl=ctrl, NI=50, candidates=(8, 16, 32))
+    autotune.tune_adjoint(m, x0, T, ctrl=ctrl, NI=50, K=32)
+    m.set_lanes(B, fl)
+    m.set_adjoint("reverse")
+    out = dmx.rollout(m, x0, T, ctrl=ctrl, NI=50, K=32, tape=True)
+    assert int((out["status"] != 0).sum().item()) == 0
+    rnd = torch.tensor(np.random.default_rng(21).normal(size=(27, B)) * 0.1, device="cuda")
+    xT_bar = rnd.clone()
+    xT_bar[7:10] += 2 * (out["xT"][7:10] - torch.tensor(W.chain_goal(), device="cuda")[:, None])
+    gx, gu = dmx.rollout_grad(out["tape"], xT_bar)
+    idx = np.array([0, 5, 7, 11, 8195, 16383])
+    hlog, n = out["tape"].read()
+    n = n.cpu().numpy()[idx]
+    hl = hlog[: int(n.max()), torch.tensor(idx, device="cuda")].cpu().numpy().T
+    o = _oracle_along(orc_mod, sc, inp, idx, hl, n, xT_bar.cpu().numpy().T[idx], NI=50)
+    g = {"x0_bar": gx.cpu().numpy().T[idx], "ctrl_bar": np.transpose(gu.cpu().numpy(), (2, 0, 1))[idx]}
+    assert np.count_nonzero(np.abs(o["ctrl_bar"]).reshape(len(idx), -1).max(axis=1) > 1e-3) >= 4
+    assert_grad(g, o)
+    assert_grad(g, o, "ctrl_bar")
+
+
+def test_quadruped_gradient_at_full_horizons(dmx, orc_mod):
+    """Quadruped at its workload's batch (8192 robots, horizons U[0.5, 3] s,
+    autotuned lanes and checkpoint interval): the three robots with the
+    longest horizons (~3 s, ~4000 steps each) against the oracle's discrete
+    adjoint along the GPU's step sizes, 1e-6 (the oracle's conditioning floor
+    there is ~1e-8)."""
+    import torch
+    from paper_2506_14186_gb300 import autotune
+    sc, inp = W.quadruped_scene(), W.quadruped_inputs(8192)
+    B = 8192
+    m = dmx.Model(sc)
+    x0, T = _dev(inp["x0"].T), _dev(inp["T"])
+    ctrl = _dev(np.transpose(inp["ctrl"], (1, 2, 0)))
+    kw = dict(ctrl=ctrl, NI=1)
+    fl, _ = autotune.tune_forward(m, x0, torch.clamp(T, max=0.25), **kw)
+    autotune.tune_adjoint(m, x0, T, K=32, **kw)
+    K, _ = autotune.tune_checkpoint(m, x0, T, **kw)
+    m.set_lanes(B, fl)
+    m.set_adjoint("reverse")
+    out = dmx.rollout(m, x0, T, K=K, tape=True, **kw)
+    assert int((out["status"] != 0).sum().item()) == 0
+    xT_bar = torch.zeros_like(out["xT"])
+    xT_bar[0:3] = 1.0
+    gx, gu = dmx.rollout_grad(out["tape"], xT_bar)
+    idx = np.sort(np.argsort(-inp["T"])[:3])
+    hlog, n = out["tape"].read()
+    n = n.cpu().numpy()[idx]
+    hl = hlog[: int(n.max()), torch.tensor(idx, device="cuda")].cpu().numpy().T
+    o = _oracle_along(orc_mod, sc, inp, idx, hl, n, xT_bar.cpu().numpy().T[idx], NI=1)
+    g = {"x0_bar": gx.cpu().numpy().T[idx], "ctrl_bar": np.transpose(gu.cpu().numpy(), (2, 0, 1))[idx]}
+    assert_grad(g, o)
+    assert_grad(g, o, "ctrl_bar")

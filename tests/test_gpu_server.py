@@ -91,3 +91,25 @@ def test_memory_budget_admission(dmx):
     with pytest.raises(dmx.DmxError, match="server budget"):
         srv.submit(m, np.ascontiguousarray(big["x0"].T), np.ascontiguousarray(big["T"]))
     srv.close()
+
+
+def test_concurrent_requests_overlap_on_the_device(dmx):
+    """Requests admitted together run at the same time: four requests of 64
+    box pushes (T = 1 s, each far from filling the GPU), submitted at once
+    with pageable numpy buffers, all complete within 2x the latency of one
+    request alone (issued one after another they would take ~4x), and each
+    result equals the one of the request alone."""
+    m = dmx.Model(W.box_scene())
+    inp = W.box_push_inputs(64, T=1.0)
+    x0, T = np.ascontiguousarray(inp["x0"].T), np.ascontiguousarray(inp["T"])
+    srv = dmx.Server(device_bytes=4 << 30, max_inflight=8, nstreams=8)
+    srv.wait(srv.submit(m, x0, T), timeout=300)                   # warm-up (lane choice, pools)
+    alone = [srv.wait(srv.submit(m, x0, T), timeout=300) for _ in range(2)]
+    t_alone = min(a["latency_s"] for a in alone)
+    tickets = [srv.submit(m, x0, T) for _ in range(4)]
+    outs = [srv.wait(t, timeout=300) for t in tickets]
+    srv.close()
+    t_four = max(o["latency_s"] for o in outs)
+    assert t_four < 2.0 * t_alone, (t_four, t_alone)
+    for o in outs:
+        np.testing.assert_array_equal(o["xT"], alone[0]["xT"])

@@ -233,3 +233,35 @@ def test_gradient_conditioning_floor(orc):
         floors[T] = worst
     assert floors[0.1] < 1e-8, floors
     assert floors[0.3] > 1e-7, floors
+
+
+def test_arm_gradient_conditioning_floor_at_full_horizon(orc):
+    """The same question for the arm pushing the cube over its full 2 s
+    horizon (50 torque intervals, as timed by the benchmark): the control and
+    x0 gradients of the squared cube-to-goal distance plus a random cotangent
+    on the final coordinates, at x0 and at x0 moved by 1e-15 (relative and
+    absolute), along the same step sizes, move by less than 1e-7.  So the
+    1e-6 gradient bar can be checked at the full horizon."""
+    sc = W.chain_cube_scene()
+    m = orc.OracleModel(sc)
+    inp = W.chain_inputs(16384)
+    idx = np.array([0, 5])                       # the arm reaches the cube in both
+    x0, ctrl, T = inp["x0"][idx], inp["ctrl"][idx], inp["T"][idx]
+    H, N, xT = [], [], []
+    for e in range(len(idx)):
+        r = m.rollout(x0[e], ctrl=ctrl[e], T=float(T[e]), NI=50)
+        assert r["status"] == 0
+        H.append(r["hlog"]); N.append(r["nsteps"]); xT.append(r["xT"])
+    hl = np.zeros((len(idx), max(N)))
+    for e in range(len(idx)):
+        hl[e, :N[e]] = H[e]
+    xT_bar = 0.1 * np.random.default_rng(9).normal(size=(len(idx), m.nx))
+    xT_bar[:, 7:10] += 2 * (np.array(xT)[:, 7:10] - W.chain_goal())
+    g0 = m.batch_replay_grad(x0, T, hl, N, xT_bar, ctrl=ctrl, NI=50)
+    assert np.abs(g0["ctrl_bar"]).max() > 0
+    rng = np.random.default_rng(10)
+    x1 = x0 * (1 + 1e-15 * rng.normal(size=x0.shape)) + 1e-15 * rng.normal(size=x0.shape)
+    g1 = m.batch_replay_grad(x1, T, hl, N, xT_bar, ctrl=ctrl, NI=50)
+    floor = max(max(rel_err(g1["ctrl_bar"][e].ravel(), g0["ctrl_bar"][e].ravel()),
+                    rel_err(g1["x0_bar"][e], g0["x0_bar"][e])) for e in range(len(idx)))
+    assert 0 < floor < 1e-7, floor
