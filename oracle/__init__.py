@@ -37,6 +37,8 @@ JOINT = {"free": 0, "hinge": 1}
 GEOM = {"sphere": 0, "capsule": 1, "box": 2}
 ACT = {"motor": 0, "position": 1}
 STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "nonfinite", 4: "solver_noconv"}
+# integration schemes: adaptive Dormand-Prince 5(4) and Tsitouras 5(4), fixed-step semi-implicit Euler
+METHODS = {"dopri5": 0, "tsit5": 1, "euler": 2}
 
 
 def build(force: bool = False) -> str:
@@ -195,11 +197,11 @@ class OracleModel:
         lib().orc_integrate_pos(self.h, _p(_f64(q)), _p(_f64(dlt)), _p(out))
         return out
 
-    def step_error(self, x, h, u=None, rtol=1e-6, atol=1e-8):
-        """Error norm of one DOPRI5 attempt of size h from x (accepted iff <= 1)."""
+    def step_error(self, x, h, u=None, rtol=1e-6, atol=1e-8, method="dopri5"):
+        """Error norm of one attempt of size h from x (accepted iff <= 1; 0 for a fixed-step scheme)."""
         u = _f64(u if u is not None else np.zeros(max(self.nu, 1)))
         return lib().orc_step_error(self.h, _p(_f64(x)), _p(u), ctypes.c_double(h), ctypes.c_double(rtol),
-                                    ctypes.c_double(atol))
+                                    ctypes.c_double(atol), METHODS[method])
 
     def error_norm(self, q0, v0, q1, v1, e, rtol=1e-6, atol=1e-8):
         """The controller's error norm of an embedded difference e (2 nv tangent
@@ -207,41 +209,46 @@ class OracleModel:
         return lib().orc_error_norm(self.h, _p(_f64(q0)), _p(_f64(v0)), _p(_f64(q1)), _p(_f64(v1)), _p(_f64(e)),
                                     ctypes.c_double(rtol), ctypes.c_double(atol))
 
-    def step_jacobian(self, q, v, u, h, cfd=False):
+    def step_jacobian(self, q, v, u, h, cfd=False, method="dopri5"):
         Jx = np.zeros((self.nx, self.nx)); Ju = np.zeros((self.nx, max(self.nu, 1)))
         u = _f64(u if u is not None else np.zeros(max(self.nu, 1)))
-        lib().orc_step_jacobian(self.h, _p(_f64(q)), _p(_f64(v)), _p(u), ctypes.c_double(h), int(cfd), _p(Jx), _p(Ju))
+        lib().orc_step_jacobian(self.h, _p(_f64(q)), _p(_f64(v)), _p(u), ctypes.c_double(h), int(cfd), _p(Jx), _p(Ju),
+                                METHODS[method])
         return Jx, Ju[:, :self.nu]
 
     # ---------------------------------------------------------------- rollouts (one env)
-    def rollout(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, hcap=200000):
+    def rollout(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, hcap=200000,
+                method="dopri5"):
         xT = np.zeros(self.nx); xb = np.zeros((NI + 1, self.nx)); st = np.zeros(4, dtype=np.int32)
         hlog = np.zeros(hcap)
         c = _f64(ctrl) if ctrl is not None else _f64(np.zeros(max(NI * self.nu, 1)))
         n = lib().orc_rollout(self.h, _p(_f64(x0)), _p(c), ctypes.c_double(T), NI, ctypes.c_double(rtol),
-                              ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(xT), _p(xb), _p(st), _p(hlog), hcap)
+                              ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(xT), _p(xb), _p(st), _p(hlog), hcap,
+                              METHODS[method])
         return {"xT": xT, "xb": xb, "status": int(st[0]), "nsteps": int(st[1]), "nrej": int(st[2]),
                 "nrhs": int(st[3]), "hlog": hlog[:min(n, hcap)].copy()}
 
-    def replay(self, x0, hlog, ctrl=None, T=1.0, NI=1):
+    def replay(self, x0, hlog, ctrl=None, T=1.0, NI=1, method="dopri5"):
         xT = np.zeros(self.nx); xb = np.zeros((NI + 1, self.nx))
         c = _f64(ctrl) if ctrl is not None else _f64(np.zeros(max(NI * self.nu, 1)))
         hl = _f64(hlog)
-        lib().orc_replay(self.h, _p(_f64(x0)), _p(c), ctypes.c_double(T), NI, _p(hl), len(hl), _p(xT), _p(xb))
+        lib().orc_replay(self.h, _p(_f64(x0)), _p(c), ctypes.c_double(T), NI, _p(hl), len(hl), _p(xT), _p(xb),
+                         METHODS[method])
         return xT, xb
 
     def rollout_grad(self, x0, xT_bar, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000,
-                     cfd=False, xb_bar=None):
+                     cfd=False, xb_bar=None, method="dopri5"):
         xT = np.zeros(self.nx); gx = np.zeros(self.nx); gu = np.zeros(max(NI * self.nu, 1)); st = np.zeros(4, dtype=np.int32)
         c = _f64(ctrl) if ctrl is not None else _f64(np.zeros(max(NI * self.nu, 1)))
         xbb = _f64(xb_bar) if xb_bar is not None else None
         lib().orc_rollout_grad(self.h, _p(_f64(x0)), _p(c), ctypes.c_double(T), NI, ctypes.c_double(rtol),
                                ctypes.c_double(atol), ctypes.c_double(h0), max_steps, int(cfd), _p(_f64(xT_bar)),
-                               _p(xbb), _p(xT), _p(gx), _p(gu), _p(st))
+                               _p(xbb), _p(xT), _p(gx), _p(gu), _p(st), METHODS[method])
         return {"xT": xT, "x0_bar": gx, "ctrl_bar": gu[:NI * self.nu].reshape(NI, self.nu), "status": int(st[0]),
                 "nsteps": int(st[1])}
 
-    def count_flops(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, search=True):
+    def count_flops(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, search=True,
+                    method="dopri5"):
         """FP64 operations of one adaptive rollout (counting scalar).  search=False
         counts each constraint solve as started at its final active set (one
         Newton system plus one residual check) instead of the oracle's search
@@ -249,21 +256,24 @@ class OracleModel:
         st = np.zeros(4, dtype=np.int32)
         c = _f64(ctrl) if ctrl is not None else _f64(np.zeros(max(NI * self.nu, 1)))
         n = lib().orc_count_flops(self.h, _p(_f64(x0)), _p(c), ctypes.c_double(T), NI, ctypes.c_double(rtol),
-                                  ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(st), int(bool(search)))
+                                  ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(st), int(bool(search)),
+                                  METHODS[method])
         return int(n), {"status": int(st[0]), "nsteps": int(st[1]), "nrej": int(st[2]), "nrhs": int(st[3])}
 
-    def count_adjoint_flops(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000):
+    def count_adjoint_flops(self, x0, ctrl=None, T=1.0, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000,
+                            method="dopri5"):
         """FP64 operations of the discrete adjoint of one rollout: every accepted
         step evaluated once with one tangent (primal recompute + linearised step)."""
         st = np.zeros(4, dtype=np.int32)
         c = _f64(ctrl) if ctrl is not None else _f64(np.zeros(max(NI * self.nu, 1)))
         n = lib().orc_count_adjoint_flops(self.h, _p(_f64(x0)), _p(c), ctypes.c_double(T), NI, ctypes.c_double(rtol),
-                                          ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(st))
+                                          ctypes.c_double(atol), ctypes.c_double(h0), max_steps, _p(st),
+                                          METHODS[method])
         return int(n), {"status": int(st[0]), "nsteps": int(st[1]), "nrej": int(st[2]), "nrhs": int(st[3])}
 
     # ---------------------------------------------------------------- batched (env-major arrays)
     def batch_rollout(self, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, nthreads=None,
-                      want_xb=False):
+                      want_xb=False, method="dopri5"):
         x0 = _f64(x0)
         B = x0.shape[0]
         xT = np.zeros((B, self.nx)); st = np.zeros((B, 4), dtype=np.int32)
@@ -271,11 +281,12 @@ class OracleModel:
         c = _f64(ctrl) if (ctrl is not None and self.nu) else None
         lib().orc_batch_rollout(self.h, B, _p(x0), _p(c), _p(_f64(np.broadcast_to(T, (B,)))), NI,
                                 ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_double(h0), max_steps,
-                                _p(xT), _p(xb), _p(st), int(nthreads or os.cpu_count() or 1))
+                                _p(xT), _p(xb), _p(st), int(nthreads or os.cpu_count() or 1), METHODS[method])
         return {"xT": xT, "xb": xb, "status": st[:, 0].copy(), "nsteps": st[:, 1].copy(), "nrej": st[:, 2].copy(),
                 "nrhs": st[:, 3].copy()}
 
-    def batch_replay_grad(self, x0, T, hlog, n, xT_bar, ctrl=None, NI=1, cfd=False, xb_bar=None, nthreads=None):
+    def batch_replay_grad(self, x0, T, hlog, n, xT_bar, ctrl=None, NI=1, cfd=False, xb_bar=None, nthreads=None,
+                          method="dopri5"):
         """Discrete adjoint along given accepted step sizes (hlog [B, >= max n], n [B])."""
         x0 = _f64(x0)
         B = x0.shape[0]
@@ -287,11 +298,11 @@ class OracleModel:
         lib().orc_batch_replay_grad(self.h, B, _p(x0), _p(c), _p(_f64(np.broadcast_to(T, (B,)))), NI, _p(hlog),
                                     hlog.shape[1], _p(n), int(cfd), _p(_f64(xT_bar)),
                                     _p(_f64(xb_bar) if xb_bar is not None else None), _p(xT), _p(gx), _p(gu),
-                                    int(nthreads or os.cpu_count() or 1))
+                                    int(nthreads or os.cpu_count() or 1), METHODS[method])
         return {"xT": xT, "x0_bar": gx, "ctrl_bar": gu}
 
     def batch_grad(self, x0, T, xT_bar, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, cfd=False,
-                   xb_bar=None, nthreads=None):
+                   xb_bar=None, nthreads=None, method="dopri5"):
         x0 = _f64(x0)
         B = x0.shape[0]
         xT = np.zeros((B, self.nx)); gx = np.zeros((B, self.nx)); st = np.zeros((B, 4), dtype=np.int32)
@@ -300,12 +311,20 @@ class OracleModel:
         lib().orc_batch_grad(self.h, B, _p(x0), _p(c), _p(_f64(np.broadcast_to(T, (B,)))), NI,
                              ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_double(h0), max_steps, int(cfd),
                              _p(_f64(xT_bar)), _p(_f64(xb_bar) if xb_bar is not None else None), _p(xT), _p(gx),
-                             _p(gu), _p(st), int(nthreads or os.cpu_count() or 1))
+                             _p(gu), _p(st), int(nthreads or os.cpu_count() or 1), METHODS[method])
         return {"xT": xT, "x0_bar": gx, "ctrl_bar": gu, "status": st[:, 0].copy(), "nsteps": st[:, 1].copy()}
 
 
-def tableau():
-    """The DOPRI5 coefficients the oracle integrates with (a 7x7, b, bhat, c)."""
-    a = np.zeros(49); b = np.zeros(7); bh = np.zeros(7); c = np.zeros(7)
-    lib().orc_tableau(_p(a), _p(b), _p(bh), _p(c))
-    return a.reshape(7, 7), b, bh, c
+def tableau(method="dopri5"):
+    """Coefficients the oracle integrates with: (a 7x7, b, bhat, c) of the
+    explicit scheme (position coefficients equal to the velocity ones), or
+    with partitioned=True style access through tableau_full."""
+    t = tableau_full(method)
+    return t["av"], t["b"], t["bhat"], t["c"]
+
+
+def tableau_full(method="dopri5"):
+    """All coefficients of a scheme: stages S, aq and av (7x7), b, bhat, c."""
+    aq = np.zeros(49); av = np.zeros(49); b = np.zeros(7); bh = np.zeros(7); c = np.zeros(7)
+    S = lib().orc_tableau(METHODS[method], _p(aq), _p(av), _p(b), _p(bh), _p(c))
+    return {"S": int(S), "aq": aq.reshape(7, 7), "av": av.reshape(7, 7), "b": b, "bhat": bh, "c": c}

@@ -27,9 +27,10 @@ template <class Fn> void parallel_for(int n, int nthreads, Fn fn) {
     });
   for (auto& x : th) x.join();
 }
-Opts make_opts(double T, int NI, double rtol, double atol, double h0, int max_steps) {
+Opts make_opts(double T, int NI, double rtol, double atol, double h0, int max_steps, int method) {
   Opts o;
   o.T = T; o.NI = NI; o.rtol = rtol; o.atol = atol; o.h0 = h0; o.max_steps = max_steps;
+  o.method = (method >= METHOD_DOPRI5 && method <= METHOD_EULER) ? method : METHOD_DOPRI5;
   return o;
 }
 void put_stats(const Result& r, int* s) { s[0] = r.status; s[1] = r.nsteps; s[2] = r.nrej; s[3] = r.nrhs; }
@@ -57,12 +58,15 @@ void orc_dims(void* h, int* out) {
 double orc_body_invw(void* h, int b) { return M(h).body_invw[b]; }
 double orc_pair_invw(void* h, int p) { return M(h).pair[p].invw; }
 
-void orc_tableau(double* a, double* b, double* bhat, double* c) {
-  const Tableau& t = dopri5();
+// Coefficients of scheme `method`: aq, av (7 x 7), b, bhat, c; returns the
+// number of stages (stage 0 included).
+int orc_tableau(int method, double* aq, double* av, double* b, double* bhat, double* c) {
+  const Tableau& t = tableau_of(method);
   for (int i = 0; i < 7; ++i) {
-    for (int j = 0; j < 7; ++j) a[7 * i + j] = t.a[i][j];
+    for (int j = 0; j < 7; ++j) { aq[7 * i + j] = t.aq[i][j]; av[7 * i + j] = t.av[i][j]; }
     b[i] = t.b[i]; bhat[i] = t.bhat[i]; c[i] = t.c[i];
   }
+  return t.S;
 }
 
 int orc_kinematics(void* h, const double* q, double* R, double* p, double* com) {
@@ -179,15 +183,17 @@ int orc_rhs_jacobian(void* h, const double* q, const double* v, const double* u,
 void orc_integrate_pos(void* h, const double* q, const double* dlt, double* out) { integrate_pos<double>(M(h), q, dlt, out); }
 
 int orc_rollout(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol, double atol, double h0,
-                int max_steps, double* xT, double* xb, int* stats, double* hlog, int hcap) {
+                int max_steps, double* xT, double* xb, int* stats, double* hlog, int hcap, int method) {
   std::vector<double> hl;
-  Result r = rollout<double>(M(h), x0, ctrl, make_opts(T, NI, rtol, atol, h0, max_steps), xT, xb, nullptr, &hl, nullptr, 0);
+  Result r = rollout<double>(M(h), x0, ctrl, make_opts(T, NI, rtol, atol, h0, max_steps, method), xT, xb, nullptr, &hl,
+                             nullptr, 0);
   put_stats(r, stats);
   if (hlog) for (int i = 0; i < std::min<int>(hcap, (int)hl.size()); ++i) hlog[i] = hl[i];
   return (int)hl.size();
 }
-int orc_replay(void* h, const double* x0, const double* ctrl, double T, int NI, const double* hlog, int n, double* xT, double* xb) {
-  Result r = rollout<double>(M(h), x0, ctrl, make_opts(T, NI, 0, 0, 0, 0), xT, xb, nullptr, nullptr, hlog, n);
+int orc_replay(void* h, const double* x0, const double* ctrl, double T, int NI, const double* hlog, int n, double* xT,
+               double* xb, int method) {
+  Result r = rollout<double>(M(h), x0, ctrl, make_opts(T, NI, 0, 0, 0, 0, method), xT, xb, nullptr, nullptr, hlog, n);
   return r.nsteps;
 }
 // Error norm of a given embedded difference e (2 nv tangent components)
@@ -199,27 +205,29 @@ double orc_error_norm(void* h, const double* q0, const double* v0, const double*
 }
 // Error norm of one DOPRI5 attempt of size hs from x = [q; v] (controls u):
 // the value the adaptive controller compares with 1.
-double orc_step_error(void* h, const double* x, const double* u, double hs, double rtol, double atol) {
+double orc_step_error(void* h, const double* x, const double* u, double hs, double rtol, double atol, int method) {
   Model& m = M(h);
   const int nq = m.nq, nv = m.nv;
   std::vector<double> a1(nv), q7(nq), v7(nv), a7(nv), e(2 * nv);
   StageRhs<double> f{m, false};
   f(x, x + nq, u, a1.data());
-  dopri5_step(m, f, x, x + nq, a1.data(), u, hs, q7.data(), v7.data(), a7.data(), e.data());
+  rk_step(m, tableau_of(method), f, x, x + nq, a1.data(), u, hs, q7.data(), v7.data(), a7.data(), e.data());
   return error_norm<double>(m, x, x + nq, q7.data(), v7.data(), e.data(), rtol, atol);
 }
-int orc_step_jacobian(void* h, const double* q, const double* v, const double* u, double hs, int cfd, double* Jx, double* Ju) {
+int orc_step_jacobian(void* h, const double* q, const double* v, const double* u, double hs, int cfd, double* Jx,
+                      double* Ju, int method) {
   Model& m = M(h);
   std::vector<double> A, B;
-  step_jacobian(m, q, v, u, hs, cfd != 0, A, B);
+  step_jacobian(m, q, v, u, hs, cfd != 0, A, B, method);
   std::copy(A.begin(), A.end(), Jx);
   if (Ju && m.nu) std::copy(B.begin(), B.end(), Ju);
   return 0;
 }
 int orc_rollout_grad(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol, double atol,
                      double h0, int max_steps, int cfd, const double* xT_bar, const double* xb_bar, double* xT,
-                     double* x0_bar, double* ctrl_bar, int* stats) {
-  Result r = rollout_grad(M(h), x0, ctrl, make_opts(T, NI, rtol, atol, h0, max_steps), cfd != 0, xT_bar, xb_bar, xT, x0_bar, ctrl_bar);
+                     double* x0_bar, double* ctrl_bar, int* stats, int method) {
+  Result r = rollout_grad(M(h), x0, ctrl, make_opts(T, NI, rtol, atol, h0, max_steps, method), cfd != 0, xT_bar, xb_bar,
+                          xT, x0_bar, ctrl_bar);
   put_stats(r, stats);
   return 0;
 }
@@ -227,11 +235,11 @@ int orc_rollout_grad(void* h, const double* x0, const double* ctrl, double T, in
 // Gradient along a given accepted step sequence (per environment: hlog[e][0:n[e]]).
 int orc_batch_replay_grad(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, const double* hlog,
                           int hstride, const int* n, int cfd, const double* xT_bar, const double* xb_bar, double* xT,
-                          double* x0_bar, double* ctrl_bar, int nthreads) {
+                          double* x0_bar, double* ctrl_bar, int nthreads, int method) {
   Model& m = M(h);
   const int nx = m.nq + m.nv, nu = m.nu;
   parallel_for(B, nthreads, [&](int b) {
-    rollout_grad(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr, make_opts(T[b], NI, 1, 1, 1, 1 << 30),
+    rollout_grad(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr, make_opts(T[b], NI, 1, 1, 1, 1 << 30, method),
                  cfd != 0, xT_bar + (size_t)b * nx, xb_bar ? xb_bar + (size_t)b * (NI + 1) * nx : nullptr,
                  xT + (size_t)b * nx, x0_bar + (size_t)b * nx, ctrl_bar ? ctrl_bar + (size_t)b * NI * nu : nullptr,
                  hlog + (size_t)b * hstride, n[b]);
@@ -239,12 +247,12 @@ int orc_batch_replay_grad(void* h, int B, const double* x0, const double* ctrl, 
   return 0;
 }
 int orc_batch_rollout(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, double rtol,
-                      double atol, double h0, int max_steps, double* xT, double* xb, int* stats, int nthreads) {
+                      double atol, double h0, int max_steps, double* xT, double* xb, int* stats, int nthreads, int method) {
   Model& m = M(h);
   const int nx = m.nq + m.nv, nu = m.nu;
   parallel_for(B, nthreads, [&](int b) {
     Result r = rollout<double>(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr,
-                               make_opts(T[b], NI, rtol, atol, h0, max_steps), xT + (size_t)b * nx,
+                               make_opts(T[b], NI, rtol, atol, h0, max_steps, method), xT + (size_t)b * nx,
                                xb ? xb + (size_t)b * (NI + 1) * nx : nullptr, nullptr, nullptr, nullptr, 0);
     put_stats(r, stats + 4 * b);
   });
@@ -252,12 +260,12 @@ int orc_batch_rollout(void* h, int B, const double* x0, const double* ctrl, cons
 }
 int orc_batch_grad(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, double rtol,
                    double atol, double h0, int max_steps, int cfd, const double* xT_bar, const double* xb_bar,
-                   double* xT, double* x0_bar, double* ctrl_bar, int* stats, int nthreads) {
+                   double* xT, double* x0_bar, double* ctrl_bar, int* stats, int nthreads, int method) {
   Model& m = M(h);
   const int nx = m.nq + m.nv, nu = m.nu;
   parallel_for(B, nthreads, [&](int b) {
     Result r = rollout_grad(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr,
-                            make_opts(T[b], NI, rtol, atol, h0, max_steps), cfd != 0, xT_bar + (size_t)b * nx,
+                            make_opts(T[b], NI, rtol, atol, h0, max_steps, method), cfd != 0, xT_bar + (size_t)b * nx,
                             xb_bar ? xb_bar + (size_t)b * (NI + 1) * nx : nullptr, xT + (size_t)b * nx,
                             x0_bar + (size_t)b * nx, ctrl_bar ? ctrl_bar + (size_t)b * NI * nu : nullptr);
     put_stats(r, stats + 4 * b);
@@ -270,7 +278,7 @@ int orc_batch_grad(void* h, int B, const double* x0, const double* ctrl, const d
 // acceleration is counted; 0: the solve is counted as started at its final
 // active set (one Newton system and one residual check per right-hand side).
 long long orc_count_flops(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol, double atol,
-                          double h0, int max_steps, int* stats, int search) {
+                          double h0, int max_steps, int* stats, int search, int method) {
   Model& m = M(h);
   const int nx = m.nq + m.nv, nu = m.nu;
   std::vector<Cnt> xc(nx), uc((size_t)std::max(1, NI * nu)), xTc(nx);
@@ -278,7 +286,7 @@ long long orc_count_flops(void* h, const double* x0, const double* ctrl, double 
   for (int i = 0; i < NI * nu; ++i) uc[i] = Cnt(ctrl[i]);
   g_flops = 0;
   g_count_search = search;
-  Result r = rollout<Cnt>(m, xc.data(), uc.data(), make_opts(T, NI, rtol, atol, h0, max_steps), xTc.data(), nullptr,
+  Result r = rollout<Cnt>(m, xc.data(), uc.data(), make_opts(T, NI, rtol, atol, h0, max_steps, method), xTc.data(), nullptr,
                           nullptr, nullptr, nullptr, 0);
   put_stats(r, stats);
   return (long long)g_flops;
@@ -291,13 +299,14 @@ long long orc_count_flops(void* h, const double* x0, const double* ctrl, double 
 // multiply-adds as the forward one).  The active-set searches are not counted
 // (the derivative type searches in plain doubles).
 long long orc_count_adjoint_flops(void* h, const double* x0, const double* ctrl, double T, int NI, double rtol,
-                                  double atol, double h0, int max_steps, int* stats) {
+                                  double atol, double h0, int max_steps, int* stats, int method) {
   using D = Dual<Cnt>;
   Model& m = M(h);
   const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
   std::vector<StepRec> rec;
   std::vector<double> xT(nx);
-  Result r = rollout<double>(m, x0, ctrl, make_opts(T, NI, rtol, atol, h0, max_steps), xT.data(), nullptr, &rec,
+  const Opts o = make_opts(T, NI, rtol, atol, h0, max_steps, method);
+  Result r = rollout<double>(m, x0, ctrl, o, xT.data(), nullptr, &rec,
                              nullptr, nullptr, 0);
   put_stats(r, stats);
   std::vector<D> qd(nq), vd(nv), ud(std::max(nu, 1)), a1(nv), q7(nq), v7(nv), a7(nv), e(2 * nv);
@@ -309,7 +318,8 @@ long long orc_count_adjoint_flops(void* h, const double* x0, const double* ctrl,
     for (int i = 0; i < nu; ++i) ud[i] = D(Cnt(ctrl[(size_t)s.k * nu + i]), Cnt(1.0));
     StageRhs<D> f{m, false};
     f(qd.data(), vd.data(), ud.data(), a1.data());
-    dopri5_step(m, f, qd.data(), vd.data(), a1.data(), ud.data(), s.h, q7.data(), v7.data(), a7.data(), e.data());
+    rk_step(m, tableau_of(o.method), f, qd.data(), vd.data(), a1.data(), ud.data(), s.h, q7.data(), v7.data(), a7.data(),
+            e.data());
   }
   return (long long)g_flops;
 }

@@ -8,6 +8,8 @@
 //   App. B.1 (Fig. 12) PID step-size controller with P = 0.2, I = 0.4, D = 0
 //   App. C.2           Dormand-Prince 5(4) (cited there) with quaternions
 //                      integrated exactly; discretize-then-optimize gradient
+//   Fig. 12, Sec. 3.1  Tsitouras 5(4) (the paper's default solver) and the
+//                      fixed-step semi-implicit Euler of MuJoCo XLA
 //   Sec. 4 (ST)        x' = sg(F) + F~ - sg(F~): values from F, derivatives
 //                      from F~ evaluated on the F trajectory
 // Step sizes of accepted steps are held constant in the derivative; rejected
@@ -20,30 +22,98 @@
 
 namespace orc {
 
-// Dormand & Prince (1980) 5(4) tableau; row 7 equals the 5th-order weights
-// (first-same-as-last), bhat are the embedded 4th-order weights.
+// Explicit one-step schemes on (q, v) as partitioned tableaus.  Stage s
+// (s = 1 .. S-1) takes
+//   V_s = v_n + h sum_{j<s} av[s][j] K_j,
+//   Q_s = q_n (+) h sum_{j<=s} aq[s][j] V_j   (V_0 = v_n; a diagonal entry uses
+//                                             the stage's own new velocity),
+//   K_s = F(Q_s, V_s, u),
+// and the last stage is the step's result (its K is the next step's K_0,
+// first-same-as-last).  Adaptive schemes carry the weights e = b - bhat of the
+// embedded error estimate.
+enum { METHOD_DOPRI5 = 0, METHOD_TSIT5 = 1, METHOD_EULER = 2 };
 struct Tableau {
-  double a[7][7];
-  double b[7], bhat[7], c[7];
+  int S = 7;                      // stage evaluations per step, stage 0 included
+  bool adaptive = true;
+  double aq[7][7] = {}, av[7][7] = {};
+  double b[7] = {}, bhat[7] = {}, c[7] = {};
 };
+
+// Dormand & Prince (1980) 5(4); row 7 equals the 5th-order weights (FSAL),
+// bhat are the embedded 4th-order weights.
 inline const Tableau& dopri5() {
   static const Tableau T = [] {
     Tableau t{};
-    t.a[1][0] = 1.0 / 5.0;
-    t.a[2][0] = 3.0 / 40.0; t.a[2][1] = 9.0 / 40.0;
-    t.a[3][0] = 44.0 / 45.0; t.a[3][1] = -56.0 / 15.0; t.a[3][2] = 32.0 / 9.0;
-    t.a[4][0] = 19372.0 / 6561.0; t.a[4][1] = -25360.0 / 2187.0; t.a[4][2] = 64448.0 / 6561.0; t.a[4][3] = -212.0 / 729.0;
-    t.a[5][0] = 9017.0 / 3168.0; t.a[5][1] = -355.0 / 33.0; t.a[5][2] = 46732.0 / 5247.0; t.a[5][3] = 49.0 / 176.0;
-    t.a[5][4] = -5103.0 / 18656.0;
-    t.a[6][0] = 35.0 / 384.0; t.a[6][1] = 0.0; t.a[6][2] = 500.0 / 1113.0; t.a[6][3] = 125.0 / 192.0;
-    t.a[6][4] = -2187.0 / 6784.0; t.a[6][5] = 11.0 / 84.0;
-    for (int j = 0; j < 7; ++j) t.b[j] = (j < 6) ? t.a[6][j] : 0.0;
+    double (&a)[7][7] = t.av;
+    a[1][0] = 1.0 / 5.0;
+    a[2][0] = 3.0 / 40.0; a[2][1] = 9.0 / 40.0;
+    a[3][0] = 44.0 / 45.0; a[3][1] = -56.0 / 15.0; a[3][2] = 32.0 / 9.0;
+    a[4][0] = 19372.0 / 6561.0; a[4][1] = -25360.0 / 2187.0; a[4][2] = 64448.0 / 6561.0; a[4][3] = -212.0 / 729.0;
+    a[5][0] = 9017.0 / 3168.0; a[5][1] = -355.0 / 33.0; a[5][2] = 46732.0 / 5247.0; a[5][3] = 49.0 / 176.0;
+    a[5][4] = -5103.0 / 18656.0;
+    a[6][0] = 35.0 / 384.0; a[6][1] = 0.0; a[6][2] = 500.0 / 1113.0; a[6][3] = 125.0 / 192.0;
+    a[6][4] = -2187.0 / 6784.0; a[6][5] = 11.0 / 84.0;
+    for (int i = 0; i < 7; ++i)
+      for (int j = 0; j < 7; ++j) t.aq[i][j] = a[i][j];
+    for (int j = 0; j < 7; ++j) t.b[j] = (j < 6) ? a[6][j] : 0.0;
     const double bh[7] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
     const double c[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
     for (int j = 0; j < 7; ++j) { t.bhat[j] = bh[j]; t.c[j] = c[j]; }
     return t;
   }();
   return T;
+}
+
+// Tsitouras (2011) 5(4), the paper's default solver (Fig. 12): FSAL, row 7 =
+// the 5th-order weights; e = b - bhat given directly (the pair's published
+// error weights), bhat = b - e.
+inline const Tableau& tsit5() {
+  static const Tableau T = [] {
+    Tableau t{};
+    double (&a)[7][7] = t.av;
+    a[1][0] = 0.161;
+    a[2][0] = -0.008480655492356989; a[2][1] = 0.335480655492357;
+    a[3][0] = 2.897153057105493; a[3][1] = -6.359448489975075; a[3][2] = 4.3622954328695815;
+    a[4][0] = 5.325864828439257; a[4][1] = -11.748883564062828; a[4][2] = 7.4955393428898365;
+    a[4][3] = -0.09249506636175525;
+    a[5][0] = 5.86145544294642; a[5][1] = -12.92096931784711; a[5][2] = 8.159367898576159;
+    a[5][3] = -0.071584973281401; a[5][4] = -0.028269050394068383;
+    a[6][0] = 0.09646076681806523; a[6][1] = 0.01; a[6][2] = 0.4798896504144996; a[6][3] = 1.379008574103742;
+    a[6][4] = -3.290069515436081; a[6][5] = 2.324710524099774;
+    for (int i = 0; i < 7; ++i)
+      for (int j = 0; j < 7; ++j) t.aq[i][j] = a[i][j];
+    const double e[7] = {-0.00178001105222577714, -0.0008164344596567469, 0.007880878010261995, -0.1447110071732629,
+                         0.5823571654525552, -0.45808210592918697, 0.015151515151515152};
+    const double c[7] = {0.0, 0.161, 0.327, 0.9, 0.9800255409045097, 1.0, 1.0};
+    for (int j = 0; j < 7; ++j) {
+      t.b[j] = (j < 6) ? a[6][j] : 0.0;
+      t.bhat[j] = t.b[j] - e[j];
+      t.c[j] = c[j];
+    }
+    return t;
+  }();
+  return T;
+}
+
+// Semi-implicit (symplectic) Euler with a fixed step, the default integrator
+// of MuJoCo XLA that the paper compares against (Sec. 3.1, Fig. 12):
+// v_{n+1} = v_n + h F(q_n, v_n), q_{n+1} = q_n (+) h v_{n+1}.  One right-hand
+// side per step; no error estimate.
+inline const Tableau& euler_si() {
+  static const Tableau T = [] {
+    Tableau t{};
+    t.S = 2;
+    t.adaptive = false;
+    t.av[1][0] = 1.0;
+    t.aq[1][1] = 1.0;
+    t.b[0] = 1.0; t.bhat[0] = 1.0; t.c[1] = 1.0;
+    return t;
+  }();
+  return T;
+}
+
+inline const Tableau& tableau_of(int method) {
+  return method == METHOD_TSIT5 ? tsit5() : method == METHOD_EULER ? euler_si() : dopri5();
 }
 
 // q (+) delta: positions advanced by a tangent increment.  Free joint:
@@ -133,39 +203,45 @@ template <> struct StageRhs<Dual<double>> {
   }
 };
 
-// One DOPRI5 attempt of size h from (q, v) with stage-1 derivative a1.
-// Writes the 5th-order solution (q7, v7), its derivative a7 (FSAL) and the
-// embedded difference e (2 nv tangent components).
+// One attempt of size h of the scheme tb from (q, v) with stage-0 derivative
+// a1.  Writes the result (q7, v7), its derivative a7 (FSAL) and, for adaptive
+// schemes, the embedded difference e (2 nv tangent components; zero for a
+// fixed-step scheme).
 template <class S, class R>
-void dopri5_step(const Model& m, R& f, const S* q, const S* v, const S* a1, const S* u, double h,
-                 S* q7, S* v7, S* a7, S* e) {
-  const Tableau& tb = dopri5();
-  const int nv = m.nv, nq = m.nq;
-  std::vector<std::vector<S>> ks_v(7, std::vector<S>(nv)), ks_a(7, std::vector<S>(nv));
+void rk_step(const Model& m, const Tableau& tb, R& f, const S* q, const S* v, const S* a1, const S* u, double h,
+             S* q7, S* v7, S* a7, S* e) {
+  const int nv = m.nv, nq = m.nq, ns = tb.S;
+  std::vector<std::vector<S>> ks_v(ns, std::vector<S>(nv)), ks_a(ns, std::vector<S>(nv));
   for (int i = 0; i < nv; ++i) { ks_v[0][i] = v[i]; ks_a[0][i] = a1[i]; }
   std::vector<S> dq(nv), qs(nq), vs(nv);
-  for (int s = 1; s < 7; ++s) {
+  for (int s = 1; s < ns; ++s) {
     for (int i = 0; i < nv; ++i) {
-      S sq = S(0.0), sv = S(0.0);
+      S sv = S(0.0);
       for (int j = 0; j < s; ++j) {
-        if (tb.a[s][j] == 0.0) continue;
-        sq = sq + tb.a[s][j] * ks_v[j][i];
-        sv = sv + tb.a[s][j] * ks_a[j][i];
+        if (tb.av[s][j] == 0.0) continue;
+        sv = sv + tb.av[s][j] * ks_a[j][i];
+      }
+      vs[i] = v[i] + h * sv;
+      ks_v[s][i] = vs[i];
+    }
+    for (int i = 0; i < nv; ++i) {
+      S sq = S(0.0);
+      for (int j = 0; j <= s; ++j) {
+        if (tb.aq[s][j] == 0.0) continue;
+        sq = sq + tb.aq[s][j] * ks_v[j][i];
       }
       dq[i] = h * sq;
-      vs[i] = v[i] + h * sv;
     }
     integrate_pos(m, q, dq.data(), qs.data());
-    for (int i = 0; i < nv; ++i) ks_v[s][i] = vs[i];
     f(qs.data(), vs.data(), u, ks_a[s].data());
-    if (s == 6) {
+    if (s == ns - 1) {
       for (int i = 0; i < nq; ++i) q7[i] = qs[i];
-      for (int i = 0; i < nv; ++i) { v7[i] = vs[i]; a7[i] = ks_a[6][i]; }
+      for (int i = 0; i < nv; ++i) { v7[i] = vs[i]; a7[i] = ks_a[s][i]; }
     }
   }
   for (int i = 0; i < nv; ++i) {
     S ep = S(0.0), ev = S(0.0);
-    for (int j = 0; j < 7; ++j) {
+    for (int j = 0; j < ns && tb.adaptive; ++j) {
       double w = tb.b[j] - tb.bhat[j];
       if (w == 0.0) continue;
       ep = ep + w * ks_v[j][i];
@@ -176,11 +252,19 @@ void dopri5_step(const Model& m, R& f, const S* q, const S* v, const S* a1, cons
   }
 }
 
+// The Dormand-Prince attempt (the default scheme).
+template <class S, class R>
+void dopri5_step(const Model& m, R& f, const S* q, const S* v, const S* a1, const S* u, double h,
+                 S* q7, S* v7, S* a7, S* e) {
+  rk_step(m, dopri5(), f, q, v, a1, u, h, q7, v7, a7, e);
+}
+
 struct Opts {
   double T = 1.0;
   int NI = 1;
   double rtol = 1e-6, atol = 1e-8, h0 = 1e-3;
   int max_steps = 100000;
+  int method = METHOD_DOPRI5;   // fixed-step schemes take h0 for every step
 };
 struct Result {
   int status = ENV_OK, nsteps = 0, nrej = 0, nrhs = 0;
@@ -209,6 +293,7 @@ Result rollout(const Model& m, const S* x0, const S* ctrl, const Opts& o, S* xT,
   if (xb) for (int i = 0; i < nx; ++i) xb[i] = x0[i];
   if (!finite) { res.status = ENV_NONFINITE; return res; }
   StageRhs<S> f{m, false};
+  const Tableau& tb = tableau_of(o.method);
   auto uk = [&](int k) { return nu ? ctrl + (size_t)k * nu : ctrl; };
   int k = 0;
   double t = 0.0;
@@ -226,10 +311,12 @@ Result rollout(const Model& m, const S* x0, const S* ctrl, const Opts& o, S* xT,
     const double ht = clamped ? hb : h;
     if (!replay && ht < 1e-12) { res.status = ENV_H_UNDERFLOW; break; }
     f.noconv = false;
-    dopri5_step(m, f, q.data(), v.data(), a1.data(), uk(k), ht, q7.data(), v7.data(), a7.data(), e.data());
-    res.nrhs += 6;
+    rk_step(m, tb, f, q.data(), v.data(), a1.data(), uk(k), ht, q7.data(), v7.data(), a7.data(), e.data());
+    res.nrhs += tb.S - 1;
     ++attempts;
-    double err = replay ? 0.0 : val(error_norm<S>(m, q.data(), v.data(), q7.data(), v7.data(), e.data(), o.rtol, o.atol));
+    double err = (replay || !tb.adaptive)
+                     ? 0.0
+                     : val(error_norm<S>(m, q.data(), v.data(), q7.data(), v7.data(), e.data(), o.rtol, o.atol));
     if (err <= 1.0) {
       if (f.noconv) { res.status = ENV_SOLVER_NOCONV; break; }
       if (rec) {
@@ -246,11 +333,15 @@ Result rollout(const Model& m, const S* x0, const S* ctrl, const Opts& o, S* xT,
       q = q7; v = v7; a1 = a7;
       ++res.nsteps;
       ++ir;
-      const double errf = std::max(err, 1e-10);
-      double fac = 0.9 * std::pow(errf, -0.6 / 5.0) * std::pow(err_prev, 0.2 / 5.0);
-      fac = std::min(10.0, std::max(0.2, fac));
-      err_prev = errf;
-      h = ht * fac;
+      if (tb.adaptive) {
+        const double errf = std::max(err, 1e-10);
+        double fac = 0.9 * std::pow(errf, -0.6 / 5.0) * std::pow(err_prev, 0.2 / 5.0);
+        fac = std::min(10.0, std::max(0.2, fac));
+        err_prev = errf;
+        h = ht * fac;
+      } else {
+        h = o.h0;    // fixed step (the last step of an interval may have been shortened)
+      }
       if (reached) {
         if (rec) rec->back().reached = true;
         ++k;
@@ -276,7 +367,7 @@ Result rollout(const Model& m, const S* x0, const S* ctrl, const Opts& o, S* xT,
 // time.  Jx is nx x nx, Ju is nx x nu (row major).  With cfd the derivatives
 // of every stage come from F~ (straight-through).
 inline void step_jacobian(const Model& m, const double* q, const double* v, const double* u, double h, bool cfd,
-                          std::vector<double>& Jx, std::vector<double>& Ju) {
+                          std::vector<double>& Jx, std::vector<double>& Ju, int method = METHOD_DOPRI5) {
   using D = Dual<double>;
   const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
   Jx.assign((size_t)nx * nx, 0.0);
@@ -288,7 +379,8 @@ inline void step_jacobian(const Model& m, const double* q, const double* v, cons
     for (int i = 0; i < nu; ++i) ud[i] = D(u[i], dir == nx + i ? 1.0 : 0.0);
     StageRhs<D> f{m, cfd};
     f(qd.data(), vd.data(), ud.data(), a1.data());
-    dopri5_step(m, f, qd.data(), vd.data(), a1.data(), ud.data(), h, q7.data(), v7.data(), a7.data(), e.data());
+    rk_step(m, tableau_of(method), f, qd.data(), vd.data(), a1.data(), ud.data(), h, q7.data(), v7.data(), a7.data(),
+            e.data());
     for (int i = 0; i < nq; ++i) {
       if (dir < nx) Jx[(size_t)i * nx + dir] = q7[i].d; else Ju[(size_t)i * nu + (dir - nx)] = q7[i].d;
     }
@@ -316,7 +408,7 @@ inline Result rollout_grad(const Model& m, const double* x0, const double* ctrl,
     if (r.reached && xb_bar)
       for (int i = 0; i < nx; ++i) lam[i] += xb_bar[(size_t)(r.k + 1) * nx + i];
     const double* u = nu ? ctrl + (size_t)r.k * nu : ctrl;
-    step_jacobian(m, r.q.data(), r.v.data(), u, r.h, cfd, Jx, Ju);
+    step_jacobian(m, r.q.data(), r.v.data(), u, r.h, cfd, Jx, Ju, o.method);
     if (ctrl_bar)
       for (int j = 0; j < nu; ++j) {
         double s = 0;

@@ -26,11 +26,11 @@ def test_ballistic_gradient_closed_form(orc):
     np.testing.assert_allclose(g, ref, atol=1e-13)
 
 
-def _frozen_fd(m, x0, hlog, wT, ctrl=None, T=1.0, NI=1, eps=1e-6, wb=None):
+def _frozen_fd(m, x0, hlog, wT, ctrl=None, T=1.0, NI=1, eps=1e-6, wb=None, method="dopri5"):
     """Central differences of <wT, xT> (+ sum_k <wb_k, x(t_k)>) of the replayed
     (frozen-step) discrete map w.r.t. x0 and the controls."""
     def L(x, c):
-        xT, xb = m.replay(x, hlog, ctrl=c, T=T, NI=NI)
+        xT, xb = m.replay(x, hlog, ctrl=c, T=T, NI=NI, method=method)
         val = wT @ xT
         if wb is not None:
             val += (wb * xb).sum()
@@ -265,3 +265,31 @@ def test_arm_gradient_conditioning_floor_at_full_horizon(orc):
     floor = max(max(rel_err(g1["ctrl_bar"][e].ravel(), g0["ctrl_bar"][e].ravel()),
                     rel_err(g1["x0_bar"][e], g0["x0_bar"][e])) for e in range(len(idx)))
     assert 0 < floor < 1e-7, floor
+
+
+@pytest.mark.parametrize("method", ["tsit5", "euler"])
+def test_other_schemes_gradient_frozen_steps(orc, method):
+    """The discrete adjoint of the Tsitouras scheme and of fixed-step
+    semi-implicit Euler (h = 1 ms): ball bounce and arm controls against
+    central differences of the replayed map."""
+    m = orc.OracleModel(W.ball_scene())
+    x0 = W.ball_inputs(3, seed=1)["x0"][1]
+    r = m.rollout(x0, T=1.0, method=method)
+    assert r["status"] == 0
+    w = np.zeros(13); w[2] = 1.0; w[7] = 0.3; w[9] = -0.5
+    g = m.rollout_grad(x0, w, T=1.0, method=method)
+    np.testing.assert_array_equal(g["xT"], r["xT"])
+    assert _best_fd_err(m, x0, r["hlog"], w, g, method=method) < 1e-5
+    sc = W.chain_cube_scene()
+    m = orc.OracleModel(sc)
+    inp = W.chain_inputs(1, T=0.2, NI=4)
+    x0, ctrl = inp["x0"][0], inp["ctrl"][0]
+    r = m.rollout(x0, ctrl=ctrl, T=0.2, NI=4, method=method)
+    w = np.random.default_rng(2).normal(size=m.nx)
+    g = m.rollout_grad(x0, w, ctrl=ctrl, T=0.2, NI=4, method=method)
+    arm = list(range(7)) + list(range(14, 21))
+    best = []
+    for eps in (1e-6, 1e-7):
+        fdx, fdu = _frozen_fd(m, x0, r["hlog"], w, ctrl=ctrl, T=0.2, NI=4, eps=eps, method=method)
+        best.append(max(rel_err(g["x0_bar"][arm], fdx[arm]), rel_err(g["ctrl_bar"].ravel(), fdu.ravel())))
+    assert min(best) < 1e-5

@@ -184,3 +184,85 @@ def test_chaos_floor(orc):
         near.append(rel_err(m.replay(xp, r5["hlog"], T=0.05)[0], r5["xT"]))
     assert max(far) > 1e-9
     assert max(near) < 1e-10
+
+
+# ------------------------------------------------------------------ other schemes (Fig. 12, Sec. 3.1)
+def _hinge_scene(damping=0.3):
+    sc = W.chain_cube_scene()
+    sc["bodies"] = [sc["bodies"][0]]
+    sc["bodies"][0]["damping"] = damping
+    sc["geoms"] = [sc["geoms"][0]]
+    sc["pairs"] = []
+    sc["actuators"] = []
+    sc["qpos0"] = [0.0]
+    return sc
+
+
+def test_semi_implicit_euler_closed_form(orc):
+    """Damped hinge, v' = -c v with c = b / I: semi-implicit Euler gives
+    v_n = v0 (1 - h c)^n and q_n = q0 + h sum_{k=1..n} v_k (the position takes
+    the new velocity), exactly; the last step of the horizon is shortened."""
+    m = orc.OracleModel(_hinge_scene())
+    I = m.mass(np.zeros(1))[0, 0]
+    c = 0.3 / I
+    h, T = 0.01, 0.255
+    r = m.rollout(np.array([0.2, 2.0]), T=T, h0=h, method="euler")
+    assert r["status"] == 0 and r["nrej"] == 0
+    hl = r["hlog"]
+    assert len(hl) == 26 and np.all(hl[:25] == h) and abs(hl[25] - 0.005) < 1e-15
+    v, q = 2.0, 0.2
+    for hk in hl:
+        v = v * (1 - hk * c)
+        q = q + hk * v
+    assert abs(r["xT"][1] - v) < 1e-14 and abs(r["xT"][0] - q) < 1e-14
+
+
+def test_tsit5_step_is_the_stability_polynomial(orc):
+    """On the linear damped hinge one Tsit5 step multiplies v by
+    R(z) = 1 + z b^T (I - z A)^-1 1 (z = -h c) of the published tableau."""
+    from tests.test_oracle_tableau import _golden_tsit5
+    a, b, _, _ = _golden_tsit5()
+    m = orc.OracleModel(_hinge_scene())
+    c = 0.3 / m.mass(np.zeros(1))[0, 0]
+    for h in (0.02, 0.05, 0.2, 0.7):                 # z from -0.2 to -7 (outside the stability region)
+        z = -h * c
+        R = 1 + z * b @ np.linalg.solve(np.eye(7) - z * a, np.ones(7))
+        xT, _ = m.replay(np.array([0.0, 1.5]), [h], T=1e3, method="tsit5")
+        assert abs(xT[1] - 1.5 * R) < 1e-13 * max(1.0, abs(1.5 * R))
+
+
+@pytest.mark.parametrize("method,order", [("tsit5", 5), ("euler", 1)])
+def test_convergence_order_of_other_schemes(orc, method, order):
+    """Fixed steps on the torque-free top: the global error of the angular
+    velocity falls by ~2^order per halving of h."""
+    m = orc.OracleModel(_top_scene())
+    w0 = np.array([1.0, 0.5, 4.0])
+    x0 = np.concatenate([[0, 0, 1.0, 1, 0, 0, 0, 0, 0, 0], w0])
+    ns = (32, 64, 128) if order == 5 else (200, 400, 800)
+    errs = []
+    for n in ns:
+        xT, _ = m.replay(x0, np.full(n, 1.0 / n), T=1.0, method=method)
+        errs.append(np.abs(xT[10:13] - _top_exact(w0, 1.0)).max())
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 0.7 * 2 ** order < e1 / e2 < 1.5 * 2 ** order, errs
+
+
+def test_tsit5_adaptive_rollout_and_controller(orc):
+    """Tsit5 with the same PID controller: the ball drop integrates to the
+    closed-form rest height, and on the top the accepted error norms settle
+    at the PI fixed point 0.9^(5/I) like DOPRI5's."""
+    sc = W.ball_scene()
+    m = orc.OracleModel(sc)
+    x0 = np.array([0, 0, 0.3, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0])
+    a = m.rollout(x0, T=3.0)
+    b = m.rollout(x0, T=3.0, method="tsit5")
+    assert b["status"] == 0 and abs(b["xT"][2] - a["xT"][2]) < 1e-8
+    mt = orc.OracleModel(_top_scene())
+    xt = np.array([0, 0, 1.0, 1, 0, 0, 0, 0, 0, 0, 1.0, 0.5, 4.0])
+    r = mt.rollout(xt, T=1.0, rtol=0.0, atol=1e-8, h0=5e-3, method="tsit5")
+    x = xt.copy()
+    errs = []
+    for h in r["hlog"][:-1]:
+        errs.append(mt.step_error(x, h, rtol=0.0, atol=1e-8, method="tsit5"))
+        x, _ = mt.replay(x, [h], T=1e3, method="tsit5")
+    np.testing.assert_allclose(errs[-10:], 0.9 ** 12.5, rtol=1e-6)

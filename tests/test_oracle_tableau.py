@@ -65,3 +65,54 @@ def test_order_conditions(orc):
     for got, want in conds[:8]:                               # embedded method: order 4
         assert abs(got - want) < 1e-14
     assert max(abs(g - w) for g, w in conds[8:]) > 1e-6       # ... but not order 5
+
+
+# ------------------------------------------------------------------ Tsitouras 5(4), semi-implicit Euler
+def _golden_tsit5():
+    a = np.zeros((7, 7)); e = np.zeros(7); c = np.zeros(7)
+    for line in open(os.path.join(HERE, "golden", "tsit5_tableau.txt")):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        if line[0] == "a":
+            a[int(line[1]), int(line[2])] = float(line[3])
+        else:
+            {"e": e, "c": c}[line[0]][int(line[1])] = float(line[2])
+    b = np.zeros(7); b[:6] = a[6, :6]
+    return a, b, b - e, c
+
+
+def test_tsit5_matches_published_coefficients(orc):
+    t = orc.tableau_full("tsit5")
+    ga, gb, gbh, gc = _golden_tsit5()
+    assert t["S"] == 7
+    np.testing.assert_array_equal(t["av"], ga)
+    np.testing.assert_array_equal(t["aq"], ga)
+    np.testing.assert_allclose(t["b"], gb, rtol=0, atol=1e-17)
+    np.testing.assert_allclose(t["bhat"], gbh, rtol=0, atol=1e-17)
+    np.testing.assert_array_equal(t["c"], gc)
+
+
+def test_tsit5_order_conditions():
+    """The published decimals satisfy every order-5 condition of b and every
+    order-4 condition of bhat to rounding (and bhat is not of order 5)."""
+    a, b, bh, c = _golden_tsit5()
+    np.testing.assert_allclose(a.sum(axis=1), c, atol=1e-15)
+    assert np.all(np.triu(a) == 0.0) and b[6] == 0.0
+    for got, want in _conditions(a, b, c):
+        assert abs(got - want) < 1e-14
+    conds = _conditions(a, bh, c)
+    for got, want in conds[:8]:
+        assert abs(got - want) < 1e-14
+    assert max(abs(g - w) for g, w in conds[8:]) > 1e-6
+
+
+def test_semi_implicit_euler_coefficients(orc):
+    """Semi-implicit Euler as a two-stage partitioned scheme: the velocity takes
+    the stage-0 derivative, the position takes the NEW velocity (diagonal
+    position coefficient), no error estimate."""
+    t = orc.tableau_full("euler")
+    assert t["S"] == 2
+    assert t["av"][1, 0] == 1.0 and t["av"][1, 1] == 0.0
+    assert t["aq"][1, 1] == 1.0 and t["aq"][1, 0] == 0.0
+    np.testing.assert_array_equal(t["b"], t["bhat"])           # no embedded difference
