@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--grad-only", action="store_true", help="only the fwd+adjoint leg (one JSON line)")
     p.add_argument("--grad-envs", type=int, default=16384, help="environments of the fwd+adjoint leg")
     p.add_argument("--all", action="store_true", help="every workload (forward, fwd+adjoint, CPU oracle samples)")
+    p.add_argument("--pareto", action="store_true", help="integrator comparison: error vs runtime on cube tosses")
+    p.add_argument("--pareto-envs", type=int, default=2048)
+    p.add_argument("--pareto-sample", type=int, default=32, help="tosses compared with the oracle reference")
     p.add_argument("--adj-lanes", type=int, default=0, help="lanes per environment of the adjoint (0 = autotuned)")
     p.add_argument("--requests", type=int, default=24, help="served requests timed (after the warm-up ones)")
     p.add_argument("--warmup-requests", type=int, default=4)
@@ -771,6 +774,91 @@ def run_serving(args):
             "config": {"workload": "served MPC requests", **res["config"]}, "serving": res}
 
 
+# ------------------------------------------------------------------ integrator comparison
+def toss_reference(scene, inp, n, eps=1e-4, rtol=1e-11):
+    """Reference loss (final x of the cube) and gradient w.r.t. the initial
+    velocity of the first n tosses: the CPU oracle at rtol 1e-11 and central
+    differences (eps = 1e-4) of that tight-tolerance rollout, as the paper's
+    ground truth is built (Fig. 12: finite differences of an adaptive solver
+    at tolerance 1e-12)."""
+    import oracle
+    m = oracle.OracleModel(scene)
+    X, T = inp["x0"][:n], inp["T"][:n]
+
+    def loss(Xp):
+        return m.batch_rollout(Xp, T, rtol=rtol, atol=rtol * 1e-2, h0=1e-4, max_steps=10 ** 6)["xT"][:, 0]
+    G = np.zeros((n, 3))
+    for k in range(3):
+        Xp, Xm = X.copy(), X.copy()
+        Xp[:, 7 + k] += eps
+        Xm[:, 7 + k] -= eps
+        G[:, k] = (loss(Xp) - loss(Xm)) / (2 * eps)
+    return loss(X), G
+
+
+def run_pareto(args):
+    """Error of the loss and of its gradient vs GPU runtime for fixed-step
+    semi-implicit Euler and the adaptive Dormand-Prince and Tsitouras schemes
+    (the paper's Fig. 12 and Sec. 3.1 comparison) on 2048 seeded cube tosses
+    (T = 1 s, solref 0.005 s): forward and forward+adjoint batch times on the
+    GPU; errors of the sampled tosses against the tight-tolerance reference."""
+    import torch
+
+    import paper_2506_14186_gb300 as dmx
+    from paper_2506_14186_gb300 import _build
+    from paper_2506_14186_gb300 import workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    sc, inp = W.toss_scene(), W.toss_inputs(args.pareto_envs)
+    nref = min(args.pareto_sample, args.pareto_envs)
+    t0 = time.perf_counter()
+    ref_loss, ref_grad = toss_reference(sc, inp, nref)
+    t_ref = time.perf_counter() - t0
+    m = dmx.Model(sc)
+    B = args.pareto_envs
+    x0 = torch.tensor(np.ascontiguousarray(inp["x0"].T), device="cuda")
+    T = torch.tensor(inp["T"], device="cuda")
+    xT_bar = torch.zeros((13, B), dtype=torch.float64, device="cuda")
+    xT_bar[0] = 1.0
+    configs = [("euler", {"h0": h}) for h in (2e-3, 1e-3, 5e-4, 2.5e-4, 1.25e-4, 6.25e-5)]
+    for method in ("dopri5", "tsit5"):
+        configs += [(method, {"rtol": r, "atol": r * 1e-2}) for r in (1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9)]
+    points = []
+    for method, kw in configs:
+        a = dict(kw, max_steps=40000, method=method, K=32)
+        dmx.rollout(m, x0, torch.clamp(T, max=0.05), **a)                  # warm-up
+        out, t_f = _events_time(lambda: dmx.rollout(m, x0, T, **a))
+        (out, (gx, _)), t_g = _events_time(
+            lambda: (lambda o: (o, dmx.rollout_grad(o["tape"], xT_bar)))(dmx.rollout(m, x0, T, tape=True, **a)))
+        assert int((out["status"] != 0).sum().item()) == 0, (method, kw)
+        loss = out["xT"][0, :nref].cpu().numpy()
+        grad = gx[7:10, :nref].cpu().numpy().T
+        le = np.abs(loss - ref_loss) / np.maximum(np.abs(ref_loss), 1e-12)
+        ge = np.linalg.norm(grad - ref_grad, axis=1) / np.linalg.norm(ref_grad, axis=1)
+        points.append({"method": method, **{k: v for k, v in kw.items()},
+                       "steps_per_env": float(out["nsteps"].double().mean().item()),
+                       "forward_s": t_f, "fwd_adjoint_s": t_g,
+                       "loss_rel_err_median": float(np.median(le)), "grad_rel_err_median": float(np.median(ge)),
+                       "grad_rel_err_p90": float(np.percentile(ge, 90))})
+
+    def front(key_t, key_e):
+        pts = sorted(points, key=lambda p: p[key_t])
+        out, best = [], float("inf")
+        for p in pts:
+            if p[key_e] < best:
+                best = p[key_e]
+                out.append(f"{p['method']} {p.get('h0', p.get('rtol'))}")
+        return out
+    return {"metric": "error of loss and gradient vs runtime (integrator comparison)", "impl": "ours",
+            "dtype": "f64", "data": "synthetic (seeded cube tosses)",
+            "config": {"workload": "cube toss", "B": B, "T_s": 1.0, "solref": [0.005, 1.0],
+                       "loss": "final x position", "gradient": "w.r.t. the initial velocity",
+                       "reference": f"CPU oracle rtol 1e-11, central differences eps 1e-4, first {nref} tosses "
+                                    f"({t_ref:.1f} s)"},
+            "points": points, "front_gradient": front("fwd_adjoint_s", "grad_rel_err_median"),
+            "front_loss": front("forward_s", "loss_rel_err_median")}
+
+
 def main():
     args = parse()
     if args.serving:
@@ -778,6 +866,9 @@ def main():
         return
     if args.all:
         print(json.dumps(run_all(args)), flush=True)
+        return
+    if args.pareto:
+        print(json.dumps(run_pareto(args)), flush=True)
         return
     if args.grad_only:
         import torch

@@ -64,6 +64,12 @@ enum { DMX_JNT_FREE = 0, DMX_JNT_HINGE = 1 };
 enum { DMX_GEOM_SPHERE = 0, DMX_GEOM_CAPSULE = 1, DMX_GEOM_BOX = 2 };
 enum { DMX_ACT_MOTOR = 0, DMX_ACT_POSITION = 1 };
 enum { DMX_FORM_PERSISTENT = 0, DMX_FORM_STEP = 1, DMX_FORM_STEP_GRAPH = 2 };
+/* integration schemes (dmx_rollout_args.method): adaptive Dormand-Prince 5(4)
+ * (App. C.2) and Tsitouras 5(4) (the paper's default solver, Fig. 12), both with
+ * the PID step-size controller of App. B; semi-implicit Euler with the fixed
+ * step h0 (the MuJoCo XLA integrator the paper compares against, Sec. 3.1:
+ * v_{n+1} = v_n + h F(q_n, v_n), q_{n+1} = q_n (+) h v_{n+1}; rtol/atol unused). */
+enum { DMX_METHOD_DOPRI5 = 0, DMX_METHOD_TSIT5 = 1, DMX_METHOD_EULER = 2 };
 /* adjoint kernels of dmx_rollout_grad (dmx_set_adjoint) */
 enum { DMX_ADJ_REVERSE = 0, DMX_ADJ_TANGENT = 1, DMX_ADJ_RECOMPUTE = 2 };
 
@@ -140,7 +146,7 @@ typedef struct {
   const double* ctrl;         /* [NI][nu][B] piecewise-constant controls, NULL iff nu == 0 */
   const double* T;            /* [B] horizons (s), > 0 */
   int32_t NI;                 /* control intervals over [0, T], >= 1 */
-  double rtol, atol;          /* error-norm tolerances, > 0 */
+  double rtol, atol;          /* error-norm tolerances: rtol >= 0, atol > 0 */
   double h0;                  /* first trial step (s), > 0 */
   int32_t max_steps;          /* step-attempt budget per environment, >= 1 */
   int32_t K;                  /* checkpoint interval (accepted steps) of the tape, >= 1 */
@@ -156,6 +162,7 @@ typedef struct {
   int32_t* status;            /* out [B] DMX_ENV_* codes, or NULL */
   dmx_tape** tape;            /* out: tape for dmx_rollout_grad (checkpoints every K accepted
                                  steps + accepted step sizes), or NULL for forward only */
+  int32_t method;             /* DMX_METHOD_*: integration scheme (0 = adaptive Dormand-Prince 5(4)) */
 } dmx_rollout_args;
 
 /* Batched adaptive rollout x0 -> x(T) (Sec. 3.1; one independent step-size

@@ -28,6 +28,8 @@ c_i32, c_f64, c_p = ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
 DMX_OK, DMX_ERR_INVALID, DMX_ERR_OOM, DMX_ERR_CUDA, DMX_NOT_READY, DMX_ERR_TIMEOUT, DMX_ERR_UNIMPLEMENTED = range(7)
 ENV_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "nonfinite", 4: "solver_noconv", 5: "row_overflow"}
 FORMS = {"persistent": 0, "step": 1, "graph": 2}
+# integration schemes: adaptive Dormand-Prince 5(4) and Tsitouras 5(4), fixed-step semi-implicit Euler
+METHODS = {"dopri5": 0, "tsit5": 1, "euler": 2}
 ADJOINT_MODES = {"reverse": 0, "tangent": 1, "recompute": 2}
 _JOINT = {"free": 0, "hinge": 1}
 _GEOM = {"sphere": 0, "capsule": 1, "box": 2}
@@ -69,7 +71,7 @@ class RolloutArgs(ctypes.Structure):
     _fields_ = [("B", c_i32), ("x0", c_p), ("ctrl", c_p), ("T", c_p), ("NI", c_i32), ("rtol", c_f64),
                 ("atol", c_f64), ("h0", c_f64), ("max_steps", c_i32), ("K", c_i32), ("form", c_i32),
                 ("lanes", c_i32), ("host", c_i32), ("xT", c_p), ("xb", c_p), ("nsteps", c_p), ("nrej", c_p),
-                ("status", c_p), ("tape", ctypes.POINTER(c_p))]
+                ("status", c_p), ("tape", ctypes.POINTER(c_p)), ("method", c_i32)]
 
 
 class ServerCfg(ctypes.Structure):
@@ -224,10 +226,11 @@ class Tape:
 
 
 def rollout(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, K=32,
-            form="persistent", lanes=0, want_xb=False, tape=False, stream=None):
-    """Batched adaptive rollout on the device.  Returns a dict of CUDA tensors
-    xT [nx, B], xb [NI+1, nx, B] (if want_xb), nsteps/nrej/status [B] (int32)
-    and, with tape=True, a Tape for rollout_grad."""
+            form="persistent", lanes=0, want_xb=False, tape=False, stream=None, method="dopri5"):
+    """Batched rollout on the device (method: "dopri5" / "tsit5" adaptive, "euler"
+    fixed step h0).  Returns a dict of CUDA tensors xT [nx, B], xb [NI+1, nx, B]
+    (if want_xb), nsteps/nrej/status [B] (int32) and, with tape=True, a Tape for
+    rollout_grad."""
     import torch
     _require_cuda(x0, "x0", torch.float64)
     _require_cuda(T, "T", torch.float64)
@@ -250,7 +253,7 @@ def rollout(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_st
     args = RolloutArgs(B, x0.data_ptr(), ctrl.data_ptr() if (model.nu and ctrl is not None) else None, T.data_ptr(),
                        NI, rtol, atol, h0, max_steps, K, FORMS[form], lanes, 0, xT.data_ptr(),
                        xb.data_ptr() if xb is not None else None, nsteps.data_ptr(), nrej.data_ptr(),
-                       status.data_ptr(), ctypes.pointer(th) if tape else None)
+                       status.data_ptr(), ctypes.pointer(th) if tape else None, METHODS[method])
     _check(lib().dmx_rollout(model.h, ctypes.byref(args), _stream_handle(stream)))
     out = {"xT": xT, "xb": xb, "nsteps": nsteps, "nrej": nrej, "status": status}
     if tape:
@@ -259,7 +262,7 @@ def rollout(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_st
 
 
 def rollout_host(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, form="persistent",
-                 lanes=0, xT=None, stream=None):
+                 lanes=0, xT=None, stream=None, method="dopri5"):
     """Same rollout through the C ABI with HOST buffers (numpy arrays or pinned
     CPU tensors, SoA layout); the library copies in, integrates and copies out."""
     def host_ptr(a):
@@ -275,7 +278,7 @@ def rollout_host(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, m
     nsteps = np.empty(B, dtype=np.int32)
     args = RolloutArgs(B, host_ptr(x0), host_ptr(ctrl) if model.nu else None, host_ptr(T), NI, rtol, atol, h0,
                        max_steps, 32, FORMS[form], lanes, 1, host_ptr(xT), None, host_ptr(nsteps), None,
-                       host_ptr(status), None)
+                       host_ptr(status), None, METHODS[method])
     _check(lib().dmx_rollout(model.h, ctypes.byref(args), _stream_handle(stream)))
     return {"xT": xT, "status": status, "nsteps": nsteps}
 
@@ -330,7 +333,7 @@ def eval_rhs(model, q, v, u=None, cfd=False, lanes=0, stream=None):
 
 
 def rollout_static(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, lanes=0,
-                   xT=None, nsteps=None, status=None, stream=None):
+                   xT=None, nsteps=None, status=None, stream=None, method="dopri5"):
     """dmx_rollout_static: the rollout without any device allocation inside
     the call (state in the library's fixed device array).  Outputs go to the
     caller's tensors xT [nx, B], nsteps / status [B] (int32); allocate them
@@ -349,7 +352,7 @@ def rollout_static(model, x0, T, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3,
         status = torch.empty(B, dtype=torch.int32, device=x0.device)
     args = RolloutArgs(B, x0.data_ptr(), ctrl.data_ptr() if model.nu else None, T.data_ptr(), NI, rtol, atol, h0,
                        max_steps, 1, FORMS["step"], lanes, 0, xT.data_ptr(), None, nsteps.data_ptr(), None,
-                       status.data_ptr(), None)
+                       status.data_ptr(), None, METHODS[method])
     _check(lib().dmx_rollout_static(model.h, ctypes.byref(args), _stream_handle(stream)))
     return xT, nsteps, status
 

@@ -2,7 +2,7 @@
 // accepted steps, App. C.2), with the straight-through CFD treatment of Sec. 4.
 //
 // One warp per environment.  For every accepted step, in reverse order, the
-// warp evaluates the DOPRI5 step map (q_n, v_n, u) -> (q_{n+1}, v_{n+1}) once
+// warp evaluates the step map (q_n, v_n, u) -> (q_{n+1}, v_{n+1}) once
 // in forward-mode derivative scalars with ONE INPUT DIRECTION PER LANE: all
 // lanes run the same instruction stream (the primal part is identical in
 // every lane), so on GB300, where an FP64 warp instruction costs the same
@@ -44,38 +44,38 @@ __device__ __forceinline__ int adj_interval(double T, int NI, double t) {
   return k;
 }
 
-// One DOPRI5 step of size h in derivative scalars from (qn, vn) in the dual
-// workspace; leaves the 5th-order solution in (qs, vs).  Stage derivatives of
+// One step of scheme mt (TAB(mt)) of size h in derivative scalars from (qn, vn)
+// in the dual workspace; leaves the result in (qs, vs).  Stage derivatives of
 // F; with cfd the tangents of F~ replace them (straight-through).
-__device__ int dual_step(const Grp<1>& g, const DevModel& m, const WsT<Dual>& w, const Dual* u, double h, bool cfd,
-                         int* maskF, int* maskC) {
+__device__ int dual_step(const Grp<1>& g, const DevModel& m, const WsT<Dual>& w, const Dual* u, double h, int mt,
+                         bool cfd, int* maskF, int* maskC) {
   const Layout& L = *w.L;
-  const int nv = m.nv;
+  const int nv = m.nv, S = TAB(mt).S;
   const Dual* qn = w.at(L.qn); const Dual* vn = w.at(L.vn);
   Dual* qs = w.at(L.qs); Dual* vs = w.at(L.vs);
   Dual* kv = w.at(L.kv); Dual* ka = w.at(L.ka); Dual* dq = w.at(L.dq);
   int* pm = w.i + L.pmask;
   int st = 0;
-  for (int s = 0; s < 7; ++s) {
+  for (int s = 0; s < S; ++s) {
     if (s == 0) {
       for (int i = 0; i < m.nq; ++i) qs[i] = qn[i];
       for (int i = 0; i < nv; ++i) vs[i] = vn[i];
     } else {
+      const unsigned mq = TAB(mt).nzq[s], mv = TAB(mt).nzv[s];
       for (int i = 0; i < nv; ++i) {
         Dual sq = 0.0, sv = 0.0;
         for (int j = 0; j < s; ++j) {
-          if (!((c_tab.nz[s] >> j) & 1u)) continue;
-          const double c = c_tab.a[s][j];
-          sq += c * kv[j * nv + i];
-          sv += c * ka[j * nv + i];
+          if ((mq >> j) & 1u) sq += TAB(mt).aq[s][j] * kv[j * nv + i];
+          if ((mv >> j) & 1u) sv += TAB(mt).av[s][j] * ka[j * nv + i];
         }
-        dq[i] = h * sq;
         vs[i] = vn[i] + h * sv;
+        if ((mq >> s) & 1u) sq += TAB(mt).aq[s][s] * vs[i];
+        dq[i] = h * sq;
       }
       integrate_pos(g, m, qn, (const Dual*)dq, qs);
     }
     for (int i = 0; i < nv; ++i) kv[s * nv + i] = vs[i];
-    if (s == 6) break;                          // b_7 = 0: the last stage derivative is not needed
+    if (s == S - 1) break;                      // the last stage's derivative is not part of the step
     for (int k = 0; k < MASKW; ++k) pm[k] = maskF[k];
     int r = rhs(g, m, w, (const Dual*)qs, (const Dual*)vs, u, false, ka + s * nv);
     for (int k = 0; k < MASKW; ++k) maskF[k] = pm[k];
@@ -147,14 +147,14 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_adjoint(AdjParams P) {
         if (n == n1 - 1) break;
         const double h = P.hlog[(size_t)n * P.B + env];
         int st;
-        dopri5_attempt(g, m, wp, (const double*)u, h, 1.0, 1.0, &st);
+        rk_attempt(g, m, wp, (const double*)u, h, P.method, 1.0, 1.0, &st);
         const double tn = adj_boundary(T, P.NI, k + 1);
         const bool reached = (h == tn - t) || (t + h >= tn);
         t = reached ? tn : t + h;
         const double* qs = wp.at(sL.qs); const double* vs = wp.at(sL.vs);
         double* ka = wp.at(sL.ka);
         for (int i = 0; i < nq; ++i) qn[i] = qs[i];
-        for (int i = 0; i < nv; ++i) { vn[i] = vs[i]; ka[i] = ka[6 * nv + i]; }
+        for (int i = 0; i < nv; ++i) { vn[i] = vs[i]; ka[i] = ka[(TAB(P.method).S - 1) * nv + i]; }
         if (reached && k + 1 < P.NI) {
           ++k;
           for (int a = 0; a < nu; ++a) u[a] = P.ctrl[((size_t)k * nu + a) * P.B + env];
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_adjoint(AdjParams P) {
           for (int i = 0; i < nq; ++i) qd[i] = Dual(row[i], d == i ? 1.0 : 0.0);
           for (int i = 0; i < nv; ++i) vd[i] = Dual(row[nq + i], d == nq + i ? 1.0 : 0.0);
           for (int a = 0; a < nu; ++a) ud[a] = Dual(P.ctrl[((size_t)kn * nu + a) * P.B + env], d == nx + a ? 1.0 : 0.0);
-          dual_step(g, m, wd, (const Dual*)ud, h, P.cfd != 0, maskF, maskC);
+          dual_step(g, m, wd, (const Dual*)ud, h, P.method, P.cfd != 0, maskF, maskC);
           const Dual* qs = wd.at(sL.qs); const Dual* vs = wd.at(sL.vs);
           double acc = 0.0;
           for (int i = 0; i < nq; ++i) acc += xbar[i] * qs[i].d;

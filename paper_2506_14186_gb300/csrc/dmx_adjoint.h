@@ -11,6 +11,7 @@ struct AdjParams {
   Layout L;
   LayoutBar LB;           // reverse-mode kernel: cotangent workspace
   int B, NI, K, cfd;
+  int method;             // METHOD_* integration scheme of the taped rollout
   const double* ckpt;     // [ncheck][nx+1][B] tape checkpoints (state, time)
   const double* hlog;     // [max_steps][B] accepted step sizes
   const int* tape_n;      // [B] accepted steps
@@ -21,7 +22,7 @@ struct AdjParams {
   double* x0_bar;         // [nx][B]
   double* ctrl_bar;       // [NI][nu][B] or null
   double* segbuf;         // per warp (tangent) or group (reverse): recomputed steps of a segment
-  double* snapbuf;        // reverse mode: per group, K steps x 6 stage snapshots of SN doubles (or null)
+  double* snapbuf;        // reverse mode: per group, K steps x (S - 1) stage snapshots of SN doubles (or null)
   int SN;                 // doubles per snapshot
   int* queue;             // next environment
 };
@@ -48,6 +49,10 @@ __host__ __device__ inline SnapOff snap_offsets(const DevModel& m, const Layout&
   o.size = (o.oi + (nints + 1) / 2 + 1) & ~1;
   return o;
 }
+
+// Doubles per recomputed step in the reverse kernel's segment buffer: q_n,
+// the stage velocities V_0..V_6, t_n.
+__host__ __device__ inline int rev_row_doubles(const DevModel& m) { return m.nq + 7 * m.nv + 1; }
 
 cudaError_t launch_adjoint(const AdjParams& P, int blocks, cudaStream_t st);
 // reverse-mode kernel, G lanes per environment (G = 2, 4, 8, 16, 32)

@@ -4,23 +4,24 @@
 // kernels, persistent (groups take the next environment from a counter).
 //
 // For every accepted step, in reverse order, the step map
-// (q_n, v_n, u) -> (q_{n+1}, v_{n+1}) of the Dormand-Prince scheme with the
-// taped step size h (held constant) is transposed stage by stage:
-//   stage s state  Q_s = q_n (+) h sum_j a_sj V_j,  V_s = v_n + h sum_j a_sj K_j,
-//   K_s = F(Q_s, V_s, u)  (s = 0..5),  (q_{n+1}, v_{n+1}) = (Q_6, V_6).
-// Walking s = 6..0, the stage cotangents (Qbar_s, Vbar_s) collect the
+// (q_n, v_n, u) -> (q_{n+1}, v_{n+1}) of the taped scheme (Dormand-Prince,
+// Tsitouras or semi-implicit Euler, dmx_device.cuh) with the taped step size
+// h (held constant) is transposed stage by stage:
+//   stage s state  V_s = v_n + h sum_{j<s} av_sj K_j,  Q_s = q_n (+) h sum_{j<=s} aq_sj V_j,
+//   K_s = F(Q_s, V_s, u)  (s = 0..S-2),  (q_{n+1}, v_{n+1}) = (Q_{S-1}, V_{S-1}).
+// Walking s = S-1..0, the stage cotangents (Qbar_s, Vbar_s) collect the
 // contributions of the later stages, K_s's cotangent goes through the
 // right-hand side VJP at (Q_s, V_s) (of F~ at the F stage states when cfd:
 // straight-through), and (q_n, v_n, u) receive the rest.  The stage states
 // come from a forward recompute of the segment between two checkpoints (the
 // tape holds the state every K accepted steps), stored per step in a
-// per-group buffer: q_n, V_0..V_5 and t_n.
+// per-group buffer: q_n, V_0..V_{S-1} and t_n.
 //
 // Without the CFD right-hand side (cfd = 0) the reverse sweep needs the
 // right-hand sides that the segment recompute already evaluated (same stage
 // states, same inputs).  When P.snapbuf is given, the recompute copies the
 // part of each stage's workspace that the VJP reads to device memory
-// (K steps x 6 stages per group) and the reverse sweep restores it instead of
+// (K steps x (S - 1) stages per group) and the reverse sweep restores it instead of
 // evaluating the right-hand side a second time: device memory traded for
 // FP64 work.  The final active set of a stage does not depend on the
 // warm start of its Newton search, so the restored workspace equals a
@@ -39,9 +40,6 @@ __device__ __forceinline__ int rev_interval(double T, int NI, double t) {
   while (k + 1 < NI && t >= rev_boundary(T, NI, k + 1)) ++k;
   return k;
 }
-
-// Doubles per recomputed step in the segment buffer: q_n, V_0..V_5, t_n.
-__host__ __device__ __forceinline__ int rev_row(const DevModel& m) { return m.nq + 6 * m.nv + 1; }
 
 // Workspace of the right-hand side just evaluated (status st) -> snapshot dst.
 template <int G>
@@ -83,17 +81,17 @@ __device__ int snap_restore(const Grp<G>& g, const DevModel& m, const Ws& w, con
   return st;
 }
 
-// (qnb, vnb, ub) = transposed step map applied to (Qb, Vb) = the cotangent of
-// (q_{n+1}, v_{n+1}); reads q_n from b.qn and V_0..V_5 from b.vst.  Qb and Vb
-// are consumed (left zero).  snaps: the step's 6 stage snapshots (SN doubles
-// each), or null to evaluate each stage's right-hand side.  Returns the worst
-// right-hand-side status.
+// (qnb, vnb, ub) = transposed step map of scheme mt applied to (Qb, Vb) = the
+// cotangent of (q_{n+1}, v_{n+1}); reads q_n from b.qn and V_0..V_{S-1} from
+// b.vst.  Qb and Vb are consumed (left zero).  snaps: the step's S - 1 stage
+// snapshots (SN doubles each), or null to evaluate each stage's right-hand
+// side.  Returns the worst right-hand-side status.
 template <int G>
-__device__ int dopri5_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const WsB& b, const double* u,
-                               double h, bool cfd, const double* snaps, int SN) {
+__device__ int rk_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const WsB& b, const double* u,
+                           double h, int mt, bool cfd, const double* snaps, int SN) {
   const Layout& L = *w.L;
   const LayoutBar& LB = *b.L;
-  const int nv = m.nv;
+  const int nv = m.nv, S = TAB(mt).S;
   const double* qn = b.at(LB.qn); const double* vst = b.at(LB.vst);
   double* dq = b.at(LB.dq); double* dqb = b.at(LB.dqb); double* Qs = b.at(LB.Qs);
   double* kab = b.at(LB.kab); double* kvb = b.at(LB.kvb);
@@ -105,48 +103,41 @@ __device__ int dopri5_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, 
   for (int i = g.lane; i < nv; i += G) vnb[i] = 0.0;
   for (int a = g.lane; a < m.nu; a += G) ub[a] = 0.0;
   g.sync();
-  for (int s = 6; s >= 0; --s) {
+  for (int s = S - 1; s >= 0; --s) {
+    const unsigned mq = TAB(mt).nzq[s], mv = TAB(mt).nzv[s];
     if (s >= 1) {
       for (int i = g.lane; i < nv; i += G) {
         double sq = 0;
-        for (int j = 0; j < s; ++j) {
-          if (!((c_tab.nz[s] >> j) & 1u)) continue;
-          const double c = c_tab.a[s][j];
-          sq += c * vst[j * nv + i];
-        }
+        for (int j = 0; j <= s; ++j)
+          if ((mq >> j) & 1u) sq += TAB(mt).aq[s][j] * vst[j * nv + i];
         dq[i] = h * sq;
       }
       g.sync();
-      if (s <= 5) integrate_pos(g, m, qn, (const double*)dq, Qs);
+      if (s <= S - 2) integrate_pos(g, m, qn, (const double*)dq, Qs);
     } else {
       for (int i = g.lane; i < m.nq; i += G) Qs[i] = qn[i];
       g.sync();
     }
-    if (s <= 5) {
+    if (s <= S - 2) {
       const double* Vs = vst + s * nv;
       const int r = snaps ? snap_restore(g, m, w, snaps + (size_t)s * SN)
                           : rhs(g, m, w, (const double*)Qs, Vs, u, cfd, w.at(L.ka));
       if (r > st) st = r;
       rhs_vjp(g, m, w, b, Qs, Vs, u, cfd, r, kab + s * nv, Qb, Vb, ub);
-      for (int i = g.lane; i < nv; i += G) Vb[i] += kvb[s * nv + i];   // K^v_s = V_s
+      for (int i = g.lane; i < nv; i += G) Vb[i] += kvb[s * nv + i];   // V_s in the later stages' positions
       g.sync();
     }
     if (s >= 1) {
-      for (int i = g.lane; i < nv; i += G) {
-        vnb[i] += Vb[i];
-        for (int j = 0; j < s; ++j) {
-          if (!((c_tab.nz[s] >> j) & 1u)) continue;
-          const double c = c_tab.a[s][j];
-          kab[j * nv + i] += h * c * Vb[i];
-        }
-      }
+      // positions first: a diagonal coefficient puts V_s into Q_s itself
       integrate_pos_vjp(g, m, qn, dq, Qb, qnb, dqb);
-      for (int i = g.lane; i < nv; i += G)
-        for (int j = 0; j < s; ++j) {
-          if (!((c_tab.nz[s] >> j) & 1u)) continue;
-          const double c = c_tab.a[s][j];
-          kvb[j * nv + i] += h * c * dqb[i];
-        }
+      for (int i = g.lane; i < nv; i += G) {
+        for (int j = 0; j < s; ++j)
+          if ((mq >> j) & 1u) kvb[j * nv + i] += h * TAB(mt).aq[s][j] * dqb[i];
+        if ((mq >> s) & 1u) Vb[i] += h * TAB(mt).aq[s][s] * dqb[i];
+        vnb[i] += Vb[i];
+        for (int j = 0; j < s; ++j)
+          if ((mv >> j) & 1u) kab[j * nv + i] += h * TAB(mt).av[s][j] * Vb[i];
+      }
     } else {
       for (int i = g.lane; i < m.nq; i += G) qnb[i] += Qb[i];
       for (int i = g.lane; i < nv; i += G) vnb[i] += Vb[i];
@@ -173,11 +164,12 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_rev(AdjParams P) {
   const Ws w{smem + (size_t)gib * per, reinterpret_cast<int*>(smem + (size_t)ngb * per) + (size_t)gib * sL.ni, &sL};
   const WsB b{smem + (size_t)gib * per + sL.nd, &sB};
   const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
-  const int RW = rev_row(m);
+  const int RW = rev_row_doubles(m);
+  const int mt = P.method, S = TAB(mt).S;
   double* seg = P.segbuf + (size_t)(blockIdx.x * ngb + gib) * P.K * RW;
   const bool use_snap = P.snapbuf != nullptr && P.cfd == 0;
   const int SN = P.SN;
-  double* snb = use_snap ? P.snapbuf + (size_t)(blockIdx.x * ngb + gib) * P.K * 6 * SN : nullptr;
+  double* snb = use_snap ? P.snapbuf + (size_t)(blockIdx.x * ngb + gib) * P.K * (S - 1) * SN : nullptr;
   double* qn = w.at(sL.qn); double* vn = w.at(sL.vn); double* u = w.at(sL.u); double* ka = w.at(sL.ka);
   double* xbar = b.at(sB.xb);
   for (;;) {
@@ -210,16 +202,16 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_rev(AdjParams P) {
       for (int n = n0; n < n1; ++n) {
         double* row = seg + (size_t)(n - n0) * RW;
         const double h = P.hlog[(size_t)n * P.B + env];
-        double* sn_step = use_snap ? snb + (size_t)(n - n0) * 6 * SN : nullptr;
-        double* sn_next = (use_snap && n + 1 < n1) ? sn_step + (size_t)6 * SN : nullptr;
-        dopri5_stages(g, m, w, (const double*)u, h, [&](int s, int r) {
-          if (s <= 5) { if (sn_step) snap_save(g, m, w, sn_step + (size_t)s * SN, r); }
-          else if (sn_next) snap_save(g, m, w, sn_next, r);   // stage 6 = stage 0 of the next step
+        double* sn_step = use_snap ? snb + (size_t)(n - n0) * (S - 1) * SN : nullptr;
+        double* sn_next = (use_snap && n + 1 < n1) ? sn_step + (size_t)(S - 1) * SN : nullptr;
+        rk_stages(g, m, w, (const double*)u, h, mt, [&](int s, int r) {
+          if (s <= S - 2) { if (sn_step) snap_save(g, m, w, sn_step + (size_t)s * SN, r); }
+          else if (sn_next) snap_save(g, m, w, sn_next, r);   // the last stage = stage 0 of the next step
         });
         const double* kv = w.at(sL.kv);
         for (int i = g.lane; i < nq; i += G) row[i] = qn[i];
-        for (int i = g.lane; i < 6 * nv; i += G) row[nq + i] = kv[i];
-        if (g.lane == 0) row[nq + 6 * nv] = t;
+        for (int i = g.lane; i < S * nv; i += G) row[nq + i] = kv[i];
+        if (g.lane == 0) row[nq + 7 * nv] = t;
         if (n == n1 - 1) break;
         const double tn = rev_boundary(T, P.NI, k + 1);
         const bool reached = (h == tn - t) || (t + h >= tn);
@@ -227,7 +219,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_rev(AdjParams P) {
         const double* qs = w.at(sL.qs); const double* vs = w.at(sL.vs);
         g.sync();
         for (int i = g.lane; i < nq; i += G) qn[i] = qs[i];
-        for (int i = g.lane; i < nv; i += G) { vn[i] = vs[i]; ka[i] = ka[6 * nv + i]; }
+        for (int i = g.lane; i < nv; i += G) { vn[i] = vs[i]; ka[i] = ka[(S - 1) * nv + i]; }
         g.sync();
         if (reached && k + 1 < P.NI) {
           ++k;
@@ -244,7 +236,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_rev(AdjParams P) {
       double* Qb = b.at(sB.Qb); double* Vb = b.at(sB.Vb);
       for (int n = n1 - 1; n >= n0; --n) {
         const double* row = seg + (size_t)(n - n0) * RW;
-        const double tn0 = row[nq + 6 * nv];
+        const double tn0 = row[nq + 7 * nv];
         const int kn = rev_interval(T, P.NI, tn0);
         const double h = P.hlog[(size_t)n * P.B + env];
         const double tb = rev_boundary(T, P.NI, kn + 1);
@@ -252,14 +244,14 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_rev(AdjParams P) {
         if (reached && P.xb_bar)
           for (int i = g.lane; i < nx; i += G) xbar[i] += P.xb_bar[((size_t)(kn + 1) * nx + i) * P.B + env];
         for (int i = g.lane; i < nq; i += G) bq[i] = row[i];
-        for (int i = g.lane; i < 6 * nv; i += G) bv[i] = row[nq + i];
+        for (int i = g.lane; i < S * nv; i += G) bv[i] = row[nq + i];
         for (int a = g.lane; a < nu; a += G) u[a] = P.ctrl[((size_t)kn * nu + a) * P.B + env];
         g.sync();
         for (int i = g.lane; i < nq; i += G) Qb[i] = xbar[i];
         for (int i = g.lane; i < nv; i += G) Vb[i] = xbar[nq + i];
         g.sync();
-        const int st = dopri5_step_vjp(g, m, w, b, (const double*)u, h, P.cfd != 0,
-                                       use_snap ? snb + (size_t)(n - n0) * 6 * SN : nullptr, SN);
+        const int st = rk_step_vjp(g, m, w, b, (const double*)u, h, mt, P.cfd != 0,
+                                   use_snap ? snb + (size_t)(n - n0) * (S - 1) * SN : nullptr, SN);
         if (st > worst) worst = st;
         const double* qnb = b.at(sB.qnb); const double* vnb = b.at(sB.vnb); const double* ub = b.at(sB.ub);
         for (int i = g.lane; i < nq; i += G) xbar[i] = qnb[i];

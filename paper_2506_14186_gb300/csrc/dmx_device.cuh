@@ -17,6 +17,7 @@
 //                           softplus in place of the ReLU of a_ref (backward)
 //   Sec. 3.1, App. B, C.2   adaptive Dormand-Prince 5(4), PID controller,
 //                           quaternions integrated exactly
+//   Fig. 12                 Tsitouras 5(4) and fixed-step semi-implicit Euler
 //
 // GB300 notes: FP64 runs at 1/62 of the FP32 rate and a warp instruction costs
 // the same whatever its active lanes, so work is split across the group where
@@ -1037,17 +1038,38 @@ __device__ int rhs(const Grp<G>& g, const DevModel& m, const WsT<T>& w, const T*
 }
 
 // ------------------------------------------------------------------ integrator
-// Dormand & Prince (1980) 5(4) coefficients: a (row 7 = the 5th-order weights
-// b, first same as last) and e = b - bhat (bhat: embedded 4th-order weights).
-// nz[s] / enz: bit j set where a[s][j] / e[j] is non-zero, so that the stage
-// sums skip the zero coefficients with an integer test.
+// Explicit one-step schemes as partitioned tableaus on (q, v).  Stage s
+// (s = 1 .. S-1) takes V_s = v_n + h sum_{j<s} av[s][j] K_j and
+// Q_s = q_n (+) h sum_{j<=s} aq[s][j] V_j (V_0 = v_n; a diagonal position
+// coefficient uses the stage's own new velocity), K_s = F(Q_s, V_s, u); the
+// last stage is the step's result and its K the next step's K_0 (first same
+// as last).  e = b - bhat: weights of the embedded error estimate of the
+// adaptive schemes.  nzq / nzv / enz: bit j set where the coefficient is
+// non-zero, so that the stage sums skip zeros with an integer test.
+enum { METHOD_DOPRI5 = 0, METHOD_TSIT5 = 1, METHOD_EULER = 2, NMETHOD = 3 };
 struct Tab {
-  double a[7][7];
+  int S, adaptive;
+  double aq[7][7], av[7][7];
   double e[7];
-  unsigned nz[7], enz;
+  unsigned nzq[7], nzv[7], enz;
 };
-__host__ __device__ constexpr Tab make_tab() {
-  Tab t{{{0, 0, 0, 0, 0, 0, 0},
+__host__ __device__ constexpr void finish_tab(Tab& t) {
+  for (int s = 0; s < 7; ++s) {
+    t.nzq[s] = 0u; t.nzv[s] = 0u;
+    for (int j = 0; j < 7; ++j) {
+      if (t.aq[s][j] != 0.0) t.nzq[s] |= 1u << j;
+      if (t.av[s][j] != 0.0) t.nzv[s] |= 1u << j;
+    }
+  }
+  t.enz = 0u;
+  for (int j = 0; j < 7; ++j)
+    if (t.e[j] != 0.0) t.enz |= 1u << j;
+}
+// Dormand & Prince (1980) 5(4): row 7 = the 5th-order weights b.
+__host__ __device__ constexpr Tab make_dopri5() {
+  Tab t{7, 1,
+        {},
+        {{0, 0, 0, 0, 0, 0, 0},
          {1.0 / 5.0, 0, 0, 0, 0, 0, 0},
          {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0, 0},
          {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0, 0},
@@ -1056,16 +1078,48 @@ __host__ __device__ constexpr Tab make_tab() {
          {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0}},
         {35.0 / 384.0 - 5179.0 / 57600.0, 0.0, 500.0 / 1113.0 - 7571.0 / 16695.0, 125.0 / 192.0 - 393.0 / 640.0,
          -2187.0 / 6784.0 + 92097.0 / 339200.0, 11.0 / 84.0 - 187.0 / 2100.0, -1.0 / 40.0},
-        {0, 0, 0, 0, 0, 0, 0},
-        0u};
+        {}, {}, 0u};
   for (int s = 0; s < 7; ++s)
-    for (int j = 0; j < 7; ++j)
-      if (t.a[s][j] != 0.0) t.nz[s] |= 1u << j;
-  for (int j = 0; j < 7; ++j)
-    if (t.e[j] != 0.0) t.enz |= 1u << j;
+    for (int j = 0; j < 7; ++j) t.aq[s][j] = t.av[s][j];
+  finish_tab(t);
   return t;
 }
-static __constant__ Tab c_tab = make_tab();
+// Tsitouras (2011) 5(4) (the paper's default solver): row 7 = b, e its
+// published error weights.
+__host__ __device__ constexpr Tab make_tsit5() {
+  Tab t{7, 1,
+        {},
+        {{0, 0, 0, 0, 0, 0, 0},
+         {0.161, 0, 0, 0, 0, 0, 0},
+         {-0.008480655492356989, 0.335480655492357, 0, 0, 0, 0, 0},
+         {2.897153057105493, -6.359448489975075, 4.3622954328695815, 0, 0, 0, 0},
+         {5.325864828439257, -11.748883564062828, 7.4955393428898365, -0.09249506636175525, 0, 0, 0},
+         {5.86145544294642, -12.92096931784711, 8.159367898576159, -0.071584973281401, -0.028269050394068383, 0, 0},
+         {0.09646076681806523, 0.01, 0.4798896504144996, 1.379008574103742, -3.290069515436081, 2.324710524099774,
+          0}},
+        {-0.00178001105222577714, -0.0008164344596567469, 0.007880878010261995, -0.1447110071732629,
+         0.5823571654525552, -0.45808210592918697, 0.015151515151515152},
+        {}, {}, 0u};
+  for (int s = 0; s < 7; ++s)
+    for (int j = 0; j < 7; ++j) t.aq[s][j] = t.av[s][j];
+  finish_tab(t);
+  return t;
+}
+// Semi-implicit Euler with a fixed step (the MuJoCo XLA integrator the paper
+// compares against): v_{n+1} = v_n + h K_0, q_{n+1} = q_n (+) h v_{n+1}.
+__host__ __device__ constexpr Tab make_euler() {
+  Tab t{2, 0, {}, {}, {}, {}, {}, 0u};
+  t.av[1][0] = 1.0;
+  t.aq[1][1] = 1.0;
+  finish_tab(t);
+  return t;
+}
+struct TabSet {
+  Tab t[NMETHOD];
+};
+__host__ __device__ constexpr TabSet make_tabs() { return TabSet{{make_dopri5(), make_tsit5(), make_euler()}}; }
+static __constant__ TabSet c_tabs = make_tabs();
+#define TAB(mt) (c_tabs.t[(mt)])
 
 // q (+) dq for every joint (free: translation + body-frame rotation exponential).
 template <int G, class T>
@@ -1109,32 +1163,33 @@ __device__ __forceinline__ double pos_mag(const DevModel& m, const double* q, in
   return d < 3 ? fabs(q[m.b_qadr[b] + d]) : 1.0;
 }
 
-// The six new stages of a DOPRI5 step of size h from (qn, vn) with
-// ka[0] = F(qn, vn): stage velocities kv[s], derivatives ka[s], the
-// 5th-order solution in (qs, vs) and its derivative in ka[6].  hook(s, status)
+// The new stages of one step of scheme mt (TAB(mt)) of size h from (qn, vn)
+// with ka[0] = F(qn, vn): stage velocities kv[s], derivatives ka[s], the
+// result in (qs, vs) and its derivative in ka[(S-1) nv].  hook(s, status)
 // runs after the right-hand side of stage s (the workspace then holds that
 // evaluation).  Returns the worst stage status.
 template <int G, class Hook>
-__device__ int dopri5_stages(const Grp<G>& g, const DevModel& m, const Ws& w, const double* u, double h, Hook&& hook) {
+__device__ int rk_stages(const Grp<G>& g, const DevModel& m, const Ws& w, const double* u, double h, int mt,
+                         Hook&& hook) {
   const Layout& L = *w.L;
-  const int nv = m.nv;
+  const int nv = m.nv, S = TAB(mt).S;
   const double* qn = w.at(L.qn); const double* vn = w.at(L.vn);
   double* qs = w.at(L.qs); double* vs = w.at(L.vs);
   double* kv = w.at(L.kv); double* ka = w.at(L.ka); double* dq = w.at(L.dq);
   int st = 0;
   for (int i = g.lane; i < nv; i += G) kv[i] = vn[i];
   g.sync();
-  for (int s = 1; s < 7; ++s) {
+  for (int s = 1; s < S; ++s) {
+    const unsigned mq = TAB(mt).nzq[s], mv = TAB(mt).nzv[s];
     for (int i = g.lane; i < nv; i += G) {
       double sq = 0, sv = 0;
       for (int j = 0; j < s; ++j) {
-        if (!((c_tab.nz[s] >> j) & 1u)) continue;
-        const double c = c_tab.a[s][j];
-        sq += c * kv[j * nv + i];
-        sv += c * ka[j * nv + i];
+        if ((mq >> j) & 1u) sq += TAB(mt).aq[s][j] * kv[j * nv + i];
+        if ((mv >> j) & 1u) sv += TAB(mt).av[s][j] * ka[j * nv + i];
       }
-      dq[i] = h * sq;
       const double vv = vn[i] + h * sv;
+      if ((mq >> s) & 1u) sq += TAB(mt).aq[s][s] * vv;
+      dq[i] = h * sq;
       vs[i] = vv;
       kv[s * nv + i] = vv;
     }
@@ -1147,24 +1202,28 @@ __device__ int dopri5_stages(const Grp<G>& g, const DevModel& m, const Ws& w, co
   return st;
 }
 
-// One DOPRI5 attempt of size h from (qn, vn) with ka[0] = F(qn, vn).  Leaves
-// the 5th-order solution in (qs, vs) and its derivative in ka[6]; returns the
-// RMS error norm (NaN-safe: non-finite -> +inf) and the worst stage status.
+// One attempt of scheme mt of size h from (qn, vn) with ka[0] = F(qn, vn).
+// Leaves the result in (qs, vs) and its derivative in ka[(S-1) nv]; returns
+// the RMS error norm of the embedded estimate (NaN-safe: non-finite -> +inf;
+// 0 for a fixed-step scheme) and the worst stage status.
 template <int G>
-__device__ double dopri5_attempt(const Grp<G>& g, const DevModel& m, const Ws& w, const double* u, double h,
-                                 double rtol, double atol, int* st_out) {
+__device__ double rk_attempt(const Grp<G>& g, const DevModel& m, const Ws& w, const double* u, double h, int mt,
+                             double rtol, double atol, int* st_out) {
   const Layout& L = *w.L;
   const int nv = m.nv;
   const double* qn = w.at(L.qn); const double* vn = w.at(L.vn);
   const double* qs = w.at(L.qs); const double* vs = w.at(L.vs);
   const double* kv = w.at(L.kv); const double* ka = w.at(L.ka);
-  const int st = dopri5_stages(g, m, w, u, h, [](int, int) {});
+  const int st = rk_stages(g, m, w, u, h, mt, [](int, int) {});
+  *st_out = st;
+  if (!TAB(mt).adaptive) return 0.0;
+  const unsigned enz = TAB(mt).enz;
   double acc = 0;
   for (int i = g.lane; i < nv; i += G) {
     double ep = 0, ev = 0;
     for (int j = 0; j < 7; ++j) {
-      if (!((c_tab.enz >> j) & 1u)) continue;
-      const double c = c_tab.e[j];
+      if (!((enz >> j) & 1u)) continue;
+      const double c = TAB(mt).e[j];
       ep += c * kv[j * nv + i];
       ev += c * ka[j * nv + i];
     }
@@ -1175,7 +1234,6 @@ __device__ double dopri5_attempt(const Grp<G>& g, const DevModel& m, const Ws& w
     acc += r1 * r1 + r2 * r2;
   }
   acc = g.sum(acc);
-  *st_out = st;
   const double err = sqrt(acc / (2.0 * nv));
   return isfinite(err) ? err : INFINITY;
 }

@@ -7,7 +7,9 @@
 // (steps never straddle a control change; a step that would leave less than
 // 1e-12 s before the boundary is stretched to it); accept iff the RMS error
 // norm <= 1; PID factor 0.9 err^-(P+I)/5 err_prev^(P/5) clipped to [0.2, 10]
-// with P = 0.2, I = 0.4; on rejection h *= max(0.2, 0.9 err^-1/5).
+// with P = 0.2, I = 0.4; on rejection h *= max(0.2, 0.9 err^-1/5).  A
+// fixed-step scheme (semi-implicit Euler) accepts every step and proposes h0
+// after each.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -83,7 +85,8 @@ __device__ void env_attempt(const Grp<G>& g, const DevModel& m, const Ws& w, con
   const double ht = clamped ? hb : s.h;
   if (ht < 1e-12) { s.st = ENV_H_UNDERFLOW; s.done = 1; return; }
   int stage_st = 0;
-  const double err = dopri5_attempt(g, m, w, w.at(L.u), ht, P.rtol, P.atol, &stage_st);
+  const int mt = P.method;
+  const double err = rk_attempt(g, m, w, w.at(L.u), ht, mt, P.rtol, P.atol, &stage_st);
   ++s.att;
   if (err <= 1.0) {
     if (stage_st != ENV_OK) { s.st = stage_st; s.done = 1; return; }
@@ -93,18 +96,23 @@ __device__ void env_attempt(const Grp<G>& g, const DevModel& m, const Ws& w, con
     double* qn = w.at(L.qn); double* vn = w.at(L.vn);
     const double* qs = w.at(L.qs); const double* vs = w.at(L.vs);
     double* ka = w.at(L.ka);
+    const int last = (TAB(mt).S - 1) * m.nv;
     for (int i = g.lane; i < m.nq; i += G) qn[i] = qs[i];
-    for (int i = g.lane; i < m.nv; i += G) { vn[i] = vs[i]; ka[i] = ka[6 * m.nv + i]; }
+    for (int i = g.lane; i < m.nv; i += G) { vn[i] = vs[i]; ka[i] = ka[last + i]; }
     g.sync();
     ++s.nacc;
-    const double errf = fmax(err, 1e-10);
-    // 0.9 err^-(P+I)/5 err_prev^(P/5) as one exponential of the logs (the
-    // previous log is carried over)
-    const double lerr = log(errf);
-    double fac = 0.9 * exp(-(0.6 / 5.0) * lerr + (0.2 / 5.0) * s.lerrp);
-    fac = fmin(10.0, fmax(0.2, fac));
-    s.lerrp = lerr;
-    s.h = ht * fac;
+    if (TAB(mt).adaptive) {
+      const double errf = fmax(err, 1e-10);
+      // 0.9 err^-(P+I)/5 err_prev^(P/5) as one exponential of the logs (the
+      // previous log is carried over)
+      const double lerr = log(errf);
+      double fac = 0.9 * exp(-(0.6 / 5.0) * lerr + (0.2 / 5.0) * s.lerrp);
+      fac = fmin(10.0, fmax(0.2, fac));
+      s.lerrp = lerr;
+      s.h = ht * fac;
+    } else {
+      s.h = P.h0;   // fixed step (the last step of an interval may have been shortened)
+    }
     if (P.ckpt && (s.nacc % P.K) == 0) write_checkpoint(g, m, w, P, env, s.nacc / P.K, s.t);
     if (reached) {
       ++s.k;

@@ -10,6 +10,7 @@ struct RolloutParams {
   const DevModel* model;
   Layout L;
   int B, NI, max_steps, K;
+  int method;           // METHOD_* integration scheme (dmx_device.cuh)
   double rtol, atol, h0;
   const double* x0;     // [nx][B]
   const double* ctrl;   // [NI][nu][B]

@@ -135,7 +135,7 @@ DMX_HD inline LayoutBar make_bar_layout(const DevModel& m, int rcap) {
   B.q = take(nq); B.v = take(nv); B.u = take(nu);
   B.gb = take(12 * (m.ngeom > 0 ? m.ngeom : 1)); B.iv = take(6 * nb); B.ivb = take(6 * nb);
   B.sc = take(2 * nb); B.tk = take(9 * nb);
-  B.qn = take(nq); B.vst = take(6 * nv); B.dq = take(nv); B.dqb = take(nv); B.Qs = take(nq);
+  B.qn = take(nq); B.vst = take(7 * nv); B.dq = take(nv); B.dqb = take(nv); B.Qs = take(nq);
   B.kab = take(6 * nv); B.kvb = take(6 * nv); B.Qb = take(nq); B.Vb = take(nv);
   B.qnb = take(nq); B.vnb = take(nv); B.ub = take(nu); B.xb = take(nq + nv);
   B.nd = (o + 1) & ~1;

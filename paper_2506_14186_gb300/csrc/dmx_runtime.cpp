@@ -376,7 +376,7 @@ static dmx_status make_tape(dmx_model* m, const dmx_rollout_args* a, const doubl
   t->model = m;
   t->B = a->B; t->NI = a->NI; t->K = a->K; t->nx = m->host.nq + m->host.nv; t->nu = m->host.nu;
   t->max_steps = a->max_steps; t->ncheck = ncheck_for(a->max_steps, a->K);
-  t->rtol = a->rtol; t->atol = a->atol; t->h0 = a->h0;
+  t->rtol = a->rtol; t->atol = a->atol; t->h0 = a->h0; t->method = a->method;
   const size_t B = a->B;
   const size_t bytes = sizeof(double) * ((size_t)t->ncheck * (t->nx + 1) * B + (size_t)a->max_steps * B +
                                          (size_t)a->NI * t->nu * B + B) + sizeof(int) * B;
@@ -407,10 +407,11 @@ extern "C" dmx_status dmx_rollout(dmx_model* m, const dmx_rollout_args* a, void*
   const int nq = m->host.nq, nv = m->host.nv, nx = nq + nv, nu = m->host.nu;
   if (a->B < 0) return dmx_fail(DMX_ERR_INVALID, "B must be >= 0");
   if (a->NI < 1) return dmx_fail(DMX_ERR_INVALID, "NI must be >= 1");
-  if (!(a->rtol > 0) || !(a->atol > 0) || !(a->h0 > 0)) return dmx_fail(DMX_ERR_INVALID, "rtol, atol and h0 must be > 0");
+  if (!(a->rtol >= 0) || !(a->atol > 0) || !(a->h0 > 0)) return dmx_fail(DMX_ERR_INVALID, "rtol >= 0, atol > 0 and h0 > 0 are required");
   if (a->max_steps < 1) return dmx_fail(DMX_ERR_INVALID, "max_steps must be >= 1");
   if (a->tape && a->K < 1) return dmx_fail(DMX_ERR_INVALID, "K must be >= 1 when a tape is requested");
   if (a->form < DMX_FORM_PERSISTENT || a->form > DMX_FORM_STEP_GRAPH) return dmx_fail(DMX_ERR_INVALID, "unknown form");
+  if (a->method < DMX_METHOD_DOPRI5 || a->method > DMX_METHOD_EULER) return dmx_fail(DMX_ERR_INVALID, "unknown method");
   if (a->lanes != 0 && !valid_lanes(a->lanes)) return dmx_fail(DMX_ERR_INVALID, "lanes must be 0, 1, 2, 4, 8, 16 or 32");
   if (a->B > 0 && (!a->x0 || !a->T || !a->xT)) return dmx_fail(DMX_ERR_INVALID, "x0, T and xT are required");
   if (a->B > 0 && nu > 0 && !a->ctrl) return dmx_fail(DMX_ERR_INVALID, "ctrl is required when the model has actuators");
@@ -422,7 +423,7 @@ extern "C" dmx_status dmx_rollout(dmx_model* m, const dmx_rollout_args* a, void*
   const size_t B = a->B;
   RolloutParams P{};
   P.model = m->dev; P.L = m->L; P.B = a->B; P.NI = a->NI; P.max_steps = a->max_steps; P.K = a->K > 0 ? a->K : 1;
-  P.rtol = a->rtol; P.atol = a->atol; P.h0 = a->h0;
+  P.rtol = a->rtol; P.atol = a->atol; P.h0 = a->h0; P.method = a->method;
   P.x0 = a->x0; P.ctrl = a->ctrl; P.T = a->T; P.xT = a->xT; P.xb = a->xb;
   P.nsteps = a->nsteps; P.nrej = a->nrej; P.status = a->status;
   if (a->host && B > 0) {
@@ -536,7 +537,7 @@ size_t adjoint_scratch_bound(dmx_model* m, int B, int K, int cfd) {
   }
   const size_t groups = (size_t)std::max(B, 1), k = (size_t)std::max(K, 1);
   const size_t nx = m->host.nq + m->host.nv;
-  size_t b = sizeof(double) * groups * k * std::max<size_t>(m->host.nq + 6 * m->host.nv + 1, nx + 1);
+  size_t b = sizeof(double) * groups * k * std::max<size_t>(dmx::rev_row_doubles(m->host), nx + 1);
   if (mode == DMX_ADJ_REVERSE && !cfd)
     b += std::min(kSnapMaxBytes, sizeof(double) * groups * k * 6 * (size_t)dmx::snap_offsets(m->host, m->L).size);
   (void)cfd;
@@ -567,7 +568,7 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
   }
   dmx::AdjParams P{};
   const dmx::Layout& L = layout_for(m, cfd);
-  P.model = m->dev; P.L = L; P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd;
+  P.model = m->dev; P.L = L; P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd; P.method = t->method;
   P.ckpt = t->ckpt; P.hlog = t->hlog; P.tape_n = t->n; P.ctrl = t->ctrl; P.T = t->T;
   P.xT_bar = xT_bar; P.xb_bar = xb_bar; P.x0_bar = x0_bar; P.ctrl_bar = m->host.nu ? ctrl_bar : nullptr;
   if (mode == DMX_ADJ_TANGENT) {
@@ -595,7 +596,7 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
   const int occ = std::max(1, dmx::adjoint_rev_occupancy(G, threads, smem));
   int blocks = (t->B + gpb - 1) / gpb;
   blocks = std::min(blocks, m->nsm * occ);
-  const int RW = m->host.nq + 6 * m->host.nv + 1;
+  const int RW = dmx::rev_row_doubles(m->host);
   const size_t seg_bytes = sizeof(double) * (size_t)blocks * gpb * t->K * RW;
   // stage snapshots (forward right-hand side only): used when they fit a
   // share of the free device memory, else each stage is evaluated again

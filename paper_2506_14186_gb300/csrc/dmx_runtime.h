@@ -33,6 +33,7 @@ struct dmx_model {
 struct dmx_tape {
   dmx_model* model = nullptr;
   int B = 0, NI = 1, K = 1, nx = 0, nu = 0, max_steps = 0, ncheck = 0, G = 1;
+  int method = 0;           // integration scheme of the taped rollout (DMX_METHOD_*)
   double rtol = 0, atol = 0, h0 = 0;
   void* mem = nullptr;
   size_t bytes = 0;

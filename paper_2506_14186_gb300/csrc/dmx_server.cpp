@@ -292,7 +292,7 @@ extern "C" dmx_status dmx_server_create(const dmx_server_cfg* cfg, dmx_server** 
 
 extern "C" dmx_status dmx_submit(dmx_server* s, const dmx_request* r, uint64_t* ticket) {
   if (!s || !r || !ticket) return dmx_fail(DMX_ERR_INVALID, "null argument");
-  if (!r->model || r->B < 0 || r->NI < 1 || r->max_steps < 1 || !(r->rtol > 0) || !(r->atol > 0) || !(r->h0 > 0))
+  if (!r->model || r->B < 0 || r->NI < 1 || r->max_steps < 1 || !(r->rtol >= 0) || !(r->atol > 0) || !(r->h0 > 0))
     return dmx_fail(DMX_ERR_INVALID, "bad request sizes or tolerances");
   int32_t nu = 0;
   dmx_model_dims(r->model, nullptr, nullptr, &nu);

@@ -47,7 +47,7 @@ extern "C" dmx_status dmx_rollout_static(dmx_model* m, const dmx_rollout_args* a
   const int nq = m->host.nq, nv = m->host.nv, nu = m->host.nu;
   if (a->B < 0) return dmx_fail(DMX_ERR_INVALID, "B must be >= 0");
   if (a->NI < 1) return dmx_fail(DMX_ERR_INVALID, "NI must be >= 1");
-  if (!(a->rtol > 0) || !(a->atol > 0) || !(a->h0 > 0)) return dmx_fail(DMX_ERR_INVALID, "rtol, atol and h0 must be > 0");
+  if (!(a->rtol >= 0) || !(a->atol > 0) || !(a->h0 > 0)) return dmx_fail(DMX_ERR_INVALID, "rtol >= 0, atol > 0 and h0 > 0 are required");
   if (a->max_steps < 1) return dmx_fail(DMX_ERR_INVALID, "max_steps must be >= 1");
   if (a->host) return dmx_fail(DMX_ERR_INVALID, "dmx_rollout_static takes device buffers only (host = 0)");
   if (a->tape) return dmx_fail(DMX_ERR_INVALID, "dmx_rollout_static records no tape (tape must be NULL)");
@@ -87,7 +87,7 @@ extern "C" dmx_status dmx_rollout_static(dmx_model* m, const dmx_rollout_args* a
   S.active = takeI(1);
   RolloutParams P{};
   P.model = m->dev; P.L = m->L; P.B = a->B; P.NI = a->NI; P.max_steps = a->max_steps; P.K = 1;
-  P.rtol = a->rtol; P.atol = a->atol; P.h0 = a->h0;
+  P.rtol = a->rtol; P.atol = a->atol; P.h0 = a->h0; P.method = a->method;
   P.x0 = a->x0; P.ctrl = a->ctrl; P.T = a->T; P.xT = a->xT; P.xb = a->xb;
   P.nsteps = a->nsteps; P.nrej = a->nrej; P.status = a->status;
   // the unfinished-environment counter must start at B; every other field is

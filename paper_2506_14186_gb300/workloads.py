@@ -249,9 +249,36 @@ def quadruped_inputs(B=8192, seed=1004):
     return {"x0": x0, "ctrl": ctrl, "T": T, "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3, "max_steps": 20000}
 
 
+def toss_scene():
+    """Cube toss of the integrator comparison (Sec. 3, Fig. 12): the 0.1 m,
+    1 kg cube with the toss contact setting solref (0.005 s, 1)."""
+    sc = box_scene(solref=(0.005, 1.0))
+    sc["name"] = "toss"
+    return sc
+
+
+def toss_inputs(B=2048, seed=1006, T=1.0):
+    """Cube tosses as in the paper's integrator comparison (a cube thrown
+    onto the plane at v_x = -2 m/s): centre height 0.2 + U[0, 0.05] m, small
+    random tilt (quaternion (1, N(0, 0.05)^3), normalised), initial velocity
+    (-2 + N(0, 0.05), N(0, 0.05), 0) m/s, no spin.  Loss: the final x position
+    (toss distance), gradient w.r.t. the initial velocity."""
+    g = _rng(seed)
+    x0 = np.zeros((B, 13))
+    x0[:, 2] = 0.2 + g.uniform(0.0, 0.05, B)
+    qq = np.concatenate([np.ones((B, 1)), g.normal(0.0, 0.05, (B, 3))], axis=1)
+    x0[:, 3:7] = qq / np.linalg.norm(qq, axis=1, keepdims=True)
+    x0[:, 7] = -2.0 + g.normal(0.0, 0.05, B)
+    x0[:, 8] = g.normal(0.0, 0.05, B)
+    return {"x0": x0, "ctrl": None, "T": np.full(B, T), "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3,
+            "max_steps": 20000}
+
+
 def chain_goal():
     return np.asarray(CUBE_GOAL)
 
 
-SCENES = {"ball": ball_scene, "box": box_scene, "chain_cube": chain_cube_scene, "quadruped": quadruped_scene}
-INPUTS = {"ball": ball_inputs, "box": box_push_inputs, "chain_cube": chain_inputs, "quadruped": quadruped_inputs}
+SCENES = {"ball": ball_scene, "box": box_scene, "chain_cube": chain_cube_scene, "quadruped": quadruped_scene,
+          "toss": toss_scene}
+INPUTS = {"ball": ball_inputs, "box": box_push_inputs, "chain_cube": chain_inputs, "quadruped": quadruped_inputs,
+          "toss": toss_inputs}

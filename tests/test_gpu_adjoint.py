@@ -42,13 +42,13 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def gpu_grad(dmx, model, inp, xT_bar, xb_bar=None, cfd=False, K=32, mode="reverse"):
+def gpu_grad(dmx, model, inp, xT_bar, xb_bar=None, cfd=False, K=32, mode="reverse", method="dopri5"):
     """Taped GPU rollout + adjoint (reverse-mode or tangent kernel).  Arrays
     env-major in and out."""
     model.set_adjoint(mode)
     ctrl = None if inp["ctrl"] is None else _dev(np.transpose(inp["ctrl"], (1, 2, 0)))
     out = dmx.rollout(model, _dev(inp["x0"].T), _dev(inp["T"]), ctrl=ctrl, NI=inp["NI"], rtol=inp["rtol"],
-                      atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"], K=K, tape=True)
+                      atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"], K=K, tape=True, method=method)
     xbb = None if xb_bar is None else _dev(np.transpose(xb_bar, (1, 2, 0)))
     gx, gu = dmx.rollout_grad(out["tape"], _dev(xT_bar.T), xbb, cfd=cfd)
     hlog, n = out["tape"].read()
@@ -59,10 +59,10 @@ def gpu_grad(dmx, model, inp, xT_bar, xb_bar=None, cfd=False, K=32, mode="revers
     return res
 
 
-def oracle_grad(orc_mod, scene, inp, g, xT_bar, xb_bar=None, cfd=False):
+def oracle_grad(orc_mod, scene, inp, g, xT_bar, xb_bar=None, cfd=False, method="dopri5"):
     m = orc_mod.OracleModel(scene)
     return m.batch_replay_grad(inp["x0"], inp["T"], g["hlog"], g["n"], xT_bar, ctrl=inp["ctrl"], NI=inp["NI"],
-                               cfd=cfd, xb_bar=xb_bar)
+                               cfd=cfd, xb_bar=xb_bar, method=method)
 
 
 def assert_grad(g, o, key="x0_bar"):
@@ -344,3 +344,26 @@ def test_quadruped_gradient_at_full_horizons(dmx, orc_mod):
     g = {"x0_bar": gx.cpu().numpy().T[idx], "ctrl_bar": np.transpose(gu.cpu().numpy(), (2, 0, 1))[idx]}
     assert_grad(g, o)
     assert_grad(g, o, "ctrl_bar")
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("method", ["tsit5", "euler"])
+def test_other_schemes_gradient(dmx, orc_mod, method, mode):
+    """Discrete adjoint of the Tsitouras and semi-implicit Euler rollouts in
+    every adjoint kernel against the oracle along the GPU's steps: balls
+    (1 s, with CFD), box pushes (0.1 s) and the arm (controls, boundary
+    cotangents; 0.2 s), K = 3 so segments span several checkpoints."""
+    rng = np.random.default_rng(11)
+    for name, inp, cfd in (("ball", W.ball_inputs(8), True), ("box", W.box_push_inputs(12, seed=5, T=0.1), False),
+                           ("chain_cube", W.chain_inputs(6, T=0.2, NI=4), False)):
+        sc = W.SCENES[name](**CFD_OPT) if cfd else W.SCENES[name]()
+        m = dmx.Model(sc)
+        B = len(inp["x0"])
+        xT_bar = rng.normal(size=(B, m.nx))
+        xb_bar = rng.normal(size=(B, inp["NI"] + 1, m.nx)) if name == "chain_cube" else None
+        g = gpu_grad(dmx, m, inp, xT_bar, xb_bar=xb_bar, cfd=cfd, K=3, mode=mode, method=method)
+        assert np.all(g["status"] == 0)
+        o = oracle_grad(orc_mod, sc, inp, g, xT_bar, xb_bar=xb_bar, cfd=cfd, method=method)
+        assert_grad(g, o)
+        if m.nu:
+            assert_grad(g, o, "ctrl_bar")

@@ -86,13 +86,13 @@ def gpu_rollout(dmx, model, inp, tape=False, **kw):
     return res
 
 
-def oracle_free(orc_mod, scene, inp, want_xb=False):
+def oracle_free(orc_mod, scene, inp, want_xb=False, method="dopri5"):
     m = orc_mod.OracleModel(scene)
     return m.batch_rollout(inp["x0"], inp["T"], ctrl=inp["ctrl"], NI=inp["NI"], rtol=inp["rtol"], atol=inp["atol"],
-                           h0=inp["h0"], max_steps=inp["max_steps"], want_xb=want_xb)
+                           h0=inp["h0"], max_steps=inp["max_steps"], want_xb=want_xb, method=method)
 
 
-def assert_replay_parity(orc_mod, scene, inp, g, envs=None):
+def assert_replay_parity(orc_mod, scene, inp, g, envs=None, method="dopri5"):
     """The oracle replays each environment's GPU step sequence."""
     m = orc_mod.OracleModel(scene)
     envs = range(len(inp["x0"])) if envs is None else envs
@@ -101,7 +101,8 @@ def assert_replay_parity(orc_mod, scene, inp, g, envs=None):
         n = int(g["tape_n"][e])
         assert n == g["nsteps"][e]
         ctrl = None if inp["ctrl"] is None else inp["ctrl"][e]
-        xT, xb = m.replay(inp["x0"][e], g["hlog"][e, :n], ctrl=ctrl, T=float(inp["T"][e]), NI=inp["NI"])
+        xT, xb = m.replay(inp["x0"][e], g["hlog"][e, :n], ctrl=ctrl, T=float(inp["T"][e]), NI=inp["NI"],
+                          method=method)
         worst = max(worst, rel_err(g["xT"][e], xT))
         if "xb" in g:
             for k in range(inp["NI"] + 1):
@@ -117,7 +118,7 @@ def _interval(T, NI, t):
     return k
 
 
-def assert_stepwise_parity(orc_mod, scene, inp, g, envs=None, check_valid=True):
+def assert_stepwise_parity(orc_mod, scene, inp, g, envs=None, check_valid=True, method="dopri5"):
     """Each accepted GPU step, started from the GPU's state, against one oracle
     step of the same size (tape with checkpoint interval 1); and the oracle's
     error norm of each of those steps is <= 1 (the step would be accepted)."""
@@ -134,11 +135,12 @@ def assert_stepwise_parity(orc_mod, scene, inp, g, envs=None, check_valid=True):
             ctrl = None
             if inp["ctrl"] is not None:
                 ctrl = inp["ctrl"][e][_interval(T, inp["NI"], ts)][None, :]
-            xo, _ = m.replay(xs, [h], ctrl=ctrl, T=h, NI=1)
+            xo, _ = m.replay(xs, [h], ctrl=ctrl, T=h, NI=1, method=method)
             worst = max(worst, rel_err(ck[s_ + 1, :nx], xo))
             # the GPU's step sequence is a valid one: the oracle's error norm accepts each step
             if check_valid:
-                err = m.step_error(xs, h, u=None if ctrl is None else ctrl[0], rtol=inp["rtol"], atol=inp["atol"])
+                err = m.step_error(xs, h, u=None if ctrl is None else ctrl[0], rtol=inp["rtol"], atol=inp["atol"],
+                                   method=method)
                 worst_err = max(worst_err, err)
             count += 1
     assert count > 0
@@ -393,3 +395,51 @@ def test_step_size_sequence_equals_oracle(dmx, orc_mod):
         n = int(g["tape_n"][0])
         assert n == o["nsteps"] and g["nrej"][0] == o["nrej"]
         np.testing.assert_allclose(g["hlog"][0, :n], o["hlog"], rtol=1e-9)
+
+
+# ---------------------------------------------------------------- other schemes (Fig. 12, Sec. 3.1)
+@pytest.mark.parametrize("method", ["tsit5", "euler"])
+def test_other_schemes_match_oracle(dmx, orc_mod, method):
+    """Tsitouras 5(4) with the PID controller and fixed-step semi-implicit Euler
+    (h0 = 1 ms): every accepted step against one oracle step of the same
+    scheme and size, whole-trajectory replay, and free-running step sequences
+    (balls: states and step counts; the fixed-step scheme takes exactly the
+    same steps on both sides) on balls, box pushes and the arm."""
+    sc, inp = W.ball_scene(), W.ball_inputs(16)
+    m = dmx.Model(sc)
+    g = gpu_rollout(dmx, m, inp, tape=True, K=1, method=method)
+    assert_stepwise_parity(orc_mod, sc, inp, g, method=method)
+    assert_replay_parity(orc_mod, sc, inp, g, method=method)
+    f = gpu_rollout(dmx, m, inp, method=method)
+    o = oracle_free(orc_mod, sc, inp, method=method)
+    assert_free_parity(f, o)
+    if method == "euler":
+        np.testing.assert_array_equal(f["nsteps"], o["nsteps"])
+        assert np.all(f["nrej"] == 0)
+    sc = W.box_scene()
+    inp = _sub(W.box_push_inputs(4096), np.arange(40))
+    m = dmx.Model(sc)
+    for lanes in (4, 8):
+        g = gpu_rollout(dmx, m, _short(inp, 0.1), tape=True, K=1, lanes=lanes, method=method)
+        assert_stepwise_parity(orc_mod, sc, _short(inp, 0.1), g, method=method)
+    s = _short(inp)
+    assert_replay_parity(orc_mod, sc, s, gpu_rollout(dmx, m, s, tape=True, method=method), method=method)
+    sc = W.chain_cube_scene()
+    inp = W.chain_inputs(12, T=0.2, NI=5)
+    m = dmx.Model(sc)
+    g = gpu_rollout(dmx, m, inp, tape=True, K=1, want_xb=True, method=method)
+    assert_stepwise_parity(orc_mod, sc, inp, g, method=method)
+
+
+def test_scheme_forms_bitwise_equal(dmx):
+    """Every launch form runs the same scheme: persistent, per-attempt and
+    graph-replayed forms give bitwise-equal Tsit5 and Euler results."""
+    sc = W.box_scene()
+    inp = _sub(W.box_push_inputs(4096), np.arange(29))
+    m = dmx.Model(sc)
+    for method in ("tsit5", "euler"):
+        a = gpu_rollout(dmx, m, inp, lanes=8, method=method)
+        for form in ("step", "graph"):
+            b = gpu_rollout(dmx, m, inp, lanes=8, form=form, method=method)
+            np.testing.assert_array_equal(a["xT"], b["xT"])
+            np.testing.assert_array_equal(a["nsteps"], b["nsteps"])
