@@ -286,8 +286,10 @@ class OracleModel:
                 "nrhs": st[:, 3].copy()}
 
     def batch_replay_grad(self, x0, T, hlog, n, xT_bar, ctrl=None, NI=1, cfd=False, xb_bar=None, nthreads=None,
-                          method="dopri5"):
-        """Discrete adjoint along given accepted step sizes (hlog [B, >= max n], n [B])."""
+                          method="dopri5", params=False):
+        """Discrete adjoint along given accepted step sizes (hlog [B, >= max n], n [B]);
+        params=True adds "p_bar" [B, np]: the gradient w.r.t. the model parameters
+        (solref t_c, phi_d; solimp d_o, d_w, width, midpoint; friction of each pair)."""
         x0 = _f64(x0)
         B = x0.shape[0]
         hlog = _f64(hlog)
@@ -295,11 +297,19 @@ class OracleModel:
         xT = np.zeros((B, self.nx)); gx = np.zeros((B, self.nx))
         gu = np.zeros((B, NI, self.nu)) if self.nu else None
         c = _f64(ctrl) if (ctrl is not None and self.nu) else None
+        pb = np.zeros((B, self.nparams())) if params else None
         lib().orc_batch_replay_grad(self.h, B, _p(x0), _p(c), _p(_f64(np.broadcast_to(T, (B,)))), NI, _p(hlog),
                                     hlog.shape[1], _p(n), int(cfd), _p(_f64(xT_bar)),
                                     _p(_f64(xb_bar) if xb_bar is not None else None), _p(xT), _p(gx), _p(gu),
-                                    int(nthreads or os.cpu_count() or 1), METHODS[method])
-        return {"xT": xT, "x0_bar": gx, "ctrl_bar": gu}
+                                    int(nthreads or os.cpu_count() or 1), METHODS[method], _p(pb))
+        out = {"xT": xT, "x0_bar": gx, "ctrl_bar": gu}
+        if params:
+            out["p_bar"] = pb
+        return out
+
+    def nparams(self):
+        """Model parameters of the adjoint: t_c, phi_d, d_o, d_w, width, midpoint, then mu of each pair."""
+        return int(lib().orc_nparams(self.h))
 
     def batch_grad(self, x0, T, xT_bar, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, cfd=False,
                    xb_bar=None, nthreads=None, method="dopri5"):

@@ -232,20 +232,23 @@ int orc_rollout_grad(void* h, const double* x0, const double* ctrl, double T, in
   return 0;
 }
 
-// Gradient along a given accepted step sequence (per environment: hlog[e][0:n[e]]).
+// Gradient along a given accepted step sequence (per environment: hlog[e][0:n[e]]);
+// p_bar [B][np] (optional) receives the model-parameter gradients.
 int orc_batch_replay_grad(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, const double* hlog,
                           int hstride, const int* n, int cfd, const double* xT_bar, const double* xb_bar, double* xT,
-                          double* x0_bar, double* ctrl_bar, int nthreads, int method) {
+                          double* x0_bar, double* ctrl_bar, int nthreads, int method, double* p_bar) {
   Model& m = M(h);
-  const int nx = m.nq + m.nv, nu = m.nu;
+  const int nx = m.nq + m.nv, nu = m.nu, np = n_params(m);
   parallel_for(B, nthreads, [&](int b) {
     rollout_grad(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr, make_opts(T[b], NI, 1, 1, 1, 1 << 30, method),
                  cfd != 0, xT_bar + (size_t)b * nx, xb_bar ? xb_bar + (size_t)b * (NI + 1) * nx : nullptr,
                  xT + (size_t)b * nx, x0_bar + (size_t)b * nx, ctrl_bar ? ctrl_bar + (size_t)b * NI * nu : nullptr,
-                 hlog + (size_t)b * hstride, n[b]);
+                 hlog + (size_t)b * hstride, n[b], p_bar ? p_bar + (size_t)b * np : nullptr);
   });
   return 0;
 }
+// Number of model parameters of the adjoint (solref 2, solimp 4, one friction per pair).
+int orc_nparams(void* h) { return n_params(M(h)); }
 int orc_batch_rollout(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, double rtol,
                       double atol, double h0, int max_steps, double* xT, double* xb, int* stats, int nthreads, int method) {
   Model& m = M(h);

@@ -16,6 +16,8 @@
 //   App. C.1 plane-box         box vertices against the plane, pos = v - r/2 n
 //   Sec. 4 CFD                 d(r) continued for r > 0 by the solimp-CFD
 //                              spline; ReLU of a_ref replaced by a softplus
+//   Sec. 5.1, App. E.2         contact parameters (solref, solimp, friction)
+//                              as differentiable model parameters
 // Readings where the paper is silent are listed in the design notes of the
 // repository (integrator, spline form, A_hat, solver stop rule, capsule-box).
 #pragma once
@@ -393,10 +395,22 @@ template <class S> void contacts(const Model& m, const Kin<S>& k, std::vector<Co
 }
 
 // ------------------------------------------------------------------ impedance
+// Model parameters that the adjoint differentiates (the soft-contact
+// parameters of Sec. 2.1 tuned in the system identification of Sec. 5.1 and
+// App. E.2): solref (t_c, phi_d), solimp (d_o, d_w, width, midpoint) and the
+// friction coefficient of every pair.  par<S>(k, v) is the value v of
+// parameter k; in the derivative scalar it carries a unit tangent when k is
+// the direction being differentiated (g_pdir), else none.
+enum { PAR_TC = 0, PAR_DAMP = 1, PAR_DO = 2, PAR_DW = 3, PAR_WIDTH = 4, PAR_MID = 5, PAR_MU0 = 6 };
+extern thread_local int g_pdir;
+template <class S> inline S par(int, double v) { return S(v); }
+template <> inline Dual<double> par<Dual<double>>(int k, double v) { return Dual<double>(v, g_pdir == k ? 1.0 : 0.0); }
+inline int n_params(const Model& m) { return PAR_MU0 + (int)m.pair.size(); }
+
 // Polynomial spline of the solimp shape (midpoint mid, power pw) on x in [0,1].
-template <class S> S spline_shape(const S& x, double mid, double pw) {
-  if (val(x) <= mid && mid > 0) return pow(x, pw) / std::pow(mid, pw - 1.0);
-  return 1.0 - pow(1.0 - x, pw) / std::pow(1.0 - mid, pw - 1.0);
+template <class S, class M> S spline_shape(const S& x, const M& mid, double pw) {
+  if (val(x) <= val(mid) && val(mid) > 0) return pow(x, pw) / pow(mid, pw - 1.0);
+  return 1.0 - pow(1.0 - x, pw) / pow(1.0 - mid, pw - 1.0);
 }
 inline double clamp_imp(double d) { return std::min(std::max(d, 0.0), 0.9999); }
 template <class S> S clamp_imp(const S& d) {
@@ -413,7 +427,9 @@ template <class S> S impedance(const Model& m, const S& r, bool cfd) {
     if (val(x) < 0) x = S(0.0);
     return clamp_imp(dc + (d0 - dc) * spline_shape(x, mc, pc));
   }
-  const double d_o = m.solimp[0], d_w = m.solimp[1], w = m.solimp[2], mid = m.solimp[3], pw = m.solimp[4];
+  const S d_o = par<S>(PAR_DO, m.solimp[0]), d_w = par<S>(PAR_DW, m.solimp[1]), w = par<S>(PAR_WIDTH, m.solimp[2]);
+  const S mid = par<S>(PAR_MID, m.solimp[3]);
+  const double pw = m.solimp[4];
   S x = fabs(r) / w;
   if (val(x) > 1.0) x = S(1.0);
   return clamp_imp(d_o + (d_w - d_o) * spline_shape(x, mid, pw));
@@ -442,8 +458,8 @@ template <class S>
 void make_rows(const Model& m, const Kin<S>& k, const std::vector<Contact<S>>& ct, const S* v, bool cfd, Rows<S>& R) {
   const int nv = m.nv;
   R.nr = 0; R.J.clear(); R.aref.clear(); R.D.clear(); R.slot.clear();
-  const double tc = m.solref[0], damp = m.solref[1], dw = m.solimp[1];
-  const double bcoef = 2.0 / (dw * tc), kcoef = 1.0 / (dw * dw * tc * tc * damp * damp);
+  const S tc = par<S>(PAR_TC, m.solref[0]), damp = par<S>(PAR_DAMP, m.solref[1]), dw = par<S>(PAR_DW, m.solimp[1]);
+  const S bcoef = 2.0 / (dw * tc), kcoef = 1.0 / (dw * dw * tc * tc * damp * damp);
   for (int si = 0; si < (int)ct.size(); ++si) {
     const Contact<S>& c = ct[si];
     const bool incl = cfd ? (val(c.r) < m.cfd[2]) : (val(c.r) < 0);
@@ -458,10 +474,11 @@ void make_rows(const Model& m, const Kin<S>& k, const std::vector<Contact<S>>& c
     S d = impedance(m, c.r, cfd);
     S pterm = cfd ? kcoef * d * (m.softplus_s * softplus(-c.r / m.softplus_s)) : -(kcoef * d * c.r);
     const int nrow = P.condim == 1 ? 1 : 4;
-    const double Ahat = P.condim == 1 ? P.invw : P.invw * (1.0 + P.mu * P.mu);
+    const S mu = par<S>(PAR_MU0 + c.pair, P.mu);
+    const S Ahat = P.condim == 1 ? S(P.invw) : P.invw * (1.0 + mu * mu);
     S Dv = d / (Ahat * (1.0 - d));
     for (int e = 0; e < nrow; ++e) {
-      double sgn = (e & 1) ? -P.mu : P.mu;
+      S sgn = (e & 1) ? -mu : mu;
       const std::vector<S>& jt = (e < 2) ? j1 : j2;
       S jv = S(0.0);
       for (int i = 0; i < nv; ++i) {

@@ -390,25 +390,61 @@ inline void step_jacobian(const Model& m, const double* q, const double* v, cons
   }
 }
 
+// Jacobian (nx x np, row major) of one accepted step (h fixed) with respect to
+// the model parameters (par<S>, dynamics.h), one parameter direction at a
+// time; with cfd the derivatives of every stage come from F~.
+inline void step_jacobian_params(const Model& m, const double* q, const double* v, const double* u, double h,
+                                 bool cfd, std::vector<double>& Jp, int method = METHOD_DOPRI5) {
+  using D = Dual<double>;
+  const int nq = m.nq, nv = m.nv, nu = m.nu, np = n_params(m);
+  Jp.assign((size_t)(nq + nv) * np, 0.0);
+  std::vector<D> qd(nq), vd(nv), ud(std::max(nu, 1)), a1(nv), q7(nq), v7(nv), a7(nv), e(2 * nv);
+  for (int i = 0; i < nq; ++i) qd[i] = D(q[i], 0.0);
+  for (int i = 0; i < nv; ++i) vd[i] = D(v[i], 0.0);
+  for (int i = 0; i < nu; ++i) ud[i] = D(u[i], 0.0);
+  for (int k = 0; k < np; ++k) {
+    g_pdir = k;
+    StageRhs<D> f{m, cfd};
+    f(qd.data(), vd.data(), ud.data(), a1.data());
+    rk_step(m, tableau_of(method), f, qd.data(), vd.data(), a1.data(), ud.data(), h, q7.data(), v7.data(), a7.data(),
+            e.data());
+    for (int i = 0; i < nq; ++i) Jp[(size_t)i * np + k] = q7[i].d;
+    for (int i = 0; i < nv; ++i) Jp[(size_t)(nq + i) * np + k] = v7[i].d;
+  }
+  g_pdir = -1;
+}
+
 // Discrete adjoint (discretize-then-optimize) over the accepted steps of the
 // adaptive rollout: x0_bar = d/dx0 <xT_bar, xT> + sum_k <xb_bar[k], x(t_k)>,
 // ctrl_bar likewise for the piecewise-constant controls.
 // With replay != nullptr the forward pass takes the given accepted step sizes
 // instead of choosing them (the gradient of that frozen step sequence).
+// With p_bar (n_params(m) entries) also the model-parameter gradient
+// p_bar = sum over the accepted steps of (d step / d p)^T lambda_{n+1}.
 inline Result rollout_grad(const Model& m, const double* x0, const double* ctrl, const Opts& o, bool cfd,
                            const double* xT_bar, const double* xb_bar, double* xT, double* x0_bar, double* ctrl_bar,
-                           const double* replay = nullptr, int nreplay = 0) {
+                           const double* replay = nullptr, int nreplay = 0, double* p_bar = nullptr) {
   const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
   std::vector<StepRec> rec;
   Result res = rollout<double>(m, x0, ctrl, o, xT, nullptr, &rec, nullptr, replay, nreplay);
-  std::vector<double> lam(xT_bar, xT_bar + nx), Jx, Ju, nl(nx);
+  std::vector<double> lam(xT_bar, xT_bar + nx), Jx, Ju, Jp, nl(nx);
+  const int np = n_params(m);
   if (ctrl_bar) for (int i = 0; i < o.NI * nu; ++i) ctrl_bar[i] = 0.0;
+  if (p_bar) for (int k = 0; k < np; ++k) p_bar[k] = 0.0;
   for (int n = (int)rec.size() - 1; n >= 0; --n) {
     const StepRec& r = rec[n];
     if (r.reached && xb_bar)
       for (int i = 0; i < nx; ++i) lam[i] += xb_bar[(size_t)(r.k + 1) * nx + i];
     const double* u = nu ? ctrl + (size_t)r.k * nu : ctrl;
     step_jacobian(m, r.q.data(), r.v.data(), u, r.h, cfd, Jx, Ju, o.method);
+    if (p_bar) {
+      step_jacobian_params(m, r.q.data(), r.v.data(), u, r.h, cfd, Jp, o.method);
+      for (int k = 0; k < np; ++k) {
+        double acc = 0;
+        for (int i = 0; i < nx; ++i) acc += Jp[(size_t)i * np + k] * lam[i];
+        p_bar[k] += acc;
+      }
+    }
     if (ctrl_bar)
       for (int j = 0; j < nu; ++j) {
         double s = 0;

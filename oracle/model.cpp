@@ -10,6 +10,7 @@ namespace orc {
 thread_local std::int64_t g_flops = 0;
 thread_local int g_flops_paused = 0;
 thread_local int g_count_search = 1;
+thread_local int g_pdir = -1;
 
 static void normalize4(double* q) {
   double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);

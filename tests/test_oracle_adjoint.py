@@ -293,3 +293,104 @@ def test_other_schemes_gradient_frozen_steps(orc, method):
         fdx, fdu = _frozen_fd(m, x0, r["hlog"], w, ctrl=ctrl, T=0.2, NI=4, eps=eps, method=method)
         best.append(max(rel_err(g["x0_bar"][arm], fdx[arm]), rel_err(g["ctrl_bar"].ravel(), fdu.ravel())))
     assert min(best) < 1e-5
+
+
+# ------------------------------------------------------------------ model-parameter gradients (Sec. 5.1, App. E.2)
+PARAM_NAMES = ["t_c", "phi_d", "d_o", "d_w", "width", "midpoint"]
+
+
+def _perturbed_scene(make, k, delta):
+    """Scene from make() with model parameter k moved by delta (order:
+    t_c, phi_d, d_o, d_w, width, midpoint, then mu of each pair)."""
+    sc = make()
+    o = sc["options"]
+    if k < 2:
+        o["solref"][k] += delta
+    elif k < 6:
+        o["solimp"][k - 2] += delta
+    else:
+        sc["pairs"][k - 6]["mu"] += delta
+    return sc
+
+
+def _param_value(sc, k):
+    o = sc["options"]
+    return o["solref"][k] if k < 2 else o["solimp"][k - 2] if k < 6 else sc["pairs"][k - 6]["mu"]
+
+
+def _param_fd(orc, make, x0, hlog, w, T, k, rel=1e-6, ctrl=None, NI=1):
+    """Central difference of <w, xT> of the frozen-step map (the given step
+    sizes replayed) w.r.t. model parameter k."""
+    eps = rel * max(abs(_param_value(make(), k)), 1e-3)
+    vals = []
+    for sgn in (1.0, -1.0):
+        m = orc.OracleModel(_perturbed_scene(make, k, sgn * eps))
+        xT, _ = m.replay(x0, hlog, ctrl=ctrl, T=T, NI=NI)
+        vals.append(w @ xT)
+    return (vals[0] - vals[1]) / (2 * eps)
+
+
+@pytest.mark.parametrize("name", ["ball", "box"])
+def test_parameter_gradient_frozen_steps(orc, name):
+    """p_bar of the discrete adjoint (solref, solimp, friction) against central
+    differences of the frozen-step map over models with one parameter moved."""
+    make = W.SCENES[name]
+    m = orc.OracleModel(make())
+    if name == "ball":
+        x0, T = W.ball_inputs(3, seed=2)["x0"][2], 1.0
+    else:
+        x0, T = np.array([0, 0, 0.0497, 1, 0, 0, 0, 1.2, 0.4, 0, 0, 0, 0.0]), 0.15
+    r = m.rollout(x0, T=T)
+    w = np.random.default_rng(4).normal(size=13)
+    n = np.array([len(r["hlog"])], dtype=np.int32)
+    g = m.batch_replay_grad(x0[None], np.array([T]), r["hlog"][None], n, w[None], params=True)
+    pb = g["p_bar"][0]
+    assert len(pb) == m.nparams() == 7
+    for k in range(m.nparams()):
+        if name == "ball" and k == 6:
+            assert pb[k] == 0.0                      # frictionless: mu enters no row
+            continue
+        # stiff contact curves the frozen-step map: best of a small eps sweep
+        # (truncation vs round-off), as for the state gradients
+        errs = []
+        for rel in (1e-4, 1e-5, 1e-6, 1e-7):
+            fd = _param_fd(orc, make, x0, r["hlog"], w, T, k, rel=rel)
+            errs.append(abs(pb[k] - fd) / max(abs(fd), np.abs(pb).max() * 1e-2))
+        assert min(errs) < 2e-5, (k, pb[k], errs)
+
+
+def test_rest_height_parameter_gradient(orc):
+    """A ball settled on the plane sits at R + r_rest(theta), where r_rest is
+    the root of k d(r)^2 (-r) = g (1 - d(r)) (a = 0, J v = 0; k = 1/(d_w^2 t_c^2
+    phi_d^2), d the solimp spline): the adjoint's gradient of the final height
+    w.r.t. (t_c, phi_d, d_o, d_w, width, midpoint) equals d r_rest / d theta,
+    computed here from that scalar equation alone (brentq roots of perturbed
+    equations).  The adaptive steps at rest leave velocities of ~1e-9 m/s, so
+    the comparison holds to 1e-3 relative (a missing term or a sign is O(1))."""
+    from scipy.optimize import brentq
+    sc = W.ball_scene()
+    base = [*sc["options"]["solref"], *sc["options"]["solimp"][:4]]
+    pw = sc["options"]["solimp"][4]
+
+    def spline(x, mid):
+        return x ** pw / mid ** (pw - 1) if x <= mid else 1 - (1 - x) ** pw / (1 - mid) ** (pw - 1)
+
+    def r_rest(th):
+        tc, ph, do, dw, wd, mid = th
+        k = 1.0 / (dw ** 2 * tc ** 2 * ph ** 2)
+        d = lambda r: min(max(do + (dw - do) * spline(min(abs(r) / wd, 1.0), mid), 0.0), 0.9999)
+        return brentq(lambda r: k * d(r) ** 2 * (-r) - 9.81 * (1 - d(r)), -0.0009, -1e-6, xtol=1e-18, rtol=1e-15)
+
+    m = orc.OracleModel(sc)
+    x0 = np.array([0, 0, 0.3, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0])
+    T = 2.0
+    r = m.rollout(x0, T=T)
+    w = np.zeros(13); w[2] = 1.0
+    n = np.array([len(r["hlog"])], dtype=np.int32)
+    pb = m.batch_replay_grad(x0[None], np.array([T]), r["hlog"][None], n, w[None], params=True)["p_bar"][0]
+    for k in range(6):
+        eps = 1e-6 * max(abs(base[k]), 1e-3)
+        hi, lo = list(base), list(base)
+        hi[k] += eps; lo[k] -= eps
+        ref = (r_rest(hi) - r_rest(lo)) / (2 * eps)
+        assert abs(pb[k] - ref) <= 1e-3 * abs(ref), (PARAM_NAMES[k], pb[k], ref)
