@@ -154,6 +154,15 @@ def reduce_max(x, world, device=None):
     return float(t.item())
 
 
+def allreduce_sum_(t, world):
+    """In-place sum of a tensor over the ranks (the parameter-gradient
+    exchange of the system-identification step); identity for one rank."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
 def reduce_sum(x, world, device=None):
     if world == 1:
         return x
@@ -183,18 +192,18 @@ def _sources_sha(files):
     return h.hexdigest()
 
 
-def _adjoint_flops_per_env(lanes):
-    """FP64 flops per environment of the reverse adjoint of the arm workload
-    (T = 2 s, 50 intervals, K = 32) from the committed ncu counter record
-    (2 DFMA + DMUL + DADD thread operations), if it was taken on the current
-    kernel sources with the same lane count (else None)."""
+def _adjoint_flops_per_step(lanes):
+    """Executed FP64 flops per accepted env-step of the reverse adjoint of the
+    arm workload (T = 2 s, 50 intervals, K = 32) from the committed ncu counter
+    record (2 DFMA + DMUL + DADD thread operations), if it was taken on the
+    current kernel sources with the same lane count (else None)."""
     path = os.path.join(ROOT, "profiles", "adjoint_rev_chain_cube.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     if rec.get("source_sha256") != _sources_sha(ADJOINT_SOURCES) or rec.get("lanes") != lanes:
         return None
-    return rec["fp64_flops_per_launch"] / rec["envs"]
+    return rec["fp64_flops_per_launch"] / rec["env_steps"]
 
 
 def _forward_record(kernel_lanes):
@@ -325,6 +334,8 @@ def run_ours(args):
            "h2d_bytes_per_step": int(x0_h.numel() * 8 + T_h.numel() * 8),
            "d2h_bytes_per_step": int(xT_h.numel() * 8 + 4096 * 4 * 2)}
 
+    # every rank: the parameter-gradient step ends in an all-reduce over ranks
+    sysid = None if args.no_extras else sysid_leg(dmx, dev, world=world, rank=rank)
     result = None
     if rank == 0:
         peak, peak_shapes = dmx.fp64_peak()
@@ -363,6 +374,7 @@ def run_ours(args):
                 t = e0.elapsed_time(e1)
                 extra[form] = {"value": int(out["nsteps"].sum().item()) / (t * 1e-3), "ms_per_step": t}
             result["plain_forms"] = extra
+            result["sysid"] = sysid
             result["fwd_adjoint"] = grad_leg(dmx, dev, B=args.grad_envs, adj_lanes=args.adj_lanes,
                                              reps=args.grad_reps, peak=peak)
             result["serving"] = serving_leg(dmx, W, requests=args.requests, warmup=args.warmup_requests,
@@ -433,9 +445,9 @@ def grad_leg(dmx, dev, B=16384, adj_lanes=0, reps=3, peak=None, parity_envs=(0, 
                     "kernel": f"k_adjoint_rev<{adj_lanes}>", "flop_per_env_step": ARM_ADJ_FLOP_PER_STEP,
                     "work": "oracle count: every accepted step once in the counting derivative scalar "
                             "(recompute + linearised step), python -m oracle.count_flops chain_cube"}
-        fpe = _adjoint_flops_per_env(adj_lanes)
-        if fpe is not None:
-            ex = fpe * B / t_a / 1e12
+        fps = _adjoint_flops_per_step(adj_lanes)
+        if fps is not None:
+            ex = fps * steps / t_a / 1e12
             adj_roof["executed"] = {"achieved": ex, "frac": ex / peak,
                                     "source": "ncu FP64 thread operations, profiles/adjoint_rev_chain_cube.json"}
     parity = None
@@ -448,6 +460,62 @@ def grad_leg(dmx, dev, B=16384, adj_lanes=0, reps=3, peak=None, parity_envs=(0, 
             "forward_frac": (ARM_FLOP_PER_STEP * steps / t_f / 1e12 / peak) if peak else None,
             "lanes": {"forward": fwd_lanes, "adjoint": adj_lanes, "adjoint_tuning_ms": adj_ms},
             "finite": bool(torch.isfinite(gu).all().item()), "parity_vs_oracle": parity}
+
+
+def sysid_leg(dmx, dev, world=1, rank=0, B=4096, parity_envs=(0, 1)):
+    """System identification step (Sec. 5.1 / App. E.2) on seeded cube tosses:
+    observed final positions come from a rollout of a model with other contact
+    parameters (mu 0.6, t_c 4 ms instead of 1.0 and 5 ms); the loss is the
+    squared final-position error summed over the tosses, and one step is a
+    taped forward rollout plus the gradient w.r.t. the model parameters
+    (dmx_rollout_grad_params), summed over this GPU's tosses and, with N > 1,
+    over all ranks (all-reduce of np doubles: the one collective of the path).
+    The per-environment gradients of `parity_envs` are compared with the CPU
+    oracle's discrete adjoint along the GPU's step sizes."""
+    import torch
+    from paper_2506_14186_gb300 import workloads as W
+    sc = W.toss_scene()
+    true_sc = W.box_scene(solref=(0.004, 1.0), mu=0.6)
+    inp = W.toss_inputs(B, seed=1006 + rank)
+    m, mt = dmx.Model(sc), dmx.Model(true_sc)
+    x0 = torch.tensor(np.ascontiguousarray(inp["x0"].T), device=dev)
+    T = torch.tensor(inp["T"], device=dev)
+    obs = dmx.rollout(mt, x0, T)["xT"][0:3].clone()
+    st = torch.cuda.current_stream()
+
+    def step():
+        out = dmx.rollout(m, x0, T, K=16, tape=True)
+        xT_bar = torch.zeros_like(out["xT"])
+        xT_bar[0:3] = 2 * (out["xT"][0:3] - obs)
+        gx, _, pb, ps = dmx.rollout_grad_params(out["tape"], xT_bar)
+        allreduce_sum_(ps, world)
+        return out, xT_bar, gx, pb, ps
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    out, xT_bar, gx, pb, ps = step()
+    e1.record(st)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    parity = None
+    if rank == 0 and parity_envs:
+        import oracle
+        envs = list(parity_envs)
+        hlog, n = out["tape"].read()
+        idx = torch.tensor(envs, device=dev)
+        n = n[idx].cpu().numpy()
+        hl = hlog[: int(n.max()), idx].cpu().numpy().T
+        o = oracle.OracleModel(sc).batch_replay_grad(inp["x0"][envs], inp["T"][envs], hl, n,
+                                                     xT_bar.cpu().numpy().T[envs], params=True)
+        g = pb.cpu().numpy().T[envs]
+        scale = np.maximum(np.maximum(np.abs(o["p_bar"]), np.abs(o["p_bar"]).max(axis=1, keepdims=True)), 1e-300)
+        parity = {"envs": envs, "p_bar": float(np.max(np.abs(g - o["p_bar"]) / scale)), "bar": 1e-6}
+    return {"workload": "cube tosses, final-position loss against a model with mu 0.6 and t_c 4 ms",
+            "envs_per_gpu": B, "params": ["t_c", "phi_d", "d_o", "d_w", "width", "midpoint", "mu"],
+            "grad_rollouts_per_s": B * world / t, "s": t, "env_steps": int(out["nsteps"].sum().item()),
+            "p_bar_sum": ps.cpu().numpy().tolist(), "reduction": "in-library row sums, all-reduce over ranks",
+            "kernel": "k_adjoint (forward-mode, one direction per lane)", "parity_vs_oracle": parity}
 
 
 def _grad_parity(m, out, xT_bar, gx, gu, inp, scene, envs):

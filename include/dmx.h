@@ -179,6 +179,23 @@ dmx_status dmx_rollout(dmx_model* m, const dmx_rollout_args* a, void* stream);
  * pointers, ordered on `stream`.  The tape stays valid (may be reused). */
 dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* tape, int32_t cfd, const double* xT_bar,
                             const double* xb_bar, double* x0_bar, double* ctrl_bar, void* stream);
+/* Model parameters of the gradient below (the soft-contact parameters tuned
+ * by the system identification of Sec. 5.1 / App. E.2): np = 6 + npair,
+ * values (host, may be NULL) = t_c, phi_d (solref), d_o, d_w, width,
+ * midpoint (solimp), then the friction coefficient mu of every pair. */
+dmx_status dmx_model_params(const dmx_model* m, int32_t* np, double* values);
+/* dmx_rollout_grad plus the gradient of the same loss with respect to the
+ * model parameters (p of the problem statement in Sec. 2, differentiated
+ * through the discrete adjoint with the accepted step sizes held constant;
+ * A_hat stays the model constant fixed at creation).  p_bar [np][B] receives
+ * it per environment; p_bar_sum [np] (may be NULL) the sum over the
+ * environments (a fixed-order reduction: the batch's gradient when every
+ * environment shares the model).  Computed by the forward-mode adjoint kernel
+ * (one derivative direction per lane: the states, controls and parameters),
+ * whatever dmx_set_adjoint selects.  Device pointers, ordered on `stream`. */
+dmx_status dmx_rollout_grad_params(dmx_model* m, dmx_tape* tape, int32_t cfd, const double* xT_bar,
+                                   const double* xb_bar, double* x0_bar, double* ctrl_bar, double* p_bar,
+                                   double* p_bar_sum, void* stream);
 /* Kernel that dmx_rollout_grad runs for this model (both compute the same
  * derivative; results agree to rounding):
  *   DMX_ADJ_REVERSE (default): reverse mode, a group of lanes per environment

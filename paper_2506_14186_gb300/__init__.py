@@ -39,7 +39,7 @@ _ACT = {"motor": 0, "position": 1}
 ABI_SYMBOLS = ("dmx_create_model", "dmx_destroy_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad",
                "dmx_tape_free", "dmx_tape_read", "dmx_autotune", "dmx_set_lanes", "dmx_model_info", "dmx_server_create", "dmx_submit", "dmx_poll",
                "dmx_server_destroy", "dmx_eval_rhs", "dmx_rollout_static", "dmx_set_adjoint", "dmx_eval_rhs_vjp",
-               "dmx_fp64_peak", "dmx_last_error")
+               "dmx_fp64_peak", "dmx_model_params", "dmx_rollout_grad_params", "dmx_last_error")
 
 
 class BodyDesc(ctypes.Structure):
@@ -104,7 +104,7 @@ def lib():
         for name in ("dmx_create_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad", "dmx_autotune",
                      "dmx_server_create", "dmx_submit", "dmx_poll", "dmx_server_destroy", "dmx_model_info",
                      "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read", "dmx_rollout_static", "dmx_set_adjoint",
-                     "dmx_eval_rhs_vjp", "dmx_fp64_peak"):
+                     "dmx_eval_rhs_vjp", "dmx_fp64_peak", "dmx_model_params", "dmx_rollout_grad_params"):
             getattr(L, name).restype = c_i32
         L.dmx_destroy_model.restype = None
         L.dmx_tape_free.restype = None
@@ -191,6 +191,15 @@ class Model:
     def set_lanes(self, B, lanes, grad=False):
         """grad: False / 0 forward rollout, True / 1 taped rollout, 2 reverse-mode adjoint kernel."""
         _check(lib().dmx_set_lanes(self.h, int(B), int(grad), int(lanes)))
+
+    def params(self):
+        """Model parameters of rollout_grad_params: numpy array of t_c, phi_d,
+        d_o, d_w, width, midpoint, then mu of every pair."""
+        n = c_i32()
+        _check(lib().dmx_model_params(self.h, ctypes.byref(n), None))
+        vals = (c_f64 * n.value)()
+        _check(lib().dmx_model_params(self.h, ctypes.byref(n), vals))
+        return np.array(list(vals))
 
     def set_adjoint(self, mode):
         """Adjoint kernel of rollout_grad: "reverse" (default; stage snapshots in
@@ -295,6 +304,25 @@ def rollout_grad(tape, xT_bar, xb_bar=None, cfd=False, stream=None):
     _check(lib().dmx_rollout_grad(m.h, tape.h, int(cfd), _ptr(xT_bar), _ptr(xb_bar), _ptr(x0_bar), _ptr(ctrl_bar),
                                   _stream_handle(stream)))
     return x0_bar, ctrl_bar
+
+
+def rollout_grad_params(tape, xT_bar, xb_bar=None, cfd=False, stream=None):
+    """Discrete adjoint with model-parameter gradients: returns (x0_bar [nx, B],
+    ctrl_bar [NI, nu, B] or None, p_bar [np, B], p_bar_sum [np])."""
+    import torch
+    m = tape.model
+    _require_cuda(xT_bar, "xT_bar", torch.float64)
+    if xb_bar is not None:
+        _require_cuda(xb_bar, "xb_bar", torch.float64)
+    npar = len(m.params())
+    dev = xT_bar.device
+    x0_bar = torch.empty((m.nx, tape.B), dtype=torch.float64, device=dev)
+    ctrl_bar = torch.empty((tape.NI, m.nu, tape.B), dtype=torch.float64, device=dev) if m.nu else None
+    p_bar = torch.empty((npar, tape.B), dtype=torch.float64, device=dev)
+    p_sum = torch.empty(npar, dtype=torch.float64, device=dev)
+    _check(lib().dmx_rollout_grad_params(m.h, tape.h, int(cfd), _ptr(xT_bar), _ptr(xb_bar), _ptr(x0_bar),
+                                         _ptr(ctrl_bar), _ptr(p_bar), _ptr(p_sum), _stream_handle(stream)))
+    return x0_bar, ctrl_bar, p_bar, p_sum
 
 
 def eval_rhs_vjp(model, q, v, abar, u=None, cfd=False, lanes=0, stream=None):

@@ -102,12 +102,12 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_adjoint(AdjParams P) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gwarp = blockIdx.x * ADJ_WARPS + wib;
   const unsigned full = 0xffffffffu;
-  const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu, D = nx + nu;
+  const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu, D = nx + nu + (P.p_bar ? P.np : 0);
   const int npass = (D + 31) / 32;
   Grp<1> g;                                     // every lane is a group of one
   Dual wsd[ADJ_WS];
   int wsi[ADJ_WI];
-  const WsT<Dual> wd{wsd, wsi, &sL};
+  WsT<Dual> wd{wsd, wsi, &sL};
   const WsT<double> wp{reinterpret_cast<double*>(wsd), wsi, &sL};
   double* xbar = s_xbar[wib];
   double* seg = P.segbuf + (size_t)gwarp * P.K * (nx + 1);
@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_adjoint(AdjParams P) {
     if (P.ctrl_bar)
       for (int i = lane; i < P.NI * nu; i += 32) P.ctrl_bar[(size_t)i * P.B + env] = 0.0;
     for (int k = 0; k < MASKW; ++k) { maskF[k] = 0; maskC[k] = 0; }
+    double pacc[4] = {0.0, 0.0, 0.0, 0.0};       // this lane's parameter directions
     __syncwarp();
     for (int c = N > 0 ? (N - 1) / P.K : -1; c >= 0; --c) {
       const int n0 = c * P.K, n1 = min(n0 + P.K, N);
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_adjoint(AdjParams P) {
         double gdir[4];
         for (int p = 0; p < npass; ++p) {
           const int d = p * 32 + lane;
+          wd.pdir = (d >= nx + nu && d < D) ? d - nx - nu : -1;   // a model-parameter direction
           Dual* qd = wd.at(sL.qn); Dual* vd = wd.at(sL.vn); Dual* ud = wd.at(sL.u);
           for (int i = 0; i < nq; ++i) qd[i] = Dual(row[i], d == i ? 1.0 : 0.0);
           for (int i = 0; i < nv; ++i) vd[i] = Dual(row[nq + i], d == nq + i ? 1.0 : 0.0);
@@ -192,10 +194,15 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_adjoint(AdjParams P) {
         for (int p = 0; p < npass; ++p) {
           const int d = p * 32 + lane;
           if (d < nx) xbar[d] = gdir[p];
-          else if (d < D && P.ctrl_bar) P.ctrl_bar[((size_t)kn * nu + (d - nx)) * P.B + env] += gdir[p];
+          else if (d < nx + nu) { if (P.ctrl_bar) P.ctrl_bar[((size_t)kn * nu + (d - nx)) * P.B + env] += gdir[p]; }
+          else if (d < D) pacc[p] += gdir[p];
         }
         __syncwarp();
       }
+    }
+    for (int p = 0; p < npass; ++p) {
+      const int d = p * 32 + lane;
+      if (d >= nx + nu && d < D) P.p_bar[(size_t)(d - nx - nu) * P.B + env] = pacc[p];
     }
     if (P.xb_bar)
       for (int i = lane; i < nx; i += 32) xbar[i] += P.xb_bar[(size_t)i * P.B + env];
@@ -208,6 +215,28 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_adjoint(AdjParams P) {
 
 cudaError_t launch_adjoint(const AdjParams& P, int blocks, cudaStream_t st) {
   k_adjoint<<<blocks, 32 * ADJ_WARPS, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+// Sum of every row of x [n][B]: block k strides over row k, then a fixed
+// shuffle tree and a fixed shared-memory sum (the same order every call).
+__global__ void __launch_bounds__(256) k_row_sums(const double* x, int B, double* out) {
+  __shared__ double part[8];
+  const double* row = x + (size_t)blockIdx.x * B;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < B; e += blockDim.x) acc += row[e];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+    out[blockIdx.x] = s;
+  }
+}
+cudaError_t launch_row_sums(const double* x, int n, int B, double* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_row_sums<<<n, 256, 0, st>>>(x, B, out);
   return cudaGetLastError();
 }
 int adjoint_warps_per_block() { return ADJ_WARPS; }

@@ -24,6 +24,9 @@ struct AdjParams {
   double* segbuf;         // per warp (tangent) or group (reverse): recomputed steps of a segment
   double* snapbuf;        // reverse mode: per group, K steps x (S - 1) stage snapshots of SN doubles (or null)
   int SN;                 // doubles per snapshot
+  int per, barofs;        // reverse mode: doubles per environment, offset of the cotangent workspace
+  double* p_bar;          // tangent mode: [np][B] model-parameter gradients, or null
+  int np;                 // model parameters differentiated when p_bar is set
   int* queue;             // next environment
 };
 
@@ -55,6 +58,8 @@ __host__ __device__ inline SnapOff snap_offsets(const DevModel& m, const Layout&
 __host__ __device__ inline int rev_row_doubles(const DevModel& m) { return m.nq + 7 * m.nv + 1; }
 
 cudaError_t launch_adjoint(const AdjParams& P, int blocks, cudaStream_t st);
+// out[k] = sum over e of x[k][e] (k < n, e < B): one block per row, fixed order.
+cudaError_t launch_row_sums(const double* x, int n, int B, double* out, cudaStream_t st);
 // reverse-mode kernel, G lanes per environment (G = 2, 4, 8, 16, 32)
 cudaError_t launch_adjoint_rev(int G, const AdjParams& P, int blocks, int threads, size_t smem, cudaStream_t st);
 int adjoint_rev_occupancy(int G, int threads, size_t smem);

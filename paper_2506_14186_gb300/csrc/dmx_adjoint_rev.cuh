@@ -60,7 +60,9 @@ __device__ void snap_save(const Grp<G>& g, const DevModel& m, const Ws& w, doubl
   for (int i = g.lane; i < nr; i += G) di[3 + m.nslot + i] = w.i[L.rowid + i];
   for (int i = g.lane; i < MASKW; i += G) di[3 + m.nslot + L.rcap + i] = w.i[L.amask + i];
 }
-// Snapshot src -> workspace (the state rhs() leaves for rhs_vjp); returns the status.
+// Snapshot src -> workspace (the state rhs() leaves for rhs_vjp, except the
+// contact records and Jacobian rows, which the VJP reads from the snapshot
+// itself: see snap_view); returns the status.
 template <int G>
 __device__ int snap_restore(const Grp<G>& g, const DevModel& m, const Ws& w, const double* src) {
   const Layout& L = *w.L;
@@ -70,15 +72,21 @@ __device__ int snap_restore(const Grp<G>& g, const DevModel& m, const Ws& w, con
   double* d = w.d;
   for (int i = g.lane; i < o.n1; i += G) d[L.R + i] = src[i];
   for (int i = g.lane; i < o.n2; i += G) d[L.H + i] = src[o.o2 + i];
-  for (int i = g.lane; i < 16 * m.nslot; i += G) d[L.ct + i] = src[o.o3 + i];
   for (int i = g.lane; i < m.nslot; i += G) d[L.csv + i] = src[o.o3 + 16 * m.nslot + i];
-  for (int i = g.lane; i < nr * m.nv; i += G) d[L.J + i] = src[o.o4 + i];
   for (int i = g.lane; i < nr; i += G) { d[L.Dr + i] = src[o.o5 + i]; d[L.z + i] = src[o.o6 + i]; }
   for (int i = g.lane; i <= m.nslot; i += G) w.i[L.slotrow + i] = si[2 + i];
   for (int i = g.lane; i < nr; i += G) w.i[L.rowid + i] = si[3 + m.nslot + i];
   for (int i = g.lane; i < MASKW; i += G) w.i[L.amask + i] = si[3 + m.nslot + L.rcap + i];
   g.sync();
   return st;
+}
+// The workspace view whose VJP reads the snapshot's contact records and rows.
+__device__ __forceinline__ Ws snap_view(const DevModel& m, const Ws& w, const double* src) {
+  const SnapOff o = snap_offsets(m, *w.L);
+  Ws v = w;
+  v.xct = src + o.o3;
+  v.xJ = src + o.o4;
+  return v;
 }
 
 // (qnb, vnb, ub) = transposed step map of scheme mt applied to (Qb, Vb) = the
@@ -120,10 +128,10 @@ __device__ int rk_step_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, cons
     }
     if (s <= S - 2) {
       const double* Vs = vst + s * nv;
-      const int r = snaps ? snap_restore(g, m, w, snaps + (size_t)s * SN)
-                          : rhs(g, m, w, (const double*)Qs, Vs, u, cfd, w.at(L.ka));
+      const double* sn = snaps ? snaps + (size_t)s * SN : nullptr;
+      const int r = sn ? snap_restore(g, m, w, sn) : rhs(g, m, w, (const double*)Qs, Vs, u, cfd, w.at(L.ka));
       if (r > st) st = r;
-      rhs_vjp(g, m, w, b, Qs, Vs, u, cfd, r, kab + s * nv, Qb, Vb, ub);
+      rhs_vjp(g, m, sn ? snap_view(m, w, sn) : w, b, Qs, Vs, u, cfd, r, kab + s * nv, Qb, Vb, ub);
       for (int i = g.lane; i < nv; i += G) Vb[i] += kvb[s * nv + i];   // V_s in the later stages' positions
       g.sync();
     }
@@ -160,9 +168,11 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_rev(AdjParams P) {
   const DevModel& m = *P.model;
   Grp<G> g;
   const int ngb = blockDim.x / G, gib = threadIdx.x / G;
-  const int per = sL.nd + sB.nd;
+  // doubles per environment and the cotangent workspace's offset in them (with
+  // stage snapshots it overlays the arrays only the segment recompute uses)
+  const int per = P.per;
   const Ws w{smem + (size_t)gib * per, reinterpret_cast<int*>(smem + (size_t)ngb * per) + (size_t)gib * sL.ni, &sL};
-  const WsB b{smem + (size_t)gib * per + sL.nd, &sB};
+  const WsB b{smem + (size_t)gib * per + P.barofs, &sB};
   const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
   const int RW = rev_row_doubles(m);
   const int mt = P.method, S = TAB(mt).S;
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_rev(AdjParams P) {
   const int SN = P.SN;
   double* snb = use_snap ? P.snapbuf + (size_t)(blockIdx.x * ngb + gib) * P.K * (S - 1) * SN : nullptr;
   double* qn = w.at(sL.qn); double* vn = w.at(sL.vn); double* u = w.at(sL.u); double* ka = w.at(sL.ka);
-  double* xbar = b.at(sB.xb);
+  double* xbar = sL.xbar >= 0 ? w.at(sL.xbar) : b.at(sB.xb);   // kept across the recompute phases
   for (;;) {
     int env = 0;
     if (g.lane == 0) env = atomicAdd(P.queue, 1);

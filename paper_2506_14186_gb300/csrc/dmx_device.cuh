@@ -201,7 +201,44 @@ struct WsT {
   T* d;
   int* i;
   const Layout* L;
+  // the right-hand-side VJP reads the contact records / Jacobian rows here
+  // when set (a stage snapshot in device memory), else from the workspace
+  const double* xct = nullptr;
+  const double* xJ = nullptr;
+  // derivative scalars: the model parameter (PAR_*) whose tangent this
+  // evaluation carries, -1 for none
+  int pdir = -1;
   __device__ T* at(int off) const { return d + off; }
+};
+
+// Value v of model parameter k; a derivative scalar carries a unit tangent
+// when k is the direction pdir being differentiated.
+template <class T>
+struct Par {
+  static __device__ __forceinline__ double get(int, int, double v) { return v; }
+  static __device__ __forceinline__ double bcoef(const DevModel& m, int) { return m.bcoef; }
+  static __device__ __forceinline__ double kcoef(const DevModel& m, int) { return m.kcoef; }
+  static __device__ __forceinline__ double ahat_edge(const DevModel& m, int, int p) { return m.p_ahat_edge[p]; }
+};
+template <>
+struct Par<Dual> {
+  static __device__ __forceinline__ Dual get(int pdir, int k, double v) { return Dual(v, pdir == k ? 1.0 : 0.0); }
+  // bcoef = 2 / (d_w t_c), kcoef = 1 / (d_w^2 t_c^2 phi_d^2): values as
+  // compiled, tangents by their logarithmic derivatives
+  static __device__ __forceinline__ Dual bcoef(const DevModel& m, int pdir) {
+    const double b = m.bcoef;
+    return Dual(b, pdir == PAR_TC ? -b / m.solref[0] : pdir == PAR_DW ? -b / m.solimp[1] : 0.0);
+  }
+  static __device__ __forceinline__ Dual kcoef(const DevModel& m, int pdir) {
+    const double k = m.kcoef;
+    return Dual(k, pdir == PAR_TC ? -2.0 * k / m.solref[0]
+                 : pdir == PAR_DAMP ? -2.0 * k / m.solref[1]
+                 : pdir == PAR_DW ? -2.0 * k / m.solimp[1] : 0.0);
+  }
+  // A_hat (1 + mu^2) of a pyramid-edge row
+  static __device__ __forceinline__ Dual ahat_edge(const DevModel& m, int pdir, int p) {
+    return Dual(m.p_ahat_edge[p], pdir == PAR_MU0 + p ? 2.0 * m.p_mu[p] * m.p_ahat[p] : 0.0);
+  }
 };
 using Ws = WsT<double>;
 
@@ -626,17 +663,30 @@ __device__ __forceinline__ T spline_shape(const T& x, double mid, double pw) {
   const T num = (pw == 2.0) ? y * y : (pw == 4.0 ? (y * y) * (y * y) : pow(y, pw));
   return 1.0 - num / ((pw == 2.0) ? (1.0 - mid) : ::pow(1.0 - mid, pw - 1.0));
 }
+// The same shape with a derivative-scalar midpoint (parameter tangents).
+__device__ __forceinline__ Dual spline_shape(const Dual& x, const Dual& mid, double pw) {
+  if (value(x) <= value(mid) && value(mid) > 0) {
+    const Dual num = (pw == 2.0) ? x * x : (pw == 4.0 ? (x * x) * (x * x) : pow(x, pw));
+    return num / ((pw == 2.0) ? mid : pow(mid, pw - 1.0));
+  }
+  const Dual y = 1.0 - x;
+  const Dual num = (pw == 2.0) ? y * y : (pw == 4.0 ? (y * y) * (y * y) : pow(y, pw));
+  const Dual om = 1.0 - mid;
+  return 1.0 - num / ((pw == 2.0) ? om : pow(om, pw - 1.0));
+}
 template <class T>
-__device__ __forceinline__ T impedance(const DevModel& m, const T& r, bool cfd) {
+__device__ __forceinline__ T impedance(const DevModel& m, const T& r, bool cfd, int pdir = -1) {
   T d;
   if (cfd && value(r) >= 0) {
     T x = 1.0 - r / m.cfd[2];
     if (value(x) < 0) x = 0.0;
     d = m.cfd[0] + (m.cfd[1] - m.cfd[0]) * spline_shape(x, m.cfd[3], m.cfd[4]);
   } else {
-    T x = fabs(r) / m.solimp[2];
+    const auto d_o = Par<T>::get(pdir, PAR_DO, m.solimp[0]), d_w = Par<T>::get(pdir, PAR_DW, m.solimp[1]);
+    const auto width = Par<T>::get(pdir, PAR_WIDTH, m.solimp[2]), mid = Par<T>::get(pdir, PAR_MID, m.solimp[3]);
+    T x = fabs(r) / width;
     if (value(x) > 1.0) x = 1.0;
-    d = m.solimp[0] + (m.solimp[1] - m.solimp[0]) * spline_shape(x, m.solimp[3], m.solimp[4]);
+    d = d_o + (d_w - d_o) * spline_shape(x, mid, m.solimp[4]);
   }
   if (value(d) < 0.0) return T(0.0);
   if (value(d) > 0.9999) return T(0.9999);
@@ -685,11 +735,12 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, boo
     w.i[L.sinc + s] = inc ? 1 : 0;
     if (inc) {
       const T r = ct[0];
-      const T d = impedance(m, r, cfd);
+      const T d = impedance(m, r, cfd, w.pdir);
       const int pr = m.s_pair[s];
-      const double ahat = m.p_condim[pr] == 1 ? m.p_ahat[pr] : m.p_ahat_edge[pr];
+      const auto ahat = m.p_condim[pr] == 1 ? Par<T>::get(-1, 0, m.p_ahat[pr]) : Par<T>::ahat_edge(m, w.pdir, pr);
+      const auto kc = Par<T>::kcoef(m, w.pdir);
       ct[13] = d;
-      ct[14] = cfd ? m.kcoef * d * (m.softplus * softplus(-r / m.softplus)) : -(m.kcoef * d * r);
+      ct[14] = cfd ? kc * d * (m.softplus * softplus(-r / m.softplus)) : -(kc * d * r);
       ct[15] = d / (ahat * (1.0 - d));
     }
   }
@@ -753,7 +804,7 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const WsT<T>& w, co
     if (m.p_condim[p] == 1) {
       J[r0 * nv + i] = jn;
     } else {
-      const double mu = m.p_mu[p];
+      const auto mu = Par<T>::get(w.pdir, PAR_MU0 + p, m.p_mu[p]);
       J[r0 * nv + i] = jn + mu * j1;
       J[(r0 + 1) * nv + i] = jn - mu * j1;
       J[(r0 + 2) * nv + i] = jn + mu * j2;
@@ -770,7 +821,7 @@ __device__ int make_rows(const Grp<G>& g, const DevModel& m, const WsT<T>& w, co
     const T* ct = CT + 16 * s;
     T jv = 0.0;
     for (int i = 0; i < nv; ++i) jv += J[r * nv + i] * v[i];
-    aref[r] = -(m.bcoef * jv) + ct[14];
+    aref[r] = -(Par<T>::bcoef(m, w.pdir) * jv) + ct[14];
     Dr[r] = ct[15];
     rowid[r] = m.p_row0[p] + m.s_idx[s] * nrow + e;
   }

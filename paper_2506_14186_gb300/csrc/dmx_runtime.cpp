@@ -144,7 +144,11 @@ static std::string compile_model(const dmx_model_desc* d, DevModel& m) {
     m.p_g1[p] = P.geom1; m.p_g2[p] = P.geom2; m.p_condim[p] = P.condim; m.p_mu[p] = P.mu;
     m.p_slot0[p] = m.nslot; m.p_nslot[p] = ns; m.p_row0[p] = row;
     if (m.nslot + ns > MAXS) return "too many contact slots";
-    for (int j = 0; j < ns; ++j) { m.s_pair[m.nslot + j] = p; m.s_idx[m.nslot + j] = j; }
+    for (int j = 0; j < ns; ++j) {
+      m.s_pair[m.nslot + j] = p; m.s_idx[m.nslot + j] = j;
+      m.s_barofs[m.nslot + j] = m.nslotbar;
+      m.nslotbar += P.geom2 >= 0 ? 24 : 12;     // a plane slot moves one geom
+    }
     m.nslot += ns;
     row += ns * (P.condim == 1 ? 1 : 4);
   }
@@ -164,6 +168,7 @@ static std::string compile_model(const dmx_model_desc* d, DevModel& m) {
   if (!(d->solimp_cfd[2] > 0) || !(d->softplus > 0)) return "solimp-CFD width and softplus width must be positive";
   m.bcoef = 2.0 / (dw * tc);
   m.kcoef = 1.0 / (dw * dw * tc * tc * damp * damp);
+  m.solref[0] = tc; m.solref[1] = damp;
   for (int i = 0; i < 5; ++i) { m.solimp[i] = d->solimp[i]; m.cfd[i] = d->solimp_cfd[i]; }
   m.softplus = d->softplus;
   return "";
@@ -552,6 +557,68 @@ extern "C" dmx_status dmx_set_adjoint(dmx_model* m, int32_t mode) {
   return DMX_OK;
 }
 
+// The forward-mode adjoint kernel (one derivative direction per lane; model
+// parameters too when P.p_bar is set).
+static dmx_status run_tangent_adjoint(dmx_model* m, dmx_tape* t, dmx::AdjParams& P, cudaStream_t st) {
+  const dmx::Layout& L = P.L;
+  const int nx = t->nx;
+  if (L.nd > dmx::adjoint_workspace_limit() || L.ni > dmx::adjoint_int_limit())
+    return dmx_fail(DMX_ERR_INVALID, "model workspace exceeds the tangent adjoint kernel's per-lane limit");
+  const int wpb = dmx::adjoint_warps_per_block();
+  int blocks = (t->B + wpb - 1) / wpb;
+  blocks = std::min(blocks, m->nsm * 8);
+  const size_t seg_bytes = sizeof(double) * (size_t)blocks * wpb * t->K * (nx + 1);
+  void* scratch = nullptr;
+  CK(cudaMallocAsync(&scratch, seg_bytes + 256, st));
+  P.segbuf = static_cast<double*>(scratch);
+  P.queue = reinterpret_cast<int*>(static_cast<char*>(scratch) + seg_bytes);
+  CK(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
+  CK(dmx::launch_adjoint(P, blocks, st));
+  CK(cudaFreeAsync(scratch, st));
+  return DMX_OK;
+}
+
+static int model_nparams(const dmx_model* m) { return dmx::PAR_MU0 + m->host.npair; }
+
+extern "C" dmx_status dmx_model_params(const dmx_model* m, int32_t* np, double* values) {
+  if (!m) return dmx_fail(DMX_ERR_INVALID, "null model");
+  const int n = model_nparams(m);
+  if (np) *np = n;
+  if (values) {
+    const dmx::DevModel& d = m->host;
+    values[dmx::PAR_TC] = d.solref[0]; values[dmx::PAR_DAMP] = d.solref[1];
+    values[dmx::PAR_DO] = d.solimp[0]; values[dmx::PAR_DW] = d.solimp[1];
+    values[dmx::PAR_WIDTH] = d.solimp[2]; values[dmx::PAR_MID] = d.solimp[3];
+    for (int p = 0; p < d.npair; ++p) values[dmx::PAR_MU0 + p] = d.p_mu[p];
+  }
+  return DMX_OK;
+}
+
+extern "C" dmx_status dmx_rollout_grad_params(dmx_model* m, dmx_tape* t, int32_t cfd, const double* xT_bar,
+                                              const double* xb_bar, double* x0_bar, double* ctrl_bar, double* p_bar,
+                                              double* p_bar_sum, void* stream) {
+  if (!m || !t) return dmx_fail(DMX_ERR_INVALID, "null model or tape");
+  if (t->model != m) return dmx_fail(DMX_ERR_INVALID, "tape belongs to another model");
+  if (!p_bar) return dmx_fail(DMX_ERR_INVALID, "p_bar is required");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int np = model_nparams(m);
+  if (t->B == 0) {
+    if (p_bar_sum) CK(cudaMemsetAsync(p_bar_sum, 0, sizeof(double) * np, st));
+    return DMX_OK;
+  }
+  if (!xT_bar || !x0_bar) return dmx_fail(DMX_ERR_INVALID, "xT_bar and x0_bar are required");
+  if (m->host.nu > 0 && !ctrl_bar) return dmx_fail(DMX_ERR_INVALID, "ctrl_bar is required when the model has actuators");
+  dmx::AdjParams P{};
+  P.model = m->dev; P.L = layout_for(m, cfd); P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd; P.method = t->method;
+  P.ckpt = t->ckpt; P.hlog = t->hlog; P.tape_n = t->n; P.ctrl = t->ctrl; P.T = t->T;
+  P.xT_bar = xT_bar; P.xb_bar = xb_bar; P.x0_bar = x0_bar; P.ctrl_bar = m->host.nu ? ctrl_bar : nullptr;
+  P.p_bar = p_bar; P.np = np;
+  const dmx_status s = run_tangent_adjoint(m, t, P, st);
+  if (s != DMX_OK) return s;
+  if (p_bar_sum) CK(dmx::launch_row_sums(p_bar, np, t->B, p_bar_sum, st));
+  return DMX_OK;
+}
+
 extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, const double* xT_bar,
                                        const double* xb_bar, double* x0_bar, double* ctrl_bar, void* stream) {
   if (!m || !t) return dmx_fail(DMX_ERR_INVALID, "null model or tape");
@@ -571,43 +638,52 @@ extern "C" dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* t, int32_t cfd, c
   P.model = m->dev; P.L = L; P.B = t->B; P.NI = t->NI; P.K = t->K; P.cfd = cfd; P.method = t->method;
   P.ckpt = t->ckpt; P.hlog = t->hlog; P.tape_n = t->n; P.ctrl = t->ctrl; P.T = t->T;
   P.xT_bar = xT_bar; P.xb_bar = xb_bar; P.x0_bar = x0_bar; P.ctrl_bar = m->host.nu ? ctrl_bar : nullptr;
-  if (mode == DMX_ADJ_TANGENT) {
-    if (L.nd > dmx::adjoint_workspace_limit() || L.ni > dmx::adjoint_int_limit())
-      return dmx_fail(DMX_ERR_INVALID, "model workspace exceeds the tangent adjoint kernel's per-lane limit");
-    const int wpb = dmx::adjoint_warps_per_block();
-    int blocks = (t->B + wpb - 1) / wpb;
-    blocks = std::min(blocks, m->nsm * 8);
-    const size_t seg_bytes = sizeof(double) * (size_t)blocks * wpb * t->K * (nx + 1);
-    void* scratch = nullptr;
-    CK(cudaMallocAsync(&scratch, seg_bytes + 256, st));
-    P.segbuf = static_cast<double*>(scratch);
-    P.queue = reinterpret_cast<int*>(static_cast<char*>(scratch) + seg_bytes);
-    CK(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
-    CK(dmx::launch_adjoint(P, blocks, st));
-    CK(cudaFreeAsync(scratch, st));
-    return DMX_OK;
-  }
+  if (mode == DMX_ADJ_TANGENT) return run_tangent_adjoint(m, t, P, st);
   const int G = adjoint_lanes(m, t->B, L);
   P.LB = dmx::make_bar_layout(m->host, L.rcap);
-  int threads; size_t smem;
-  if (!adj_launch_config(m, L, P.LB, G, &threads, &smem))
-    return dmx_fail(DMX_ERR_INVALID, "adjoint workspace of " + std::to_string(G) + " lanes/env does not fit shared memory");
-  const int gpb = threads / G;
-  const int occ = std::max(1, dmx::adjoint_rev_occupancy(G, threads, smem));
-  int blocks = (t->B + gpb - 1) / gpb;
-  blocks = std::min(blocks, m->nsm * occ);
+  const int gpb = 32 / G, threads = 32;
   const int RW = dmx::rev_row_doubles(m->host);
-  const size_t seg_bytes = sizeof(double) * (size_t)blocks * gpb * t->K * RW;
-  // stage snapshots (forward right-hand side only): used when they fit a
-  // share of the free device memory, else each stage is evaluated again
+  const int nsnap = t->method == DMX_METHOD_EULER ? 1 : 6;   // stage right-hand sides per step
+  // Launch plan for a workspace layout: doubles per environment, the cotangent
+  // workspace's offset, shared memory, resident blocks and segment buffer.
+  struct Plan {
+    dmx::Layout L;
+    int per = 0, barofs = 0, blocks = 0;
+    size_t smem = 0, seg = 0;
+  };
+  auto plan = [&](const dmx::Layout& Lx, bool overlay, Plan& out) {
+    out.L = Lx;
+    out.per = overlay ? std::max(Lx.nd, Lx.ovl + P.LB.nd) : Lx.nd + P.LB.nd;
+    out.per = (out.per + 1) & ~1;
+    out.barofs = overlay ? Lx.ovl : Lx.nd;
+    out.smem = (size_t)gpb * ((size_t)out.per * 8 + (size_t)Lx.ni * 4);
+    if ((int)out.smem > m->smem_max - 2048) return false;
+    const int occ = std::max(1, dmx::adjoint_rev_occupancy(G, threads, out.smem));
+    out.blocks = std::min((t->B + gpb - 1) / gpb, m->nsm * occ);
+    out.seg = sizeof(double) * (size_t)out.blocks * gpb * t->K * RW;
+    return true;
+  };
+  // With stage snapshots (forward right-hand side only, when they fit a share
+  // of the free device memory) the reverse sweep never evaluates a right-hand
+  // side, so the cotangent workspace overlays the arrays only the segment
+  // recompute uses (dmx::make_layout_adj): fewer bytes per environment, more
+  // resident warps.  Otherwise every stage is evaluated again in the sweep.
+  Plan pl;
   size_t snap_bytes = 0;
-  if (mode == DMX_ADJ_REVERSE && !cfd) {
-    P.SN = dmx::snap_offsets(m->host, L).size;
-    snap_bytes = sizeof(double) * (size_t)blocks * gpb * t->K * 6 * (size_t)P.SN;
+  if (mode == DMX_ADJ_REVERSE && !cfd && plan(dmx::make_layout_adj(m->host, L.rcap), true, pl)) {
+    P.SN = dmx::snap_offsets(m->host, pl.L).size;
+    snap_bytes = sizeof(double) * (size_t)pl.blocks * gpb * t->K * nsnap * (size_t)P.SN;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || snap_bytes > free_b / 8 || snap_bytes > kSnapMaxBytes)
       snap_bytes = 0;
   }
+  if (snap_bytes == 0 && !plan(L, false, pl))
+    return dmx_fail(DMX_ERR_INVALID, "adjoint workspace of " + std::to_string(G) + " lanes/env does not fit shared memory");
+  P.L = pl.L;
+  P.per = pl.per;
+  P.barofs = pl.barofs;
+  const int blocks = pl.blocks;
+  const size_t smem = pl.smem, seg_bytes = pl.seg;
   void* scratch = nullptr;
   CK(cudaMallocAsync(&scratch, seg_bytes + snap_bytes + 256, st));
   P.segbuf = static_cast<double*>(scratch);

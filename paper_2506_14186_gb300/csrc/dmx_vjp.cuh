@@ -325,7 +325,7 @@ __device__ __forceinline__ bool slot_jbar(const DevModel& m, const Ws& w, const 
   const bool mA = (m.b_anc[bA] >> bi) & 1u;
   const bool mB = bB >= 0 && ((m.b_anc[bB] >> bi) & 1u);
   if (mA == mB) return false;
-  const double* ct = w.at(L.ct) + 16 * s;
+  const double* ct = (w.xct ? w.xct : w.at(L.ct)) + 16 * s;
   const double* sv = w.at(L.sd) + 6 * i;
   cross3(sv, ct + 1, pv);
   pv[0] += sv[3]; pv[1] += sv[4]; pv[2] += sv[5];
@@ -364,8 +364,8 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
   const double* S = w.at(L.sd); const double* Ib = w.at(L.Ib); const double* Ic = w.at(L.Ic);
   const double* F = w.at(L.F); const double* V = w.at(L.Vb); const double* A = w.at(L.Ab);
   const double* Fb = w.at(L.Fb); const double* gR = w.at(L.gR); const double* gp = w.at(L.gp);
-  const double* an = w.at(L.an); const double* J = w.at(L.J); const double* Dr = w.at(L.Dr);
-  const double* z = w.at(L.z); const double* CT = w.at(L.ct);
+  const double* an = w.at(L.an); const double* J = w.xJ ? w.xJ : w.at(L.J); const double* Dr = w.at(L.Dr);
+  const double* z = w.at(L.z); const double* CT = w.xct ? w.xct : w.at(L.ct);
   double* Rb = b.at(LB.R); double* pb = b.at(LB.p); double* cR = b.at(LB.cR); double* cp = b.at(LB.cp);
   double* Sb = b.at(LB.S); double* Fd = b.at(LB.F); double* Ibb = b.at(LB.Ib); double* Icb = b.at(LB.Ic);
   double* Vbb = b.at(LB.V); double* Abb = b.at(LB.A); double* Fbb = b.at(LB.Fb); double* SB = b.at(LB.slot);
@@ -434,7 +434,7 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     const int r0 = slotrow[s];
     if (r0 < 0) continue;
     const double* ct = CT + 16 * s;
-    double* sb = SB + SLOTBAR * s;
+    double* sb = SB + m.s_barofs[s];
     const int p = m.s_pair[s];
     const int nrow = m.p_condim[p] == 1 ? 1 : 4;
     double cb[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -500,8 +500,8 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     for (int s = 0; s < m.nslot; ++s) {
       if (slotrow[s] < 0) continue;
       const int p = m.s_pair[s];
-      if (m.p_g1[p] == gi) acc += SB[SLOTBAR * s + c];
-      else if (m.p_g2[p] == gi) acc += SB[SLOTBAR * s + 12 + c];
+      if (m.p_g1[p] == gi) acc += SB[m.s_barofs[s] + c];
+      else if (m.p_g2[p] == gi) acc += SB[m.s_barofs[s] + 12 + c];
     }
     GB[t] = acc;
   }

@@ -394,3 +394,40 @@ def test_rest_height_parameter_gradient(orc):
         hi[k] += eps; lo[k] -= eps
         ref = (r_rest(hi) - r_rest(lo)) / (2 * eps)
         assert abs(pb[k] - ref) <= 1e-3 * abs(ref), (PARAM_NAMES[k], pb[k], ref)
+
+
+def _param_floor(orc, name, inp):
+    """Largest change of the parameter gradient when x0 moves by 1e-15
+    (relative and absolute), along the same step sizes."""
+    m = orc.OracleModel(W.SCENES[name]())
+    B = len(inp["x0"])
+    H, N = [], []
+    for e in range(B):
+        r = m.rollout(inp["x0"][e], ctrl=None if inp["ctrl"] is None else inp["ctrl"][e], T=float(inp["T"][e]),
+                      NI=inp["NI"])
+        H.append(r["hlog"]); N.append(r["nsteps"])
+    hl = np.zeros((B, max(N)))
+    for e in range(B):
+        hl[e, :N[e]] = H[e]
+    w = np.random.default_rng(17).normal(size=(B, m.nx))
+    n = np.array(N, dtype=np.int32)
+    g0 = m.batch_replay_grad(inp["x0"], inp["T"], hl, n, w, ctrl=inp["ctrl"], NI=inp["NI"], params=True)
+    rng = np.random.default_rng(3)
+    x1 = inp["x0"] * (1 + 1e-15 * rng.normal(size=inp["x0"].shape)) + 1e-15 * rng.normal(size=inp["x0"].shape)
+    g1 = m.batch_replay_grad(x1, inp["T"], hl, n, w, ctrl=inp["ctrl"], NI=inp["NI"], params=True)
+    return max(rel_err(g1["p_bar"][e], g0["p_bar"][e]) for e in range(B))
+
+
+def test_parameter_gradient_conditioning_floor(orc):
+    """Where the contact-parameter gradient is defined to rounding: with the
+    arm's cube dropped onto the plane, the quadruped (0.3 s) and tumbling
+    boxes, 1e-15 perturbations of x0 move p_bar by less than 1e-8; with the
+    cube resting on the plane or boxes sliding flat on a face (friction rows
+    of coplanar contacts at the edge of the active set) they move it by more
+    than 1e-4, so the GPU parameter-gradient tests use the former inputs."""
+    from tests.test_gpu_adjoint import param_inputs
+    for name in ("chain_cube", "quadruped", "box"):
+        assert _param_floor(orc, name, param_inputs(name)) < 1e-8, name
+    rest = W.chain_inputs(6, T=0.2, NI=4)
+    slow = W.box_push_inputs(12, seed=5, T=0.1)
+    assert max(_param_floor(orc, "chain_cube", rest), _param_floor(orc, "box", slow)) > 1e-4
