@@ -364,6 +364,72 @@ void capsule_box(const Model& m, const Kin<S>& k, const Pair& P, Contact<S>& ct)
 
 // All contact slots of the model, in pair order (every slot is evaluated;
 // inclusion in the constraint problem is decided by the caller).
+// Sphere / capsule pair (App. C.1's "removing discontinuities" pairs, the
+// billiard of Sec. 4): each geom is a segment c + s u, |s| <= L along its
+// local x (L = 0 for a sphere) of radius rad.  The closest points minimise
+// |D + s ua - t ub|^2 (D = ca - cb) over the box |s| <= La, |t| <= Lb: every
+// candidate of the optimality conditions (interior, each edge with the other
+// variable clamped) is evaluated and the least distance taken.  With the set
+// of clamped variables fixed, the free ones solve the reduced linear
+// optimality conditions, re-solved in S so that derivative types carry
+// ds/dtheta, dt/dtheta.  n points from geom 2 to geom 1, r = |d| - ra - rb,
+// pos = pa - (ra + r/2) n.  Degenerate (not differentiable): crossing axes
+// (|d| = 0), i.e. penetrations deeper than the radii.
+template <class S>
+void seg_seg(const Model& m, const Kin<S>& k, const Pair& P, Contact<S>& ct) {
+  const Geom& A = m.geom[P.g1];
+  const Geom& B = m.geom[P.g2];
+  const double ra = A.size[0], La = A.type == GEOM_CAPSULE ? A.size[1] : 0.0;
+  const double rb = B.size[0], Lb = B.type == GEOM_CAPSULE ? B.size[1] : 0.0;
+  const V3<S> ua = {k.gR[P.g1][0], k.gR[P.g1][3], k.gR[P.g1][6]};
+  const V3<S> ub = {k.gR[P.g2][0], k.gR[P.g2][3], k.gR[P.g2][6]};
+  const V3<S> D = vsub(k.gp[P.g1], k.gp[P.g2]);
+  const double c = val(vdot(ua, ub)), Du = val(vdot(D, ua)), Dv = val(vdot(D, ub));
+  auto clampd = [](double x, double L) { return std::min(std::max(x, -L), L); };
+  auto f = [&](double s, double t) {
+    double d2 = 0;
+    for (int i = 0; i < 3; ++i) {
+      const double di = val(D[i]) + s * val(ua[i]) - t * val(ub[i]);
+      d2 += di * di;
+    }
+    return d2;
+  };
+  double bs = 0, bt = 0, best = INFINITY;
+  auto consider = [&](double s, double t) {
+    if (std::fabs(s) > La || std::fabs(t) > Lb) return;
+    const double v = f(s, t);
+    if (v < best) { best = v; bs = s; bt = t; }
+  };
+  if (1.0 - c * c > 1e-12) {
+    const double s0 = (c * Dv - Du) / (1.0 - c * c);
+    consider(s0, Dv + s0 * c);
+  }
+  for (double s0 : {-La, La}) consider(s0, clampd(Dv + s0 * c, Lb));
+  for (double t0 : {-Lb, Lb}) consider(clampd(t0 * c - Du, La), t0);
+  const bool sfree = std::fabs(bs) < La, tfree = std::fabs(bt) < Lb;
+  S s = S(bs), t = S(bt);
+  const S cS = vdot(ua, ub), DuS = vdot(D, ua), DvS = vdot(D, ub);
+  if (sfree && tfree) {            // Du + s - c t = 0, -Dv - c s + t = 0
+    const S det = 1.0 - cS * cS;
+    s = (cS * DvS - DuS) / det;
+    t = DvS + cS * s;
+  } else if (sfree) {
+    s = S(bt) * cS - DuS;
+  } else if (tfree) {
+    t = DvS + S(bs) * cS;
+  }
+  const V3<S> pa = vadd(k.gp[P.g1], vscl(ua, s));
+  const V3<S> d = vsub(vadd(D, vscl(ua, s)), vscl(ub, t));
+  const S rho = sqrt(vdot(d, d));
+  const V3<S> n = vscl(d, S(1.0) / rho);
+  ct.r = rho - (ra + rb);
+  ct.n = n;
+  ct.pos = vsub(pa, vscl(n, S(ra) + 0.5 * ct.r));
+  normal_frame(n, ct.t1, ct.t2);
+  ct.bodyA = A.body;
+  ct.bodyB = B.body;
+}
+
 template <class S> void contacts(const Model& m, const Kin<S>& k, std::vector<Contact<S>>& out) {
   out.resize(m.nslot);
   const V3<S> ez = {S(0.0), S(0.0), S(1.0)}, ex = {S(1.0), S(0.0), S(0.0)}, ey = {S(0.0), S(1.0), S(0.0)};
@@ -373,7 +439,11 @@ template <class S> void contacts(const Model& m, const Kin<S>& k, std::vector<Co
     for (int j = 0; j < P.nslot; ++j) {
       Contact<S>& ct = out[P.slot0 + j];
       ct.pair = pi;
-      if (P.g2 >= 0) { capsule_box(m, k, P, ct); continue; }
+      if (P.g2 >= 0) {
+        if (m.geom[P.g2].type == GEOM_BOX) capsule_box(m, k, P, ct);
+        else seg_seg(m, k, P, ct);
+        continue;
+      }
       ct.bodyA = G.body; ct.bodyB = -1;
       ct.n = ez; ct.t1 = ex; ct.t2 = ey;
       V3<S> cpt;          // sphere centre / capsule end / box vertex

@@ -62,8 +62,12 @@ std::string build_model(Model& m, const double* body, int nbody, const double* g
     P.g1 = (int)r[0]; P.g2 = (int)r[1]; P.condim = (int)r[2]; P.mu = r[3];
     if (P.g1 < 0 || P.g1 >= ngeom || P.g2 >= ngeom) return "pair geom out of range";
     if (P.condim != 1 && P.condim != 3) return "condim must be 1 or 3";
-    if (P.g2 >= 0 && !(m.geom[P.g1].type == GEOM_CAPSULE && m.geom[P.g2].type == GEOM_BOX))
-      return "only plane pairs and capsule-box pairs are supported";
+    if (P.g2 >= 0) {
+      const int t1 = m.geom[P.g1].type, t2 = m.geom[P.g2].type;
+      const bool capbox = t1 == GEOM_CAPSULE && t2 == GEOM_BOX;
+      const bool segseg = (t1 == GEOM_SPHERE || t1 == GEOM_CAPSULE) && (t2 == GEOM_SPHERE || t2 == GEOM_CAPSULE);
+      if (!capbox && !segseg) return "geom pairs: capsule-box or sphere/capsule against sphere/capsule";
+    }
     P.nslot = pair_slots(m, P);
     P.slot0 = m.nslot;
     P.row0 = row;

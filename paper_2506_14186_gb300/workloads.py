@@ -249,6 +249,69 @@ def quadruped_inputs(B=8192, seed=1004):
     return {"x0": x0, "ctrl": ctrl, "T": T, "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3, "max_steps": 20000}
 
 
+def billiard_scene(radius=0.05, mass=0.2, condim=1, mu=0.0, **opt):
+    """Two free balls and no gravity, the ball-ball contact only (the billiard
+    toy of Sec. 4 and App. C.3 with the table contacts and gravity off)."""
+    opt.setdefault("gravity", (0.0, 0.0, 0.0))
+    bodies = [_free_body(mass, sphere_inertia(mass, radius)), _free_body(mass, sphere_inertia(mass, radius))]
+    geoms = [_geom("sphere", 0, [radius]), _geom("sphere", 1, [radius])]
+    return {"name": "billiard", "bodies": bodies, "geoms": geoms, "pairs": [_pair(0, 1, condim, mu)],
+            "actuators": [], "options": _options(**opt),
+            "qpos0": [0.0, 0.0, 0.0] + list(IDQ) + [0.3, 0.0, 0.0] + list(IDQ)}
+
+
+def billiard_inputs(B=16, seed=1007, T=0.5):
+    """Cue ball at the origin shot along +x at U[0.5, 1.5] m/s towards a ball
+    at rest 0.3 m away with a lateral offset U[-0.08, 0.08] m (glancing to
+    head-on hits, some misses)."""
+    g = _rng(seed)
+    x0 = np.zeros((B, 26))
+    x0[:, 3] = 1.0
+    x0[:, 7] = 0.3
+    x0[:, 8] = g.uniform(-0.08, 0.08, B)
+    x0[:, 10] = 1.0
+    x0[:, 14] = g.uniform(0.5, 1.5, B)
+    return {"x0": x0, "ctrl": None, "T": np.full(B, T), "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3,
+            "max_steps": 20000}
+
+
+def capsules_scene(mu=0.5, **opt):
+    """A free capsule (radius 0.03, half length 0.1), a free sphere (0.04) and
+    a second free capsule, no gravity: capsule-capsule, sphere-capsule and
+    sphere-sphere-free pairs with pyramidal friction."""
+    opt.setdefault("gravity", (0.0, 0.0, 0.0))
+    cap_i = rod_inertia(0.3, 0.03, 0.2)
+    bodies = [_free_body(0.3, cap_i), _free_body(0.2, sphere_inertia(0.2, 0.04)), _free_body(0.3, cap_i)]
+    geoms = [_geom("capsule", 0, [0.03, 0.1]), _geom("sphere", 1, [0.04]), _geom("capsule", 2, [0.03, 0.1])]
+    pairs = [_pair(0, 2, 3, mu), _pair(1, 0, 3, mu), _pair(2, 1, 3, mu)]
+    return {"name": "capsules", "bodies": bodies, "geoms": geoms, "pairs": pairs, "actuators": [],
+            "options": _options(**opt),
+            "qpos0": [0.0, 0.0, 0.0] + list(IDQ) + [0.0, 0.2, 0.0] + list(IDQ) + [0.0, 0.0, 0.2] + list(IDQ)}
+
+
+def capsules_inputs(B=16, seed=1008, T=0.4):
+    """The three bodies thrown together: positions jittered N(0, 0.01) m around
+    separated centres, random orientations, velocities towards the centroid
+    (0.8 m/s) plus N(0, 0.1), angular velocities N(0, 2)."""
+    g = _rng(seed)
+    x0 = np.zeros((B, 39))
+    centres = np.array([[0.0, 0.0, 0.0], [0.15, 0.2, 0.0], [0.0, 0.05, 0.25]])
+    for b in range(3):
+        qa, va = 7 * b, 21 + 6 * b
+        x0[:, qa:qa + 3] = centres[b] + g.normal(0.0, 0.01, (B, 3))
+        qq = g.normal(size=(B, 4))
+        x0[:, qa + 3:qa + 7] = qq / np.linalg.norm(qq, axis=1, keepdims=True)
+    cen = (x0[:, 0:3] + x0[:, 7:10] + x0[:, 14:17]) / 3
+    for b in range(3):
+        qa, va = 7 * b, 21 + 6 * b
+        d = cen - x0[:, qa:qa + 3]
+        d /= np.maximum(np.linalg.norm(d, axis=1, keepdims=True), 1e-9)
+        x0[:, va:va + 3] = 0.8 * d + g.normal(0.0, 0.1, (B, 3))
+        x0[:, va + 3:va + 6] = g.normal(0.0, 2.0, (B, 3))
+    return {"x0": x0, "ctrl": None, "T": np.full(B, T), "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3,
+            "max_steps": 20000}
+
+
 def toss_scene():
     """Cube toss of the integrator comparison (Sec. 3, Fig. 12): the 0.1 m,
     1 kg cube with the toss contact setting solref (0.005 s, 1)."""
@@ -279,6 +342,6 @@ def chain_goal():
 
 
 SCENES = {"ball": ball_scene, "box": box_scene, "chain_cube": chain_cube_scene, "quadruped": quadruped_scene,
-          "toss": toss_scene}
+          "toss": toss_scene, "billiard": billiard_scene, "capsules": capsules_scene}
 INPUTS = {"ball": ball_inputs, "box": box_push_inputs, "chain_cube": chain_inputs, "quadruped": quadruped_inputs,
-          "toss": toss_inputs}
+          "toss": toss_inputs, "billiard": billiard_inputs, "capsules": capsules_inputs}
