@@ -307,6 +307,22 @@ class OracleModel:
             out["p_bar"] = pb
         return out
 
+    def batch_grad_otd(self, x0, T, xT_bar, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000,
+                       cfd=False, xb_bar=None, nthreads=None, method="dopri5"):
+        """Optimize-then-discretize (backsolve) gradient: the continuous adjoint
+        integrated backward with the state, its own adaptive steps."""
+        x0 = _f64(x0)
+        B = x0.shape[0]
+        xT = np.zeros((B, self.nx)); gx = np.zeros((B, self.nx)); st = np.zeros((B, 8), dtype=np.int32)
+        gu = np.zeros((B, NI, self.nu)) if self.nu else None
+        c = _f64(ctrl) if (ctrl is not None and self.nu) else None
+        lib().orc_batch_grad_otd(self.h, B, _p(x0), _p(c), _p(_f64(np.broadcast_to(T, (B,)))), NI,
+                                 ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_double(h0), max_steps, int(cfd),
+                                 _p(_f64(xT_bar)), _p(_f64(xb_bar) if xb_bar is not None else None), _p(xT), _p(gx),
+                                 _p(gu), _p(st), int(nthreads or os.cpu_count() or 1), METHODS[method])
+        return {"xT": xT, "x0_bar": gx, "ctrl_bar": gu, "status": st[:, 0].copy(), "nsteps": st[:, 1].copy(),
+                "back_status": st[:, 4].copy(), "back_steps": st[:, 5].copy(), "back_rej": st[:, 6].copy()}
+
     def nparams(self):
         """Model parameters of the adjoint: t_c, phi_d, d_o, d_w, width, midpoint, then mu of each pair."""
         return int(lib().orc_nparams(self.h))

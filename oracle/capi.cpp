@@ -327,4 +327,25 @@ long long orc_count_adjoint_flops(void* h, const double* x0, const double* ctrl,
   return (long long)g_flops;
 }
 
+// Optimize-then-discretize (backsolve) gradient of a batch of rollouts
+// (environment-major arrays); stats [B][8]: forward status, steps, rejects,
+// rhs, then the backward solve's status, steps, rejects, 0.
+int orc_batch_grad_otd(void* h, int B, const double* x0, const double* ctrl, const double* T, int NI, double rtol,
+                       double atol, double h0, int max_steps, int cfd, const double* xT_bar, const double* xb_bar,
+                       double* xT, double* x0_bar, double* ctrl_bar, int* stats, int nthreads, int method) {
+  Model& m = M(h);
+  const int nx = m.nq + m.nv, nu = m.nu;
+  parallel_for(B, nthreads, [&](int b) {
+    Result back;
+    Result r = rollout_grad_otd(m, x0 + (size_t)b * nx, ctrl ? ctrl + (size_t)b * NI * nu : nullptr,
+                                make_opts(T[b], NI, rtol, atol, h0, max_steps, method), cfd != 0, xT_bar + (size_t)b * nx,
+                                xb_bar ? xb_bar + (size_t)b * (NI + 1) * nx : nullptr, xT + (size_t)b * nx,
+                                x0_bar + (size_t)b * nx, ctrl_bar ? ctrl_bar + (size_t)b * NI * nu : nullptr, &back);
+    put_stats(r, stats + 8 * b);
+    put_stats(back, stats + 8 * b + 4);
+    stats[8 * b + 7] = 0;
+  });
+  return 0;
+}
+
 }  // extern "C"

@@ -463,4 +463,174 @@ inline Result rollout_grad(const Model& m, const double* x0, const double* ctrl,
   return res;
 }
 
+// ------------------------------------------------------------------ optimize-then-discretize
+// Continuous adjoint (App. C.2 "Optimize-then-discretize", Eq. adjoint-
+// equations; the straight-through variant of App. C.3): with x = (q, v),
+// x' = f(x, u) = (G(q) v, F(q, v, u)) and a_x(T) = dL/dx(T),
+//   a_x' = -a_x^T df/dx,   a_u' = -a_x^T df/du  (per control interval),
+// integrated BACKWARD from T together with the state itself (backsolve: the
+// state runs backward from x(T), constant memory).  With cfd the VJPs use F~
+// (the state still follows F).  The backward solve takes its own adaptive
+// steps (the scheme and PID controller of the forward pass) with the error
+// norm over the state's 2 nv tangent components and every adjoint component.
+// G(q): identity for translations and hinges, q' = q (x) (0, w) / 2 for the
+// quaternion of a free joint (w: body angular velocity).  Interval-boundary
+// cotangents xb_bar[k] enter as jumps of a_x at t_k; a_u is collected per
+// interval.  In reversed time s = T - t: dx/ds = -f, da/ds = +(df/dx)^T a.
+
+// Kinematic part of the adjoint right-hand side at (q, v): kq += (d(G v)/dq)^T aq,
+// kv += G^T aq.
+inline void kin_adjoint(const Model& m, const double* q, const double* v, const double* aq, double* kq, double* kv) {
+  for (const Body& B : m.body) {
+    const int qa = B.qadr, va = B.vadr;
+    if (B.jtype == JNT_HINGE) { kv[va] += aq[qa]; continue; }
+    for (int i = 0; i < 3; ++i) kv[va + i] += aq[qa + i];
+    const double w = q[qa + 3], x = q[qa + 4], y = q[qa + 5], z = q[qa + 6];
+    const double a = v[va + 3], b = v[va + 4], c = v[va + 5];
+    const double Aw = aq[qa + 3], Ax = aq[qa + 4], Ay = aq[qa + 5], Az = aq[qa + 6];
+    // q (x) (0, a, b, c) = (-x a - y b - z c, w a + y c - z b, w b - x c + z a, w c + x b - y a)
+    kq[qa + 3] += 0.5 * (a * Ax + b * Ay + c * Az);
+    kq[qa + 4] += 0.5 * (-a * Aw - c * Ay + b * Az);
+    kq[qa + 5] += 0.5 * (-b * Aw + c * Ax - a * Az);
+    kq[qa + 6] += 0.5 * (-c * Aw - b * Ax + a * Ay);
+    kv[va + 3] += 0.5 * (-x * Aw + w * Ax + z * Ay - y * Az);
+    kv[va + 4] += 0.5 * (-y * Aw - z * Ax + w * Ay + x * Az);
+    kv[va + 5] += 0.5 * (-z * Aw + y * Ax - x * Ay + w * Az);
+  }
+}
+
+// Adjoint right-hand side in reversed time at the stage state (q, v):
+// (kq, kv, ku) = (df/dx)^T (aq, av) and (dF/du)^T av, with F (or F~).
+inline void adjoint_rhs(const Model& m, const double* q, const double* v, const double* u, bool cfd,
+                        const double* aq, const double* av, double* kq, double* kv, double* ku) {
+  using D = Dual<double>;
+  const int nq = m.nq, nv = m.nv, nu = m.nu;
+  std::vector<D> qd(nq), vd(nv), ud(std::max(nu, 1)), acc(nv);
+  for (int i = 0; i < nq; ++i) kq[i] = 0.0;
+  for (int i = 0; i < nv; ++i) kv[i] = 0.0;
+  for (int i = 0; i < nu; ++i) ku[i] = 0.0;
+  for (int dir = 0; dir < nq + nv + nu; ++dir) {     // columns of dF/d(q, v, u), one derivative direction each
+    for (int i = 0; i < nq; ++i) qd[i] = D(q[i], dir == i ? 1.0 : 0.0);
+    for (int i = 0; i < nv; ++i) vd[i] = D(v[i], dir == nq + i ? 1.0 : 0.0);
+    for (int i = 0; i < nu; ++i) ud[i] = D(u[i], dir == nq + nv + i ? 1.0 : 0.0);
+    rhs<D>(m, qd.data(), vd.data(), ud.data(), cfd, acc.data());
+    double s = 0.0;
+    for (int i = 0; i < nv; ++i) s += acc[i].d * av[i];
+    if (dir < nq) kq[dir] += s; else if (dir < nq + nv) kv[dir - nq] += s; else ku[dir - nq - nv] += s;
+  }
+  kin_adjoint(m, q, v, aq, kq, kv);
+}
+
+inline Result rollout_grad_otd(const Model& m, const double* x0, const double* ctrl, const Opts& o, bool cfd,
+                               const double* xT_bar, const double* xb_bar, double* xT, double* x0_bar,
+                               double* ctrl_bar, Result* back = nullptr) {
+  const int nq = m.nq, nv = m.nv, nx = nq + nv, nu = m.nu;
+  Result res = rollout<double>(m, x0, ctrl, o, xT, nullptr, nullptr, nullptr, nullptr, 0);
+  const Tableau& tb = tableau_of(o.method);
+  const int ns = tb.S;
+  const int na = nx + nu;                               // adjoint components (a_q, a_v, a_u)
+  std::vector<double> q(xT, xT + nq), v(xT + nq, xT + nx), a(na, 0.0);
+  for (int i = 0; i < nx; ++i) a[i] = xT_bar[i];
+  if (xb_bar) for (int i = 0; i < nx; ++i) a[i] += xb_bar[(size_t)o.NI * nx + i];
+  if (ctrl_bar) for (int i = 0; i < o.NI * nu; ++i) ctrl_bar[i] = 0.0;
+  std::vector<std::vector<double>> kv_(ns, std::vector<double>(nv)), kf(ns, std::vector<double>(nv)),
+      ka(ns, std::vector<double>(na));
+  std::vector<double> dq(nv), qs(nq), vs(nv), as(na), q7(nq), v7(nv), a7(na), tmpq(nq), tmpv(nv), tmpu(std::max(nu, 1));
+  Result bres;
+  StageRhs<double> f{m, false};
+  int k = o.NI - 1;
+  double t = o.T, h = o.h0, err_prev = 1.0;
+  auto uk = [&](int kk) { return nu ? ctrl + (size_t)kk * nu : ctrl; };
+  int attempts = 0;
+  while (t > 0.0 && k >= 0) {
+    if (attempts >= o.max_steps) { bres.status = ENV_MAX_STEPS; break; }
+    const double tlo = boundary_time(o.T, o.NI, k);
+    const double hb = t - tlo;
+    const bool clamped = h >= hb || hb - h < 1e-12;
+    const double ht = clamped ? hb : h;
+    if (ht < 1e-12) { bres.status = ENV_H_UNDERFLOW; break; }
+    const double* u = uk(k);
+    // stage 0
+    for (int i = 0; i < nv; ++i) kv_[0][i] = v[i];
+    f(q.data(), v.data(), u, kf[0].data());
+    adjoint_rhs(m, q.data(), v.data(), u, cfd, a.data(), a.data() + nq, ka[0].data(), ka[0].data() + nq,
+                ka[0].data() + nx);
+    for (int s = 1; s < ns; ++s) {
+      for (int i = 0; i < nv; ++i) {
+        double sv = 0.0;
+        for (int j = 0; j < s; ++j) if (tb.av[s][j] != 0.0) sv += tb.av[s][j] * kf[j][i];
+        vs[i] = v[i] - ht * sv;
+        kv_[s][i] = vs[i];
+      }
+      for (int i = 0; i < nv; ++i) {
+        double sq = 0.0;
+        for (int j = 0; j <= s; ++j) if (tb.aq[s][j] != 0.0) sq += tb.aq[s][j] * kv_[j][i];
+        dq[i] = -ht * sq;
+      }
+      integrate_pos(m, q.data(), dq.data(), qs.data());
+      for (int i = 0; i < na; ++i) {
+        double sa = 0.0;
+        for (int j = 0; j < s; ++j) if (tb.av[s][j] != 0.0) sa += tb.av[s][j] * ka[j][i];
+        as[i] = a[i] + ht * sa;
+      }
+      f(qs.data(), vs.data(), u, kf[s].data());
+      adjoint_rhs(m, qs.data(), vs.data(), u, cfd, as.data(), as.data() + nq, ka[s].data(), ka[s].data() + nq,
+                  ka[s].data() + nx);
+      if (s == ns - 1) { q7 = qs; v7 = vs; a7 = as; }
+    }
+    ++attempts;
+    double err = 0.0;
+    if (tb.adaptive) {
+      double acc = 0.0;
+      for (int i = 0; i < nv; ++i) {
+        double ep = 0.0, ev = 0.0;
+        for (int j = 0; j < ns; ++j) {
+          const double w = tb.b[j] - tb.bhat[j];
+          ep += w * kv_[j][i];
+          ev += w * kf[j][i];
+        }
+        ep *= ht; ev *= ht;
+        const double sp = o.atol + o.rtol * std::max(val(pos_magnitude(m, q.data(), i)), val(pos_magnitude(m, q7.data(), i)));
+        const double sv = o.atol + o.rtol * std::max(std::fabs(v[i]), std::fabs(v7[i]));
+        acc += (ep / sp) * (ep / sp) + (ev / sv) * (ev / sv);
+      }
+      for (int i = 0; i < na; ++i) {
+        double ea = 0.0;
+        for (int j = 0; j < ns; ++j) ea += (tb.b[j] - tb.bhat[j]) * ka[j][i];
+        ea *= ht;
+        const double sa = o.atol + o.rtol * std::max(std::fabs(a[i]), std::fabs(a7[i]));
+        acc += (ea / sa) * (ea / sa);
+      }
+      err = std::sqrt(acc / (2.0 * nv + na));
+    }
+    if (err <= 1.0) {
+      q = q7; v = v7; a = a7;
+      ++bres.nsteps;
+      t = clamped ? tlo : t - ht;
+      if (tb.adaptive) {
+        const double errf = std::max(err, 1e-10);
+        double fac = 0.9 * std::pow(errf, -0.6 / 5.0) * std::pow(err_prev, 0.2 / 5.0);
+        fac = std::min(10.0, std::max(0.2, fac));
+        err_prev = errf;
+        h = ht * fac;
+      } else {
+        h = o.h0;
+      }
+      if (clamped) {                                  // reached the interval's lower boundary t_k
+        if (ctrl_bar) for (int j = 0; j < nu; ++j) ctrl_bar[(size_t)k * nu + j] += a[nx + j];
+        for (int j = 0; j < nu; ++j) a[nx + j] = 0.0;
+        if (xb_bar) for (int i = 0; i < nx; ++i) a[i] += xb_bar[(size_t)k * nx + i];
+        --k;
+      }
+    } else {
+      ++bres.nrej;
+      const double fac = std::isfinite(err) ? std::max(0.2, 0.9 * std::pow(err, -1.0 / 5.0)) : 0.2;
+      h = ht * fac;
+    }
+  }
+  for (int i = 0; i < nx; ++i) x0_bar[i] = a[i];
+  if (back) *back = bres;
+  return res;
+}
+
 }  // namespace orc
