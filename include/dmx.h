@@ -95,9 +95,11 @@ typedef struct {
 } dmx_geom_desc;
 
 /* Contact pair: geom1 against the ground plane z = 0 (geom2 = -1: sphere 1
- * contact, capsule 2 end-sphere contacts, box 8 vertex contacts), or capsule
- * geom1 against box geom2 (one contact).  condim 1 = frictionless normal row,
- * condim 3 = pyramidal cone with 4 edge rows n +- mu t1, n +- mu t2. */
+ * contact, capsule 2 end-sphere contacts, box 8 vertex contacts), capsule
+ * geom1 against box geom2, or a sphere / capsule against a sphere / capsule
+ * of another body (closest points of the two segments, one contact; the
+ * ball-ball contact of the billiard, Sec. 4).  condim 1 = frictionless normal
+ * row, condim 3 = pyramidal cone with 4 edge rows n +- mu t1, n +- mu t2. */
 typedef struct {
   int32_t geom1, geom2, condim;
   double mu;
@@ -196,6 +198,36 @@ dmx_status dmx_model_params(const dmx_model* m, int32_t* np, double* values);
 dmx_status dmx_rollout_grad_params(dmx_model* m, dmx_tape* tape, int32_t cfd, const double* xT_bar,
                                    const double* xb_bar, double* x0_bar, double* ctrl_bar, double* p_bar,
                                    double* p_bar_sum, void* stream);
+/* Optimize-then-discretize gradient (App. C.2, Eq. adjoint-equations:
+ * BacksolveAdjoint; with cfd = 1 the straight-through variant of App. C.3).
+ * The continuous adjoint a_x' = -a_x^T df/dx, a_u' = -a_x^T df/du of
+ * x' = f(x, u) = (G(q) v, F(q, v, u)) is integrated backward from x(T)
+ * together with the state itself, with its own adaptive steps (the scheme
+ * `method` and the PID controller of the forward pass, error norm over the
+ * state's tangent components and every adjoint component, tolerances
+ * rtol / atol, first trial step h0), so it needs only the final states and
+ * no tape (constant memory).  The gradient is that of the continuous map up
+ * to the backward solve's tolerance, not of the discretisation (contrast
+ * dmx_rollout_grad).  Backward integration of dissipative contacts runs them
+ * anti-damped: a tolerance too tight for that may end an environment with
+ * DMX_ENV_H_UNDERFLOW in status. */
+typedef struct {
+  int32_t B, NI;
+  const double* xT;           /* [nx][B] final states of the forward rollout */
+  const double* ctrl;         /* [NI][nu][B] controls, NULL iff nu == 0 */
+  const double* T;            /* [B] horizons */
+  double rtol, atol, h0;      /* backward error control (rtol >= 0, atol > 0, h0 > 0) */
+  int32_t max_steps;          /* backward step-attempt budget per environment */
+  int32_t method;             /* DMX_METHOD_* of the backward solve */
+  int32_t cfd;                /* 1: VJPs of F~ (straight-through) */
+  const double* xT_bar;       /* [nx][B] dL/dx(T) */
+  const double* xb_bar;       /* [NI+1][nx][B] cotangents of the interval-boundary states, or NULL */
+  double* x0_bar;             /* out [nx][B] a_x(0) */
+  double* ctrl_bar;           /* out [NI][nu][B], NULL iff nu == 0 */
+  int32_t* steps;             /* out [B] accepted backward steps, or NULL */
+  int32_t* status;            /* out [B] DMX_ENV_* of the backward solve, or NULL */
+} dmx_otd_args;
+dmx_status dmx_rollout_grad_otd(dmx_model* m, const dmx_otd_args* a, void* stream);
 /* Kernel that dmx_rollout_grad runs for this model (both compute the same
  * derivative; results agree to rounding):
  *   DMX_ADJ_REVERSE (default): reverse mode, a group of lanes per environment

@@ -39,7 +39,8 @@ _ACT = {"motor": 0, "position": 1}
 ABI_SYMBOLS = ("dmx_create_model", "dmx_destroy_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad",
                "dmx_tape_free", "dmx_tape_read", "dmx_autotune", "dmx_set_lanes", "dmx_model_info", "dmx_server_create", "dmx_submit", "dmx_poll",
                "dmx_server_destroy", "dmx_eval_rhs", "dmx_rollout_static", "dmx_set_adjoint", "dmx_eval_rhs_vjp",
-               "dmx_fp64_peak", "dmx_model_params", "dmx_rollout_grad_params", "dmx_last_error")
+               "dmx_fp64_peak", "dmx_model_params", "dmx_rollout_grad_params", "dmx_rollout_grad_otd",
+               "dmx_last_error")
 
 
 class BodyDesc(ctypes.Structure):
@@ -74,6 +75,12 @@ class RolloutArgs(ctypes.Structure):
                 ("status", c_p), ("tape", ctypes.POINTER(c_p)), ("method", c_i32)]
 
 
+class OtdArgs(ctypes.Structure):
+    _fields_ = [("B", c_i32), ("NI", c_i32), ("xT", c_p), ("ctrl", c_p), ("T", c_p), ("rtol", c_f64), ("atol", c_f64),
+                ("h0", c_f64), ("max_steps", c_i32), ("method", c_i32), ("cfd", c_i32), ("xT_bar", c_p),
+                ("xb_bar", c_p), ("x0_bar", c_p), ("ctrl_bar", c_p), ("steps", c_p), ("status", c_p)]
+
+
 class ServerCfg(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_int64), ("max_inflight", c_i32), ("nstreams", c_i32),
                 ("host_stage_bytes", ctypes.c_int64)]
@@ -104,7 +111,8 @@ def lib():
         for name in ("dmx_create_model", "dmx_model_dims", "dmx_rollout", "dmx_rollout_grad", "dmx_autotune",
                      "dmx_server_create", "dmx_submit", "dmx_poll", "dmx_server_destroy", "dmx_model_info",
                      "dmx_set_lanes", "dmx_eval_rhs", "dmx_tape_read", "dmx_rollout_static", "dmx_set_adjoint",
-                     "dmx_eval_rhs_vjp", "dmx_fp64_peak", "dmx_model_params", "dmx_rollout_grad_params"):
+                     "dmx_eval_rhs_vjp", "dmx_fp64_peak", "dmx_model_params", "dmx_rollout_grad_params",
+                     "dmx_rollout_grad_otd"):
             getattr(L, name).restype = c_i32
         L.dmx_destroy_model.restype = None
         L.dmx_tape_free.restype = None
@@ -323,6 +331,30 @@ def rollout_grad_params(tape, xT_bar, xb_bar=None, cfd=False, stream=None):
     _check(lib().dmx_rollout_grad_params(m.h, tape.h, int(cfd), _ptr(xT_bar), _ptr(xb_bar), _ptr(x0_bar),
                                          _ptr(ctrl_bar), _ptr(p_bar), _ptr(p_sum), _stream_handle(stream)))
     return x0_bar, ctrl_bar, p_bar, p_sum
+
+
+def rollout_grad_otd(model, xT, T, xT_bar, ctrl=None, NI=1, xb_bar=None, cfd=False, rtol=1e-6, atol=1e-8, h0=1e-3,
+                     max_steps=20000, method="dopri5", stream=None):
+    """Optimize-then-discretize gradient (backsolve) from the final states xT
+    [nx, B]: returns (x0_bar [nx, B], ctrl_bar [NI, nu, B] or None, steps [B],
+    status [B]) of the backward solve."""
+    import torch
+    for t_, nm in ((xT, "xT"), (T, "T"), (xT_bar, "xT_bar")):
+        _require_cuda(t_, nm, torch.float64)
+    B = xT.shape[1]
+    dev = xT.device
+    x0_bar = torch.empty((model.nx, B), dtype=torch.float64, device=dev)
+    ctrl_bar = torch.empty((NI, model.nu, B), dtype=torch.float64, device=dev) if model.nu else None
+    steps = torch.empty(B, dtype=torch.int32, device=dev)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    if model.nu:
+        _require_cuda(ctrl, "ctrl", torch.float64)
+    args = OtdArgs(B, NI, xT.data_ptr(), ctrl.data_ptr() if model.nu else None, T.data_ptr(), rtol, atol, h0,
+                   max_steps, METHODS[method], int(cfd), xT_bar.data_ptr(),
+                   xb_bar.data_ptr() if xb_bar is not None else None, x0_bar.data_ptr(),
+                   ctrl_bar.data_ptr() if ctrl_bar is not None else None, steps.data_ptr(), status.data_ptr())
+    _check(lib().dmx_rollout_grad_otd(model.h, ctypes.byref(args), _stream_handle(stream)))
+    return x0_bar, ctrl_bar, steps, status
 
 
 def eval_rhs_vjp(model, q, v, abar, u=None, cfd=False, lanes=0, stream=None):

@@ -44,7 +44,7 @@ __host__ __device__ inline SnapOff snap_offsets(const DevModel& m, const Layout&
   o.o2 = o.n1;
   o.n2 = L.tmp2 + m.nv - L.H;
   o.o3 = o.o2 + o.n2;
-  o.o4 = o.o3 + 17 * m.nslot;          // contact records, then the capsule-box minimisers
+  o.o4 = o.o3 + 18 * m.nslot;          // contact records, then the closest-point parameters (2 per slot)
   o.o5 = o.o4 + L.rcap * m.nv;
   o.o6 = o.o5 + L.rcap;
   o.oi = o.o6 + L.rcap;

@@ -51,7 +51,7 @@ __device__ void snap_save(const Grp<G>& g, const DevModel& m, const Ws& w, doubl
   for (int i = g.lane; i < o.n1; i += G) dst[i] = d[L.R + i];
   for (int i = g.lane; i < o.n2; i += G) dst[o.o2 + i] = d[L.H + i];
   for (int i = g.lane; i < 16 * m.nslot; i += G) dst[o.o3 + i] = d[L.ct + i];
-  for (int i = g.lane; i < m.nslot; i += G) dst[o.o3 + 16 * m.nslot + i] = d[L.csv + i];
+  for (int i = g.lane; i < 2 * m.nslot; i += G) dst[o.o3 + 16 * m.nslot + i] = d[L.csv + i];
   for (int i = g.lane; i < nr * m.nv; i += G) dst[o.o4 + i] = d[L.J + i];
   for (int i = g.lane; i < nr; i += G) { dst[o.o5 + i] = d[L.Dr + i]; dst[o.o6 + i] = d[L.z + i]; }
   int* di = reinterpret_cast<int*>(dst + o.oi);
@@ -72,7 +72,7 @@ __device__ int snap_restore(const Grp<G>& g, const DevModel& m, const Ws& w, con
   double* d = w.d;
   for (int i = g.lane; i < o.n1; i += G) d[L.R + i] = src[i];
   for (int i = g.lane; i < o.n2; i += G) d[L.H + i] = src[o.o2 + i];
-  for (int i = g.lane; i < m.nslot; i += G) d[L.csv + i] = src[o.o3 + 16 * m.nslot + i];
+  for (int i = g.lane; i < 2 * m.nslot; i += G) d[L.csv + i] = src[o.o3 + 16 * m.nslot + i];
   for (int i = g.lane; i < nr; i += G) { d[L.Dr + i] = src[o.o5 + i]; d[L.z + i] = src[o.o6 + i]; }
   for (int i = g.lane; i <= m.nslot; i += G) w.i[L.slotrow + i] = si[2 + i];
   for (int i = g.lane; i < nr; i += G) w.i[L.rowid + i] = si[3 + m.nslot + i];

@@ -653,6 +653,91 @@ __device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1,
 }
 
 // Spline of the solimp shape on x in [0, 1] (midpoint mid, power pw).
+// Sphere / capsule pair (the billiard's ball-ball contact of Sec. 4, capsule
+// pairs of App. C.1): geom g is the segment c + s u, |s| <= L along its local
+// x (L = 0 for a sphere), radius rad.  Closest points: the least of the
+// candidates of the box-constrained optimality conditions of
+// |D + s ua - t ub|^2 (D = ca - cb): the interior point (non-parallel axes)
+// and each edge with the other parameter clamped.  Decisions on values; with
+// derivative scalars the free parameters are re-solved from the reduced
+// optimality conditions (Du + s - c t = 0, -Dv - c s + t = 0), carrying
+// ds/dtheta, dt/dtheta.  n from geom 2 to geom 1, r = |d| - ra - rb,
+// pos = pa - (ra + r/2) n; tangent frame as for capsule-box.  st_out: s, t.
+__device__ __forceinline__ double seg_half(const DevModel& m, int g) {
+  return m.g_type[g] == GEOM_CAPSULE ? m.g_size[g][1] : 0.0;
+}
+__device__ __forceinline__ void seg_closest(double c, double Du, double Dv, double La, double Lb, const double* D,
+                                            const double* ua, const double* ub, double* s_out, double* t_out) {
+  double bs = 0.0, bt = 0.0, best = INFINITY;
+  auto consider = [&](double s, double t) {
+    if (fabs(s) > La || fabs(t) > Lb) return;
+    double d2 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      const double di = D[i] + s * ua[i] - t * ub[i];
+      d2 += di * di;
+    }
+    if (d2 < best) { best = d2; bs = s; bt = t; }
+  };
+  if (1.0 - c * c > 1e-12) {
+    const double s0 = (c * Dv - Du) / (1.0 - c * c);
+    consider(s0, Dv + s0 * c);
+  }
+  consider(-La, fmin(fmax(Dv - La * c, -Lb), Lb));
+  consider(La, fmin(fmax(Dv + La * c, -Lb), Lb));
+  consider(fmin(fmax(-Lb * c - Du, -La), La), -Lb);
+  consider(fmin(fmax(Lb * c - Du, -La), La), Lb);
+  *s_out = bs;
+  *t_out = bt;
+}
+template <class T>
+__device__ void seg_seg(const DevModel& m, const T* gR, const T* gp, int g1, int g2, double thr, T* ct, T* st_out) {
+  const double ra = m.g_size[g1][0], rb = m.g_size[g2][0];
+  const double La = seg_half(m, g1), Lb = seg_half(m, g2);
+  const T* R1 = gR + 9 * g1; const T* R2 = gR + 9 * g2;
+  const T* c1 = gp + 3 * g1; const T* c2 = gp + 3 * g2;
+  const T D[3] = {c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2]};
+  const double reach = m.g_bound[g1] + m.g_bound[g2] + (thr > 0 ? thr : 0.0);
+  const double Dv0[3] = {value(D[0]), value(D[1]), value(D[2])};
+  if (Dv0[0] * Dv0[0] + Dv0[1] * Dv0[1] + Dv0[2] * Dv0[2] > reach * reach) { ct[0] = 1e30; return; }
+  const T ua[3] = {R1[0], R1[3], R1[6]}, ub[3] = {R2[0], R2[3], R2[6]};
+  const double uav[3] = {value(ua[0]), value(ua[1]), value(ua[2])}, ubv[3] = {value(ub[0]), value(ub[1]), value(ub[2])};
+  const double cv = dot3(uav, ubv), Duv = dot3(Dv0, uav), Dvv = dot3(Dv0, ubv);
+  double sv, tv;
+  seg_closest(cv, Duv, Dvv, La, Lb, Dv0, uav, ubv, &sv, &tv);
+  st_out[0] = T(sv);
+  st_out[1] = T(tv);
+  T s = sv, t = tv;
+  if constexpr (!std::is_same<T, double>::value) {
+    const bool sf = fabs(sv) < La, tf = fabs(tv) < Lb;
+    const T c = dot3(ua, ub), Du = dot3(D, ua), Dv = dot3(D, ub);
+    if (sf && tf) {
+      s = (c * Dv - Du) / (1.0 - c * c);
+      t = Dv + c * s;
+    } else if (sf) {
+      s = tv * c - Du;
+    } else if (tf) {
+      t = Dv + sv * c;
+    }
+  }
+  T d[3], n[3];
+  for (int i = 0; i < 3; ++i) d[i] = D[i] + s * ua[i] - t * ub[i];
+  const T rho = sqrt(dot3(d, d));
+  const T ir = 1.0 / rho;
+  for (int i = 0; i < 3; ++i) n[i] = d[i] * ir;
+  const T r = rho - (ra + rb);
+  ct[0] = r;
+  const T off = ra + 0.5 * r;
+  for (int i = 0; i < 3; ++i) { ct[1 + i] = c1[i] + s * ua[i] - off * n[i]; ct[4 + i] = n[i]; }
+  double ref[3] = {0, 0, 1};
+  if (fabs(value(n[2])) >= 0.5) { ref[0] = 1; ref[2] = 0; }
+  T t1[3], t2[3];
+  cross3(n, ref, t1);
+  const T il = rsqrt_t(dot3(t1, t1));
+  t1[0] *= il; t1[1] *= il; t1[2] *= il;
+  cross3(n, t1, t2);
+  for (int i = 0; i < 3; ++i) { ct[7 + i] = t1[i]; ct[10 + i] = t2[i]; }
+}
+
 template <class T>
 __device__ __forceinline__ T spline_shape(const T& x, double mid, double pw) {
   if (value(x) <= mid && mid > 0) {
@@ -707,7 +792,8 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, boo
     T* ct = CT + 16 * s;
     const int p = m.s_pair[s], j = m.s_idx[s], g1 = m.p_g1[p];
     if (m.p_g2[p] >= 0) {
-      capsule_box(m, gR, gp, g1, m.p_g2[p], thr, ct, w.at(L.csv) + s);
+      if (m.g_type[m.p_g2[p]] == GEOM_BOX) capsule_box(m, gR, gp, g1, m.p_g2[p], thr, ct, w.at(L.csv) + 2 * s);
+      else seg_seg(m, gR, gp, g1, m.p_g2[p], thr, ct, w.at(L.csv) + 2 * s);
     } else {
       const T* Rg = gR + 9 * g1; const T* cg = gp + 3 * g1;
       T pt[3];

@@ -77,7 +77,7 @@ struct Layout {
   int qn, vn, qs, vs, kv, ka, dq;
   int R, p, com, sd, Ib, Ic, F, Vb, Ab, Fb, iv, gR, gp;
   int M, H, rhs0, a, an, tmp, tmp2;
-  int ct, csv, J, aref, Dr, z, s, u;   // csv: capsule-box minimiser per slot
+  int ct, csv, J, aref, Dr, z, s, u;   // csv: closest-point parameters of each geom-pair slot (2 per slot)
   int nd;                            // doubles per environment (padded to even)
   int xl, sc;                        // kinematics scratch, aliases of Ab..Fb (12 per body) and iv (2 per body)
   int rowid, slotrow, slist, amask, pmask, misc;
@@ -104,7 +104,7 @@ DMX_HD inline Layout make_layout(const DevModel& m, int rcap) {
   L.gR = take(9 * ng); L.gp = take(3 * ng);
   L.M = take(nv * nv); L.H = take(nv * nv);
   L.rhs0 = take(nv); L.a = take(nv); L.an = take(nv); L.tmp = take(nv); L.tmp2 = take(nv);
-  L.ct = take(16 * ns); L.csv = take(ns);
+  L.ct = take(16 * ns); L.csv = take(2 * ns);
   L.J = take(rcap * nv); L.aref = take(rcap); L.Dr = take(rcap); L.z = take(rcap); L.s = take(rcap);
   L.u = take(m.nu > 0 ? m.nu : 1);
   L.nd = (o + 1) & ~1;
@@ -142,7 +142,7 @@ DMX_HD inline Layout make_layout_adj(const DevModel& m, int rcap) {
   L.gR = take(9 * ng); L.gp = take(3 * ng);
   L.H = take(nv * nv);
   L.rhs0 = take(nv); L.a = take(nv); L.an = take(nv); L.tmp = take(nv); L.tmp2 = take(nv);
-  L.csv = take(ns); L.Dr = take(rcap); L.z = take(rcap);
+  L.csv = take(2 * ns); L.Dr = take(rcap); L.z = take(rcap);
   L.u = take(m.nu > 0 ? m.nu : 1);
   L.xbar = take(nq + nv);
   L.ovl = o;

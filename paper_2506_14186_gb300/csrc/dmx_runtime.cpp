@@ -138,8 +138,13 @@ static std::string compile_model(const dmx_model_desc* d, DevModel& m) {
     const dmx_pair_desc& P = d->pair[p];
     if (P.geom1 < 0 || P.geom1 >= m.ngeom || P.geom2 >= m.ngeom || P.geom2 < -1) return "pair geom out of range";
     if (P.condim != 1 && P.condim != 3) return "condim must be 1 or 3";
-    if (P.geom2 >= 0 && !(m.g_type[P.geom1] == DMX_GEOM_CAPSULE && m.g_type[P.geom2] == DMX_GEOM_BOX))
-      return "only plane pairs and capsule-box pairs are supported";
+    if (P.geom2 >= 0) {
+      const int t1 = m.g_type[P.geom1], t2 = m.g_type[P.geom2];
+      const bool capbox = t1 == DMX_GEOM_CAPSULE && t2 == DMX_GEOM_BOX;
+      const bool segseg = (t1 == DMX_GEOM_SPHERE || t1 == DMX_GEOM_CAPSULE) && (t2 == DMX_GEOM_SPHERE || t2 == DMX_GEOM_CAPSULE);
+      if (!capbox && !segseg) return "geom pairs: capsule-box or sphere/capsule against sphere/capsule";
+      if (m.g_body[P.geom1] == m.g_body[P.geom2]) return "a geom pair must join two bodies";
+    }
     const int ns = P.geom2 >= 0 ? 1 : (m.g_type[P.geom1] == DMX_GEOM_SPHERE ? 1 : m.g_type[P.geom1] == DMX_GEOM_CAPSULE ? 2 : 8);
     m.p_g1[p] = P.geom1; m.p_g2[p] = P.geom2; m.p_condim[p] = P.condim; m.p_mu[p] = P.mu;
     m.p_slot0[p] = m.nslot; m.p_nslot[p] = ns; m.p_row0[p] = row;

@@ -220,6 +220,80 @@ __device__ __forceinline__ void box_sdf_vjp(const double* y, const double* h, do
 // cb[0..12] (cb[0] already holds the impedance part of rbar).  Accumulates the
 // pose cotangents of g1 (R1bar 9, c1bar 3) and g2 (R2bar 9, c2bar 3).
 // sv: the minimiser over the capsule axis that the forward evaluation found.
+// VJP of seg_seg (dmx_device.cuh): cb = cotangents of (r, pos, n, t1, t2);
+// b1 / b2 += pose cotangents (R 9, p 3) of geoms g1 / g2.  The free closest-
+// point parameters follow the reduced optimality conditions
+// F = (Du + s - c t, -Dv - c s + t) = 0: with lambda = A^-T (sbar, tbar),
+// A = [[1, -c], [-c, 1]] restricted to the free ones, theta gets -lambda^T dF/dtheta.
+static __device__ void seg_seg_vjp(const DevModel& m, const double* gR, const double* gp, int g1, int g2, double sv,
+                                   double tv, const double* cb, double* b1, double* b2) {
+  const double ra = m.g_size[g1][0];
+  const double La = seg_half(m, g1), Lb = seg_half(m, g2);
+  const double* R1 = gR + 9 * g1; const double* R2 = gR + 9 * g2;
+  const double* c1 = gp + 3 * g1; const double* c2 = gp + 3 * g2;
+  const double D[3] = {c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2]};
+  const double ua[3] = {R1[0], R1[3], R1[6]}, ub[3] = {R2[0], R2[3], R2[6]};
+  double d[3], n[3];
+  for (int i = 0; i < 3; ++i) d[i] = D[i] + sv * ua[i] - tv * ub[i];
+  const double rho = ::sqrt(dot3(d, d));
+  for (int i = 0; i < 3; ++i) n[i] = d[i] / rho;
+  const double r = rho - (ra + m.g_size[g2][0]), off = ra + 0.5 * r;
+  double ref[3] = {0, 0, 1};
+  if (fabs(n[2]) >= 0.5) { ref[0] = 1; ref[2] = 0; }
+  double t1r[3], t1[3];
+  cross3(n, ref, t1r);
+  const double il = rsqrt_t(dot3(t1r, t1r));
+  for (int i = 0; i < 3; ++i) t1[i] = t1r[i] * il;
+  // reverse: frame, position, distance
+  double nb[3] = {cb[4], cb[5], cb[6]}, t1b[3] = {cb[7], cb[8], cb[9]};
+  const double* t2b = cb + 10;
+  const double* posb = cb + 1;
+  acc_cross(t1, t2b, nb);                    // t2 = n x t1
+  acc_cross(t2b, n, t1b);
+  const double tt = dot3(t1, t1b);
+  double t1rb[3];
+  for (int i = 0; i < 3; ++i) t1rb[i] = il * (t1b[i] - t1[i] * tt);
+  acc_cross(ref, t1rb, nb);                  // t1r = n x ref
+  double c1b[3], uab[3], ubb[3] = {0, 0, 0}, Db[3];
+  double sb = dot3(ua, posb), tb = 0.0;      // pos = c1 + s ua - off n
+  for (int i = 0; i < 3; ++i) { c1b[i] = posb[i]; uab[i] = sv * posb[i]; nb[i] -= off * posb[i]; }
+  const double rhob = cb[0] - 0.5 * dot3(n, posb);
+  const double nn = dot3(nb, n);
+  double db[3];
+  for (int i = 0; i < 3; ++i) db[i] = (nb[i] - nn * n[i]) / rho + rhob * n[i];   // n = d / rho, rho = |d|
+  for (int i = 0; i < 3; ++i) {             // d = D + s ua - t ub
+    Db[i] = db[i];
+    uab[i] += sv * db[i];
+    ubb[i] -= tv * db[i];
+  }
+  sb += dot3(db, ua);
+  tb -= dot3(db, ub);
+  // implicit function of the free closest-point parameters
+  const bool sf = fabs(sv) < La, tf = fabs(tv) < Lb;
+  double ls = 0.0, lt = 0.0;
+  const double c = dot3(ua, ub);
+  if (sf && tf) {
+    const double det = 1.0 - c * c;
+    ls = (sb + c * tb) / det;
+    lt = (tb + c * sb) / det;
+  } else if (sf) {
+    ls = sb;
+  } else if (tf) {
+    lt = tb;
+  }
+  if (sf || tf) {
+    const double w = ls * tv + lt * sv;      // the c = ua . ub terms
+    for (int i = 0; i < 3; ++i) {
+      Db[i] += -ls * ua[i] + lt * ub[i];
+      uab[i] += -ls * D[i] + w * ub[i];
+      ubb[i] += lt * D[i] + w * ua[i];
+    }
+  }
+  b1[0] += uab[0]; b1[3] += uab[1]; b1[6] += uab[2];   // u = first column of R
+  b2[0] += ubb[0]; b2[3] += ubb[1]; b2[6] += ubb[2];
+  for (int i = 0; i < 3; ++i) { b1[9 + i] += c1b[i] + Db[i]; b2[9 + i] -= Db[i]; }
+}
+
 static __device__ void capsule_box_vjp(const DevModel& m, const double* gR, const double* gp, int g1, int g2,
                                        double sv, const double* cb, double* b1, double* b2) {
   const double rc = m.g_size[g1][0], Lh = m.g_size[g1][1];
@@ -473,7 +547,9 @@ __device__ void rhs_vjp(const Grp<G>& g, const DevModel& m, const Ws& w, const W
     double* b1 = sb; double* b2 = sb + 12;
     const int g1 = m.p_g1[p];
     if (m.p_g2[p] >= 0) {
-      capsule_box_vjp(m, gR, gp, g1, m.p_g2[p], w.at(L.csv)[s], cb, b1, b2);
+      const double* st = w.at(L.csv) + 2 * s;
+      if (m.g_type[m.p_g2[p]] == GEOM_BOX) capsule_box_vjp(m, gR, gp, g1, m.p_g2[p], st[0], cb, b1, b2);
+      else seg_seg_vjp(m, gR, gp, g1, m.p_g2[p], st[0], st[1], cb, b1, b2);
     } else {
       // r = pt_z - rad, pos = (pt_x, pt_y, pt_z - rad - r / 2); fixed frame
       const double ptb[3] = {cb[1], cb[2], cb[0] + 0.5 * cb[3]};

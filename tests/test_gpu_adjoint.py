@@ -11,6 +11,7 @@ import pytest
 
 from paper_2506_14186_gb300 import workloads as W
 from tests.conftest import rel_err
+from tests.test_gpu_rollout import BILLIARD_TRANS
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-6
@@ -205,17 +206,21 @@ TOL_VJP = 1e-10
 
 
 @pytest.mark.parametrize("cfd", [False, True])
-@pytest.mark.parametrize("name", ["ball", "box", "chain_cube", "quadruped"])
+@pytest.mark.parametrize("name", ["ball", "box", "chain_cube", "quadruped", "billiard", "capsules"])
 def test_rhs_vjp_matches_oracle_jacobian(dmx, orc_mod, name, cfd):
     """Right-hand-side VJP (dmx_eval_rhs_vjp) against the transposed Jacobian
     of the oracle's right-hand side (its derivative scalars) at states near
     contact (angular velocities included), for several lane counts."""
-    from tests.test_gpu_rollout import SEEDS, _random_states
+    from tests.test_gpu_rollout import SEEDS, _random_states, pair_states
     sc = W.SCENES[name](**CFD_OPT) if cfd else W.SCENES[name]()
     B = 48
     om = orc_mod.OracleModel(sc)
-    q, v, u = _random_states(sc, B, SEEDS[name] + 100, om)
-    rng = np.random.default_rng(SEEDS[name])
+    if name in ("billiard", "capsules"):          # states near the ball-ball / capsule contacts
+        _, q, v = pair_states(orc_mod, name, B, 31)
+        u = np.zeros((B, 1))
+    else:
+        q, v, u = _random_states(sc, B, SEEDS[name] + 100, om)
+    rng = np.random.default_rng(SEEDS.get(name, 40))
     gm = dmx.Model(sc)
     abar = rng.normal(size=(B, gm.nv))
     ref_q, ref_v, ref_u = [], [], []
@@ -223,7 +228,7 @@ def test_rhs_vjp_matches_oracle_jacobian(dmx, orc_mod, name, cfd):
         Jq, Jv, Ju = om.rhs_jacobian(q[e], v[e], u[e], cfd=cfd)
         ref_q.append(Jq.T @ abar[e]); ref_v.append(Jv.T @ abar[e]); ref_u.append(Ju.T @ abar[e])
     ref = [np.concatenate([ref_q[e], ref_v[e], ref_u[e]]) for e in range(B)]
-    for lanes in ((8, 16, 32) if name in ("chain_cube", "quadruped") else (2, 8, 32)):   # large workspaces need >= 8 lanes
+    for lanes in ((8, 16, 32) if name in ("chain_cube", "quadruped", "capsules") else (2, 8, 32)):   # large workspaces need >= 8 lanes
         qb, vb, ub, st = dmx.eval_rhs_vjp(gm, _dev(q.T), _dev(v.T), _dev(abar.T),
                                           u=_dev(u[:, :gm.nu].T) if gm.nu else None, cfd=cfd, lanes=lanes)
         assert np.all(st.cpu().numpy() == 0)
@@ -436,3 +441,29 @@ def test_parameter_gradient_matches_oracle(dmx, orc_mod, name, cfd):
     np.testing.assert_allclose(g["p_sum"], g["p_bar"].sum(axis=0), rtol=1e-12, atol=1e-12 * np.abs(g["p_bar"]).max())
     if name == "ball":
         assert np.all(g["p_bar"][:, 6] == 0.0)         # frictionless: mu enters no row
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name,cfd", [("billiard", False), ("billiard", True), ("capsules", False)])
+def test_pair_gradient(dmx, orc_mod, name, cfd, mode):
+    """Discrete adjoint through ball-ball and capsule contacts (closest-point
+    derivatives by the implicit-function theorem in the reverse kernel) in
+    every adjoint kernel, against the oracle along the GPU's steps; the
+    billiard also with the straight-through CFD gradient (contacts from
+    distance between the balls)."""
+    sc = W.SCENES[name](**CFD_OPT) if cfd else W.SCENES[name]()
+    inp = W.INPUTS[name](12)
+    m = dmx.Model(sc)
+    xT_bar = np.random.default_rng(23).normal(size=(12, m.nx))
+    if name == "billiard":
+        # a loss on the balls' positions and linear velocities; their
+        # orientations and spins are inert rounding residue (see the billiard
+        # trajectory test), and so are the cotangents of the initial ones
+        keep = np.zeros(m.nx, dtype=bool); keep[BILLIARD_TRANS] = True
+        xT_bar[:, ~keep] = 0.0
+    g = gpu_grad(dmx, m, inp, xT_bar, cfd=cfd, K=4, mode=mode)
+    assert np.all(g["status"] == 0)
+    o = oracle_grad(orc_mod, sc, inp, g, xT_bar, cfd=cfd)
+    if name == "billiard":
+        g["x0_bar"], o["x0_bar"] = g["x0_bar"][:, BILLIARD_TRANS], o["x0_bar"][:, BILLIARD_TRANS]
+    assert_grad(g, o)
