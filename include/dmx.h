@@ -52,7 +52,7 @@ typedef enum {
 /* per-environment status codes (status[B]) */
 enum {
   DMX_ENV_OK = 0,
-  DMX_ENV_MAX_STEPS = 1,      /* step attempts reached max_steps before T (App. D.1 budget) */
+  DMX_ENV_MAX_STEPS = 1,      /* step attempts reached max_steps before T (App. D budget) */
   DMX_ENV_H_UNDERFLOW = 2,    /* step size fell below 1e-12 s */
   DMX_ENV_NONFINITE = 3,      /* non-finite initial state */
   DMX_ENV_SOLVER_NOCONV = 4,  /* constraint Newton solve exceeded 50 iterations */
@@ -199,7 +199,7 @@ dmx_status dmx_rollout_grad_params(dmx_model* m, dmx_tape* tape, int32_t cfd, co
                                    const double* xb_bar, double* x0_bar, double* ctrl_bar, double* p_bar,
                                    double* p_bar_sum, void* stream);
 /* Optimize-then-discretize gradient (App. C.2, Eq. adjoint-equations:
- * BacksolveAdjoint; with cfd = 1 the straight-through variant of App. C.3).
+ * BacksolveAdjoint; with cfd = 1 the straight-through variant of App. C.4).
  * The continuous adjoint a_x' = -a_x^T df/dx, a_u' = -a_x^T df/du of
  * x' = f(x, u) = (G(q) v, F(q, v, u)) is integrated backward from x(T)
  * together with the state itself, with its own adaptive steps (the scheme

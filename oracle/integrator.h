@@ -465,7 +465,7 @@ inline Result rollout_grad(const Model& m, const double* x0, const double* ctrl,
 
 // ------------------------------------------------------------------ optimize-then-discretize
 // Continuous adjoint (App. C.2 "Optimize-then-discretize", Eq. adjoint-
-// equations; the straight-through variant of App. C.3): with x = (q, v),
+// equations; the straight-through variant of App. C.4): with x = (q, v),
 // x' = f(x, u) = (G(q) v, F(q, v, u)) and a_x(T) = dL/dx(T),
 //   a_x' = -a_x^T df/dx,   a_u' = -a_x^T df/du  (per control interval),
 // integrated BACKWARD from T together with the state itself (backsolve: the

@@ -1,5 +1,5 @@
 // Optimize-then-discretize gradient (App. C.2, Eq. adjoint-equations:
-// BacksolveAdjoint), with the straight-through CFD variant of App. C.3.
+// BacksolveAdjoint), with the straight-through CFD variant of App. C.4.
 //
 // With x = (q, v), x' = f(x, u) = (G(q) v, F(q, v, u)) and a_x(T) = dL/dx(T),
 // the continuous adjoint a_x' = -a_x^T df/dx, a_u' = -a_x^T df/du is integrated

@@ -24,7 +24,7 @@ Scenes are plain dicts:
 
 Solver parameters follow the paper: solref time constant 0.002 s with damping
 ratio 1 (the stiff setting), solimp (0, 0.95, 0.001, 0.5, 2) (Sec. 3 object
-tosses, App. D.1), solimp-CFD tuple order (d_c, d_0, w_c, m_c, p_c) (Sec. 4).
+tosses, App. E.1), solimp-CFD tuple order (d_c, d_0, w_c, m_c, p_c) (Sec. 4).
 """
 
 from __future__ import annotations
@@ -37,7 +37,7 @@ GRAVITY = (0.0, 0.0, -9.81)
 SOLREF = (0.002, 1.0)
 SOLIMP = (0.0, 0.95, 0.001, 0.5, 2.0)
 SOLIMP_CFD = (0.0, 0.0, 0.05, 1.0, 4.0)
-# Contacts from distance (Sec. 4, App. D.3): contact impedance starting at
+# Contacts from distance (Sec. 4, App. E.3): contact impedance starting at
 # d_o = 0.1 and the CFD spline (d_c, d_0, w_c, m_c, p_c) that continues it
 # from r = 0 up to the taper width w_c (0.05 m for the 0.1 m cubes here).
 CFD_SOLIMP = (0.1, 0.95, 0.001, 0.5, 2.0)
@@ -251,7 +251,7 @@ def quadruped_inputs(B=8192, seed=1004):
 
 def billiard_scene(radius=0.05, mass=0.2, condim=1, mu=0.0, **opt):
     """Two free balls and no gravity, the ball-ball contact only (the billiard
-    toy of Sec. 4 and App. C.3 with the table contacts and gravity off)."""
+    toy of Sec. 4 and App. C.4 with the table contacts and gravity off)."""
     opt.setdefault("gravity", (0.0, 0.0, 0.0))
     bodies = [_free_body(mass, sphere_inertia(mass, radius)), _free_body(mass, sphere_inertia(mass, radius))]
     geoms = [_geom("sphere", 0, [radius]), _geom("sphere", 1, [radius])]

@@ -80,7 +80,7 @@ MODES = ["reverse", "recompute", "tangent"]
 @pytest.mark.parametrize("cfd", [False, True])
 def test_ball_gradient(dmx, orc_mod, cfd, mode):
     """Bouncing balls (full batch, T = 1 s): gradient of the final height and
-    velocity w.r.t. the whole initial state; with CFD parameters of App. D.3."""
+    velocity w.r.t. the whole initial state; with CFD parameters of App. E.3."""
     sc = W.ball_scene(**CFD_OPT) if cfd else W.ball_scene()
     inp = W.ball_inputs(16)
     rng = np.random.default_rng(0)

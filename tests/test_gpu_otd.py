@@ -11,7 +11,7 @@ by 1e-9 (arm) to 1e-4 and, for grazing shots, O(1) (billiard) when x0 moves
 by 1e-15 relative, and its step counts by ~10%.  There each environment's GPU
 gradient must lie within 10x that measured spread of the oracle's (at least
 1e-9), and most environments must be well conditioned so that the bar bites:
-billiard shots with and without the straight-through CFD adjoint (App. C.3),
+billiard shots with and without the straight-through CFD adjoint (App. C.4),
 arm controls with interval-boundary cotangents."""
 
 import numpy as np

@@ -517,7 +517,7 @@ def test_pair_rhs_matches_oracle(dmx, orc_mod, name, cfd):
 # estimate are zero, so the hit cancels (both sides tunnel), but its kick
 # puts the later stage states hundreds of metres from the origin, where the
 # cancelling spatial-velocity terms leave 1e-7 rad/s^2 of spin residue that
-# differs with the summation order (Sec. 4 and App. C.3 discuss the adaptive
+# differs with the summation order (Sec. 4 and App. C.4 discuss the adaptive
 # solver seeing an interaction only at its stage states).
 BILLIARD_TRANS = [0, 1, 2, 7, 8, 9, 14, 15, 16, 20, 21, 22]
 

@@ -1,7 +1,7 @@
 """Pins of the oracle's discrete adjoint (discretize-then-optimize over the
 accepted steps) and of the straight-through CFD gradient: closed forms,
 frozen-step central differences, and the properties the paper states for the
-straight-through estimator (Sec. 4, App. C.3)."""
+straight-through estimator (Sec. 4, App. C.4)."""
 
 import numpy as np
 import pytest

@@ -1,7 +1,7 @@
 """Pins of the oracle's optimize-then-discretize gradient (App. C.2, Eq.
 adjoint-equations: the continuous adjoint integrated backward together with
 the state, BacksolveAdjoint) and of its straight-through variant with the
-CFD right-hand side (App. C.3): closed forms of the continuous gradient
+CFD right-hand side (App. C.4): closed forms of the continuous gradient
 (damped hinge, ballistic flight), agreement with central differences of the
 tight-tolerance continuous map (top, billiard hits, arm controls with
 interval-boundary cotangents), convergence with the tolerance, and the
@@ -114,7 +114,7 @@ def test_billiard_miss_straight_through(orc):
     """A miss by 1 cm over 0.4 s: the plain gradient of the target ball's
     final x w.r.t. the cue ball's state is zero (no contact ever), the
     straight-through OTD gradient with contacts from distance is not, and
-    points towards a hit (App. C.3, Sec. 4): moving the cue ball towards the
+    points towards a hit (App. C.4, Sec. 4): moving the cue ball towards the
     target's side, or the target towards the cue line, raises the loss.
     (An adaptive solver sees the interaction only at its stage states: over
     0.5 s the backward steps grow past the 0.1 s window of the approach, as

@@ -1,5 +1,5 @@
 """Pins of the oracle's sphere / capsule pair contacts (the billiard of
-Sec. 4 and App. C.3; capsule pairs of App. C.1): the signed distance and
+Sec. 4 and App. C.4; capsule pairs of App. C.1): the signed distance and
 normal against brute-force minimisation over the two segments, closed forms
 (two spheres, parallel capsules), the contact frame, the right-hand side's
 Jacobian against central differences at colliding states, and conservation
