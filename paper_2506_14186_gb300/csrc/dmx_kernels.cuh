@@ -195,15 +195,27 @@ __global__ void __launch_bounds__(32) k_rollout_persistent(RolloutParams P) {
   const DevModel& m = *P.model;
   Grp<G> g;
   const Ws w = group_workspace<G>(P, &sL);
+  // One loop level: every pass makes one step attempt of the group's
+  // environment, taking the next environment first when the group has none.
+  // The groups of a warp thus meet at every attempt; with a per-environment
+  // inner loop, a group whose environment finished would wait at that loop's
+  // exit (where the warp reconverges) for the warp's slowest environment.
+  EnvState s;
+  int env = -1;
   for (;;) {
-    int env = 0;
-    if (g.lane == 0) env = atomicAdd(P.queue, 1);
-    env = g.bcast(env, 0);
-    if (env >= P.B) break;
-    EnvState s;
-    env_start(g, m, w, P, env, s);
-    while (!s.done) env_attempt(g, m, w, P, env, s);
-    env_finish(g, m, w, P, env, s);
+    if (env < 0) {
+      int e = 0;
+      if (g.lane == 0) e = atomicAdd(P.queue, 1);
+      e = g.bcast(e, 0);
+      if (e >= P.B) break;
+      env = e;
+      env_start(g, m, w, P, env, s);
+    }
+    if (!s.done) env_attempt(g, m, w, P, env, s);
+    if (s.done) {
+      env_finish(g, m, w, P, env, s);
+      env = -1;
+    }
   }
 }
 
