@@ -41,10 +41,10 @@ WORKLOAD = {"workload": "box_push", "B": 4096, "T_s": 1.0, "rtol": 1e-6, "atol":
 FLOP_PER_STEP = 28910.0
 FLOP_PER_STEP_SEARCH = 41112.0
 # Arm pushing the cube (T = 2 s, 50 intervals): forward 148,516 per accepted
-# step; adjoint 489,196 per accepted step (every step once with one tangent in
+# step; adjoint 492,619 per accepted step (every step once with one tangent in
 # the counting derivative scalar: primal recompute + linearised step).
 ARM_FLOP_PER_STEP = 148516.0
-ARM_ADJ_FLOP_PER_STEP = 489196.0
+ARM_ADJ_FLOP_PER_STEP = 492619.0
 # FP64 peak derived from the unit counts and clock (152 SMs x 4 FP64 flop/clk
 # x 2070 MHz), reported beside the peak measured in the run.
 FP64_PEAK_DERIVED_GFLOPS = 152 * 4 * 2.070

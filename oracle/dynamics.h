@@ -17,6 +17,7 @@
 //   Sec. 4 CFD                 d(r) continued for r > 0 by the solimp-CFD
 //                              spline; ReLU of a_ref replaced by a softplus
 //   Sec. 5.1, App. E.2         contact parameters (solref, solimp, friction)
+//                              and body masses
 //                              as differentiable model parameters
 // Readings where the paper is silent are listed in the design notes of the
 // repository (integrator, spline form, A_hat, solver stop rule, capsule-box).
@@ -86,6 +87,31 @@ template <class S> struct Kin {
   std::vector<V3<S>> gp;
 };
 
+// Model parameters that the adjoint differentiates (the parameters of the
+// system identification of Sec. 5.1 and App. E.2): solref (t_c, phi_d),
+// solimp (d_o, d_w, width, midpoint), the friction coefficient of every pair,
+// then the mass of every body (its rotational inertia scaled in proportion:
+// equal density, fixed shape).  par<S>(k, v) is the value v of parameter k;
+// in the derivative scalar it carries a unit tangent when k is the direction
+// being differentiated (g_pdir), else none.
+enum { PAR_TC = 0, PAR_DAMP = 1, PAR_DO = 2, PAR_DW = 3, PAR_WIDTH = 4, PAR_MID = 5, PAR_MU0 = 6 };
+extern thread_local int g_pdir;
+template <class S> inline S par(int, double v) { return S(v); }
+template <> inline Dual<double> par<Dual<double>>(int k, double v) { return Dual<double>(v, g_pdir == k ? 1.0 : 0.0); }
+inline int par_mass(const Model& m, int b) { return PAR_MU0 + (int)m.pair.size() + b; }
+inline int n_params(const Model& m) { return par_mass(m, (int)m.body.size()); }
+// Whether S carries the tangent of body b's mass in this evaluation.
+template <class S> inline bool mass_direction(const Model&, int) { return false; }
+template <> inline bool mass_direction<Dual<double>>(const Model& m, int b) { return g_pdir == par_mass(m, b); }
+
+// A_hat of pair P (the sum of its bodies' inverse weights); the derivative
+// scalar carries its derivative with respect to the body mass g_pdir points at.
+template <class S> inline S pair_invw(const Model& m, const Pair& P) { return S(P.invw); }
+template <> inline Dual<double> pair_invw<Dual<double>>(const Model& m, const Pair& P) {
+  const int c = g_pdir - par_mass(m, 0);
+  return Dual<double>(P.invw, (c >= 0 && c < (int)P.dinvw.size()) ? P.dinvw[c] : 0.0);
+}
+
 template <class S> void kinematics(const Model& m, const S* q, Kin<S>& k) {
   const int nb = (int)m.body.size();
   k.R.resize(nb); k.p.resize(nb); k.c.resize(nb); k.Iw.resize(nb);
@@ -108,6 +134,10 @@ template <class S> void kinematics(const Model& m, const S* q, Kin<S>& k) {
     M3<S> RI;
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) RI[3 * i + j] = k.R[b][3 * i + j] * B.inertia[j];
+    if (mass_direction<S>(m, b)) {                      // inertia proportional to the mass
+      const S scale = par<S>(par_mass(m, b), B.mass) / B.mass;
+      for (int i = 0; i < 9; ++i) RI[i] = RI[i] * scale;
+    }
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j)
         k.Iw[b][3 * i + j] = RI[3 * i] * k.R[b][3 * j] + RI[3 * i + 1] * k.R[b][3 * j + 1] + RI[3 * i + 2] * k.R[b][3 * j + 2];
@@ -139,8 +169,7 @@ template <class S> void kinematics(const Model& m, const S* q, Kin<S>& k) {
 }
 
 // Spatial inertia (6x6, ordering omega; v, reference point = world origin).
-template <class S> std::array<S, 36> spatial_inertia(const Model& m, const Kin<S>& k, int b) {
-  const double mass = m.body[b].mass;
+template <class S, class Ms> std::array<S, 36> spatial_inertia_of(const Kin<S>& k, int b, const Ms& mass) {
   const V3<S>& c = k.c[b];
   M3<S> cx = {S(0.0), -c[2], c[1], c[2], S(0.0), -c[0], -c[1], c[0], S(0.0)};
   std::array<S, 36> I;
@@ -154,6 +183,11 @@ template <class S> std::array<S, 36> spatial_inertia(const Model& m, const Kin<S
       I[6 * (3 + i) + 3 + j] = (i == j) ? S(mass) : S(0.0);
     }
   return I;
+}
+template <class S> std::array<S, 36> spatial_inertia(const Model& m, const Kin<S>& k, int b) {
+  // the mass as a derivative scalar only when it is the direction differentiated
+  if (mass_direction<S>(m, b)) return spatial_inertia_of(k, b, par<S>(par_mass(m, b), m.body[b].mass));
+  return spatial_inertia_of(k, b, m.body[b].mass);
 }
 template <class S> std::array<S, 6> mat6vec(const std::array<S, 36>& A, const std::array<S, 6>& x) {
   std::array<S, 6> y;
@@ -465,17 +499,6 @@ template <class S> void contacts(const Model& m, const Kin<S>& k, std::vector<Co
 }
 
 // ------------------------------------------------------------------ impedance
-// Model parameters that the adjoint differentiates (the soft-contact
-// parameters of Sec. 2.1 tuned in the system identification of Sec. 5.1 and
-// App. E.2): solref (t_c, phi_d), solimp (d_o, d_w, width, midpoint) and the
-// friction coefficient of every pair.  par<S>(k, v) is the value v of
-// parameter k; in the derivative scalar it carries a unit tangent when k is
-// the direction being differentiated (g_pdir), else none.
-enum { PAR_TC = 0, PAR_DAMP = 1, PAR_DO = 2, PAR_DW = 3, PAR_WIDTH = 4, PAR_MID = 5, PAR_MU0 = 6 };
-extern thread_local int g_pdir;
-template <class S> inline S par(int, double v) { return S(v); }
-template <> inline Dual<double> par<Dual<double>>(int k, double v) { return Dual<double>(v, g_pdir == k ? 1.0 : 0.0); }
-inline int n_params(const Model& m) { return PAR_MU0 + (int)m.pair.size(); }
 
 // Polynomial spline of the solimp shape (midpoint mid, power pw) on x in [0,1].
 template <class S, class M> S spline_shape(const S& x, const M& mid, double pw) {
@@ -500,9 +523,18 @@ template <class S> S impedance(const Model& m, const S& r, bool cfd) {
   const S d_o = par<S>(PAR_DO, m.solimp[0]), d_w = par<S>(PAR_DW, m.solimp[1]), w = par<S>(PAR_WIDTH, m.solimp[2]);
   const S mid = par<S>(PAR_MID, m.solimp[3]);
   const double pw = m.solimp[4];
+  S span, den_lo, den_hi;                  // model constants
+  {
+    FlopsPaused fp;
+    span = d_w - d_o;
+    den_lo = pow(mid, pw - 1.0);
+    den_hi = pow(1.0 - mid, pw - 1.0);
+  }
   S x = fabs(r) / w;
   if (val(x) > 1.0) x = S(1.0);
-  return clamp_imp(d_o + (d_w - d_o) * spline_shape(x, mid, pw));
+  // the solimp spline (spline_shape) with its midpoint denominators folded
+  const S y = (val(x) <= val(mid) && val(mid) > 0) ? pow(x, pw) / den_lo : 1.0 - pow(1.0 - x, pw) / den_hi;
+  return clamp_imp(d_o + span * y);
 }
 template <class S> S softplus(const S& x) {
   if (val(x) > 0) return x + log1p(exp(-x));
@@ -529,7 +561,12 @@ void make_rows(const Model& m, const Kin<S>& k, const std::vector<Contact<S>>& c
   const int nv = m.nv;
   R.nr = 0; R.J.clear(); R.aref.clear(); R.D.clear(); R.slot.clear();
   const S tc = par<S>(PAR_TC, m.solref[0]), damp = par<S>(PAR_DAMP, m.solref[1]), dw = par<S>(PAR_DW, m.solimp[1]);
-  const S bcoef = 2.0 / (dw * tc), kcoef = 1.0 / (dw * dw * tc * tc * damp * damp);
+  S bcoef, kcoef;                          // model constants
+  {
+    FlopsPaused fp;
+    bcoef = 2.0 / (dw * tc);
+    kcoef = 1.0 / (dw * dw * tc * tc * damp * damp);
+  }
   for (int si = 0; si < (int)ct.size(); ++si) {
     const Contact<S>& c = ct[si];
     const bool incl = cfd ? (val(c.r) < m.cfd[2]) : (val(c.r) < 0);
@@ -545,7 +582,11 @@ void make_rows(const Model& m, const Kin<S>& k, const std::vector<Contact<S>>& c
     S pterm = cfd ? kcoef * d * (m.softplus_s * softplus(-c.r / m.softplus_s)) : -(kcoef * d * c.r);
     const int nrow = P.condim == 1 ? 1 : 4;
     const S mu = par<S>(PAR_MU0 + c.pair, P.mu);
-    const S Ahat = P.condim == 1 ? S(P.invw) : P.invw * (1.0 + mu * mu);
+    S Ahat;                                // model constant
+    {
+      FlopsPaused fp;
+      Ahat = P.condim == 1 ? pair_invw<S>(m, P) : pair_invw<S>(m, P) * (1.0 + mu * mu);
+    }
     S Dv = d / (Ahat * (1.0 - d));
     for (int e = 0; e < nrow; ++e) {
       S sgn = (e & 1) ? -mu : mu;
@@ -592,6 +633,36 @@ template <class S> void chol_solve(const std::vector<S>& L, int n, std::vector<S
     for (int k = i + 1; k < n; ++k) t = t - L[(size_t)k * n + i] * x[k];
     x[i] = t / L[(size_t)i * n + i];
   }
+}
+
+// ------------------------------------------------------------------ A_hat
+// Translational inverse weight of every body at the reference pose,
+// trace(Jc M(q0)^-1 Jc^T) / 3 (Jc: the body's COM point Jacobian), the
+// reading of "an approximation to diag(J M^-1 J^T)" (Sec. 2.1).  In the
+// derivative scalar with g_pdir on a body mass it carries the derivative of
+// that model constant with respect to the mass.  Returns false if M(q0) is
+// not positive definite.
+template <class S> bool body_inverse_weights(const Model& m, std::vector<S>& invw) {
+  const int nb = (int)m.body.size();
+  std::vector<S> q(m.qpos0.begin(), m.qpos0.end());
+  Kin<S> k;
+  kinematics(m, q.data(), k);
+  std::vector<S> M;
+  crba(m, k, M);
+  if (!cholesky(M, m.nv)) return false;
+  invw.assign(nb, S(0.0));
+  for (int b = 0; b < nb; ++b) {
+    S tr = S(0.0);
+    for (int ax = 0; ax < 3; ++ax) {
+      std::vector<S> col(m.nv);
+      for (int i = 0; i < m.nv; ++i) col[i] = dof_point_vel(m, k, i, b, k.c[b])[ax];
+      std::vector<S> x = col;
+      chol_solve(M, m.nv, x);
+      for (int i = 0; i < m.nv; ++i) tr = tr + col[i] * x[i];
+    }
+    invw[b] = tr / 3.0;
+  }
+  return true;
 }
 
 // ------------------------------------------------------------------ solver

@@ -97,29 +97,23 @@ std::string build_model(Model& m, const double* body, int nbody, const double* g
   m.dof_body.resize(m.nv);
   for (int b = 0; b < nbody; ++b)
     for (int d = 0; d < m.body[b].nv; ++d) m.dof_body[m.body[b].vadr + d] = b;
-  // translational inverse weight of each body at qpos0: trace(Jc M^-1 Jc^T) / 3
-  Kin<double> k;
-  kinematics(m, m.qpos0.data(), k);
-  std::vector<double> M;
-  crba(m, k, M);
-  std::vector<double> L = M;
-  if (!cholesky(L, m.nv)) return "mass matrix at qpos0 is not positive definite";
-  m.body_invw.assign(nbody, 0.0);
-  for (int b = 0; b < nbody; ++b) {
-    double tr = 0;
-    for (int ax = 0; ax < 3; ++ax) {
-      std::vector<double> col(m.nv);
-      for (int i = 0; i < m.nv; ++i) col[i] = dof_point_vel(m, k, i, b, k.c[b])[ax];
-      std::vector<double> x = col;
-      chol_solve(L, m.nv, x);
-      for (int i = 0; i < m.nv; ++i) tr += col[i] * x[i];
-    }
-    m.body_invw[b] = tr / 3.0;
+  // translational inverse weight of each body at qpos0: trace(Jc M^-1 Jc^T) / 3,
+  // and its derivative with respect to every body mass (one derivative pass each)
+  if (!body_inverse_weights(m, m.body_invw)) return "mass matrix at qpos0 is not positive definite";
+  std::vector<std::vector<double>> dinv(nbody, std::vector<double>(nbody, 0.0));
+  for (int c = 0; c < nbody; ++c) {
+    g_pdir = par_mass(m, c);
+    std::vector<Dual<double>> w;
+    body_inverse_weights(m, w);
+    for (int b = 0; b < nbody; ++b) dinv[c][b] = w[b].d;
   }
+  g_pdir = -1;
   for (Pair& P : m.pair) {
     const int bA = m.geom[P.g1].body;
     const int bB = P.g2 >= 0 ? m.geom[P.g2].body : -1;
     P.invw = m.body_invw[bA] + (bB >= 0 ? m.body_invw[bB] : 0.0);
+    P.dinvw.assign(nbody, 0.0);
+    for (int c = 0; c < nbody; ++c) P.dinvw[c] = dinv[c][bA] + (bB >= 0 ? dinv[c][bB] : 0.0);
   }
   return "";
 }

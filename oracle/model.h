@@ -39,6 +39,7 @@ struct Pair {
   double mu;
   int nslot, slot0, row0;   // contact slots and first constraint row of this pair
   double invw;              // approximate diag(J M^-1 J^T) for the normal row
+  std::vector<double> dinvw; // its derivative with respect to the mass of each body
 };
 struct Act {
   int type, body;

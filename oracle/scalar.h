@@ -21,6 +21,15 @@ extern thread_local std::int64_t g_flops;
 // While > 0, operations are not counted (used to leave the constraint solver's
 // active-set search out of the algorithmic count; see solve_constraints).
 extern thread_local int g_flops_paused;
+// While alive, operations are not counted: arithmetic on model constants
+// alone (values that a compiled model holds precomputed), which is not
+// per-step work of the method.
+struct FlopsPaused {
+  FlopsPaused() { ++g_flops_paused; }
+  ~FlopsPaused() { --g_flops_paused; }
+  FlopsPaused(const FlopsPaused&) = delete;
+  FlopsPaused& operator=(const FlopsPaused&) = delete;
+};
 // 1: count the active-set search from the unconstrained acceleration too.
 extern thread_local int g_count_search;
 

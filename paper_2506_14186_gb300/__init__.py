@@ -202,7 +202,7 @@ class Model:
 
     def params(self):
         """Model parameters of rollout_grad_params: numpy array of t_c, phi_d,
-        d_o, d_w, width, midpoint, then mu of every pair."""
+        d_o, d_w, width, midpoint, mu of every pair, then the mass of every body."""
         n = c_i32()
         _check(lib().dmx_model_params(self.h, ctypes.byref(n), None))
         vals = (c_f64 * n.value)()

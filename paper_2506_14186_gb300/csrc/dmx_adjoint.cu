@@ -234,6 +234,57 @@ __global__ void __launch_bounds__(256) k_row_sums(const double* x, int B, double
     out[blockIdx.x] = s;
   }
 }
+// Derivative of every body's translational inverse weight at qpos0 (the
+// A_hat model constant, trace(Jc M^-1 Jc^T) / 3) with respect to the
+// model parameter pdir (a body mass): the set-up computation of
+// k_body_invweight in derivative scalars, one environment, one lane, the
+// workspace in device memory (ws: nd derivative scalars then ni ints).
+__global__ void k_body_invweight_tangent(const DevModel* mp, const double* qpos0, int rcap, int pdir, Dual* ws,
+                                         Dual* scratch, double* dinvw) {
+  __shared__ Layout sL;
+  const DevModel& m = *mp;
+  if (threadIdx.x != 0) return;
+  sL = make_layout(m, rcap);
+  Grp<1> g;
+  WsT<Dual> w{ws, reinterpret_cast<int*>(ws + sL.nd), &sL};
+  w.pdir = pdir;
+  Dual* q = scratch;
+  Dual* col = scratch + m.nq;
+  Dual* x = col + m.nv;
+  for (int i = 0; i < m.nq; ++i) q[i] = Dual(qpos0[i], 0.0);
+  kinematics(g, m, w, q);
+  crba(g, m, w);
+  Dual* H = w.at(sL.H); const Dual* M = w.at(sL.M);
+  for (int i = 0; i < m.nv * m.nv; ++i) H[i] = M[i];
+  cholesky(g, H, w.at(sL.tmp2), m.nv);
+  const Dual* S = w.at(sL.sd); const Dual* C = w.at(sL.com);
+  for (int b = 0; b < m.nbody; ++b) {
+    Dual tr = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+      for (int i = 0; i < m.nv; ++i) {
+        const bool moves = (m.b_anc[b] >> m.dof_body[i]) & 1u;
+        Dual pv[3] = {0.0, 0.0, 0.0};
+        if (moves) {
+          cross3(S + 6 * i, C + 3 * b, pv);
+          pv[0] += S[6 * i + 3]; pv[1] += S[6 * i + 4]; pv[2] += S[6 * i + 5];
+        }
+        col[i] = pv[ax];
+        x[i] = pv[ax];
+      }
+      chol_solve(g, H, w.at(sL.tmp2), x, m.nv);
+      for (int i = 0; i < m.nv; ++i) tr += col[i] * x[i];
+    }
+    dinvw[b] = (tr / 3.0).d;
+  }
+}
+
+cudaError_t launch_body_invweight_tangent(const DevModel* m, const double* qpos0, int rcap, int pdir, void* ws,
+                                          void* scratch, double* dinvw, cudaStream_t st) {
+  k_body_invweight_tangent<<<1, 32, 0, st>>>(m, qpos0, rcap, pdir, static_cast<Dual*>(ws),
+                                             static_cast<Dual*>(scratch), dinvw);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_row_sums(const double* x, int n, int B, double* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_row_sums<<<n, 256, 0, st>>>(x, B, out);

@@ -60,6 +60,11 @@ __host__ __device__ inline int rev_row_doubles(const DevModel& m) { return m.nq 
 cudaError_t launch_adjoint(const AdjParams& P, int blocks, cudaStream_t st);
 // out[k] = sum over e of x[k][e] (k < n, e < B): one block per row, fixed order.
 cudaError_t launch_row_sums(const double* x, int n, int B, double* out, cudaStream_t st);
+// d (translational inverse weight of every body at qpos0) / d (parameter
+// pdir) into dinvw[nbody]; ws: Layout(rcap).nd derivative scalars (16 bytes)
+// + ni ints of device memory, scratch: nq + 2 nv derivative scalars.
+cudaError_t launch_body_invweight_tangent(const DevModel* m, const double* qpos0, int rcap, int pdir, void* ws,
+                                          void* scratch, double* dinvw, cudaStream_t st);
 // reverse-mode kernel, G lanes per environment (G = 2, 4, 8, 16, 32)
 cudaError_t launch_adjoint_rev(int G, const AdjParams& P, int blocks, int threads, size_t smem, cudaStream_t st);
 int adjoint_rev_occupancy(int G, int threads, size_t smem);

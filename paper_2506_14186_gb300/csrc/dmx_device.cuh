@@ -213,12 +213,17 @@ struct WsT {
 
 // Value v of model parameter k; a derivative scalar carries a unit tangent
 // when k is the direction pdir being differentiated.
+// Parameter order: PAR_TC .. PAR_MID, mu of every pair, then the mass of
+// every body (rotational inertia scaled in proportion).
+__device__ __forceinline__ int par_mass(const DevModel& m, int b) { return PAR_MU0 + m.npair + b; }
 template <class T>
 struct Par {
   static __device__ __forceinline__ double get(int, int, double v) { return v; }
   static __device__ __forceinline__ double bcoef(const DevModel& m, int) { return m.bcoef; }
   static __device__ __forceinline__ double kcoef(const DevModel& m, int) { return m.kcoef; }
+  static __device__ __forceinline__ double ahat(const DevModel& m, int, int p) { return m.p_ahat[p]; }
   static __device__ __forceinline__ double ahat_edge(const DevModel& m, int, int p) { return m.p_ahat_edge[p]; }
+  static __device__ __forceinline__ bool mass_dir(const DevModel&, int, int) { return false; }
 };
 template <>
 struct Par<Dual> {
@@ -235,10 +240,21 @@ struct Par<Dual> {
                  : pdir == PAR_DAMP ? -2.0 * k / m.solref[1]
                  : pdir == PAR_DW ? -2.0 * k / m.solimp[1] : 0.0);
   }
+  // d A_hat / d theta: non-zero for the body masses only
+  static __device__ __forceinline__ double dahat(const DevModel& m, int pdir, int p) {
+    const int b = pdir - par_mass(m, 0);
+    return (b >= 0 && b < m.nbody) ? m.p_dahat[p][b] : 0.0;
+  }
+  static __device__ __forceinline__ Dual ahat(const DevModel& m, int pdir, int p) {
+    return Dual(m.p_ahat[p], dahat(m, pdir, p));
+  }
   // A_hat (1 + mu^2) of a pyramid-edge row
   static __device__ __forceinline__ Dual ahat_edge(const DevModel& m, int pdir, int p) {
-    return Dual(m.p_ahat_edge[p], pdir == PAR_MU0 + p ? 2.0 * m.p_mu[p] * m.p_ahat[p] : 0.0);
+    const double mu = m.p_mu[p];
+    return Dual(m.p_ahat_edge[p], (pdir == PAR_MU0 + p ? 2.0 * mu * m.p_ahat[p] : 0.0) +
+                                      dahat(m, pdir, p) * (1.0 + mu * mu));
   }
+  static __device__ __forceinline__ bool mass_dir(const DevModel& m, int pdir, int b) { return pdir == par_mass(m, b); }
 };
 using Ws = WsT<double>;
 
@@ -385,7 +401,7 @@ __device__ void kinematics(const Grp<G>& g, const DevModel& m, const WsT<T>& w, 
   // one entry per task
   for (int k = g.lane; k < 10 * nb; k += G) {
     const int b = k / 10, e = k - 10 * b;
-    const double ms = m.b_mass[b];
+    const auto ms = Par<T>::get(w.pdir, par_mass(m, b), m.b_mass[b]);
     const T* c = C + 3 * b;
     T v;
     if (e == 0) v = ms;
@@ -396,6 +412,7 @@ __device__ void kinematics(const Grp<G>& g, const DevModel& m, const WsT<T>& w, 
       const T* Rb = R + 9 * b;
       const double* In = m.b_inertia[b];
       v = Rb[3 * i] * Rb[3 * j] * In[0] + Rb[3 * i + 1] * Rb[3 * j + 1] * In[1] + Rb[3 * i + 2] * Rb[3 * j + 2] * In[2];
+      if (Par<T>::mass_dir(m, w.pdir, b)) v = v * (ms / m.b_mass[b]);   // inertia proportional to the mass
       const T cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
       v += ms * ((i == j ? cc : T(0.0)) - c[i] * c[j]);
     }
@@ -823,7 +840,7 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, boo
       const T r = ct[0];
       const T d = impedance(m, r, cfd, w.pdir);
       const int pr = m.s_pair[s];
-      const auto ahat = m.p_condim[pr] == 1 ? Par<T>::get(-1, 0, m.p_ahat[pr]) : Par<T>::ahat_edge(m, w.pdir, pr);
+      const auto ahat = m.p_condim[pr] == 1 ? Par<T>::ahat(m, w.pdir, pr) : Par<T>::ahat_edge(m, w.pdir, pr);
       const auto kc = Par<T>::kcoef(m, w.pdir);
       ct[13] = d;
       ct[14] = cfd ? kc * d * (m.softplus * softplus(-r / m.softplus)) : -(kc * d * r);

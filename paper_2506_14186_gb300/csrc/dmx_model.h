@@ -64,6 +64,7 @@ struct DevModel {
   // pairs and slots
   int p_g1[MAXP], p_g2[MAXP], p_condim[MAXP], p_slot0[MAXP], p_nslot[MAXP], p_row0[MAXP];
   double p_mu[MAXP], p_ahat[MAXP], p_ahat_edge[MAXP];
+  double p_dahat[MAXP][MAXB];        // d A_hat / d (mass of body b), the model constant's mass derivative
   int s_pair[MAXS], s_idx[MAXS];
   int s_barofs[MAXS], nslotbar;      // adjoint: offset / total of the per-slot pose cotangents
                                      // (12 doubles for a plane slot, 24 for a geom pair)

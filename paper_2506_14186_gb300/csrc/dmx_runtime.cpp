@@ -218,6 +218,20 @@ extern "C" dmx_status dmx_create_model(const dmx_model_desc* desc, dmx_model** o
   CK(launch_body_invweight(m->dev, dq0, dinv, dscr, m->rcap, model_smem_bytes(m, 1), 0));
   double invw[MAXB];
   CK(cudaMemcpy(invw, dinv, sizeof(double) * m->host.nbody, cudaMemcpyDeviceToHost));
+  // derivative of the inverse weights with respect to every body mass (the
+  // model-parameter gradient carries A_hat's dependence on the masses)
+  double dinvw[MAXB][MAXB] = {};
+  {
+    void *ws = nullptr, *tscr = nullptr;
+    const size_t wsb = (size_t)m->L.nd * 16 + (size_t)m->L.ni * 4 + 16;
+    CK(cudaMalloc(&ws, wsb));
+    CK(cudaMalloc(&tscr, 16 * (size_t)(m->host.nq + 2 * m->host.nv)));
+    for (int c = 0; c < m->host.nbody; ++c) {
+      CK(launch_body_invweight_tangent(m->dev, dq0, m->rcap, dmx::PAR_MU0 + m->host.npair + c, ws, tscr, dinv, 0));
+      CK(cudaMemcpy(dinvw[c], dinv, sizeof(double) * m->host.nbody, cudaMemcpyDeviceToHost));
+    }
+    cudaFree(ws); cudaFree(tscr);
+  }
   cudaFree(dq0); cudaFree(dinv); cudaFree(dscr);
   for (int p = 0; p < m->host.npair; ++p) {
     const int bA = m->host.g_body[m->host.p_g1[p]];
@@ -226,6 +240,7 @@ extern "C" dmx_status dmx_create_model(const dmx_model_desc* desc, dmx_model** o
     if (!(ah > 0) || !std::isfinite(ah)) { cudaFree(m->dev); delete m; return dmx_fail(DMX_ERR_INVALID, "mass matrix at qpos0 is singular"); }
     m->host.p_ahat[p] = ah;
     m->host.p_ahat_edge[p] = ah * (1.0 + m->host.p_mu[p] * m->host.p_mu[p]);
+    for (int c = 0; c < m->host.nbody; ++c) m->host.p_dahat[p][c] = dinvw[c][bA] + (bB >= 0 ? dinvw[c][bB] : 0.0);
   }
   for (int b = 0; b < m->host.nbody; ++b) m->invw[b] = invw[b];
   CK(cudaMemcpy(m->dev, &m->host, sizeof(DevModel), cudaMemcpyHostToDevice));
@@ -583,7 +598,7 @@ static dmx_status run_tangent_adjoint(dmx_model* m, dmx_tape* t, dmx::AdjParams&
   return DMX_OK;
 }
 
-static int model_nparams(const dmx_model* m) { return dmx::PAR_MU0 + m->host.npair; }
+static int model_nparams(const dmx_model* m) { return dmx::PAR_MU0 + m->host.npair + m->host.nbody; }
 
 extern "C" dmx_status dmx_model_params(const dmx_model* m, int32_t* np, double* values) {
   if (!m) return dmx_fail(DMX_ERR_INVALID, "null model");
@@ -595,6 +610,7 @@ extern "C" dmx_status dmx_model_params(const dmx_model* m, int32_t* np, double* 
     values[dmx::PAR_DO] = d.solimp[0]; values[dmx::PAR_DW] = d.solimp[1];
     values[dmx::PAR_WIDTH] = d.solimp[2]; values[dmx::PAR_MID] = d.solimp[3];
     for (int p = 0; p < d.npair; ++p) values[dmx::PAR_MU0 + p] = d.p_mu[p];
+    for (int b = 0; b < d.nbody; ++b) values[dmx::PAR_MU0 + d.npair + b] = d.b_mass[b];
   }
   return DMX_OK;
 }

@@ -249,6 +249,30 @@ def quadruped_inputs(B=8192, seed=1004):
     return {"x0": x0, "ctrl": ctrl, "T": T, "NI": 1, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3, "max_steps": 20000}
 
 
+def arm_tilt_scene(tilt=0.015, **opt):
+    """The arm + cube with the arm's base (and so every hinge axis) tilted by
+    `tilt` rad about the world y axis: the outstretched arm descends towards
+    its tip, which starts 6.5 mm into the plane, so the capsule-plane pairs
+    (two end slots per link) carry contact forces, with friction against the
+    links' sliding, as the arm swings."""
+    sc = chain_cube_scene(**opt)
+    sc["bodies"][0]["quat"] = [math.cos(tilt / 2), 0.0, math.sin(tilt / 2), 0.0]
+    sc["name"] = "arm_tilt"
+    return sc
+
+
+def arm_tilt_inputs(B=64, seed=1009, T=0.5, NI=10):
+    """Tilted arm at rest along +x, torques ~ N(0, 1) N m per hinge and interval."""
+    g = _rng(seed)
+    scene = arm_tilt_scene()
+    nq, nv, nu = scene_dims(scene)
+    x0 = np.zeros((B, nq + nv))
+    x0[:, :nq] = np.asarray(scene["qpos0"])
+    ctrl = g.normal(0.0, 1.0, (B, NI, nu))
+    return {"x0": x0, "ctrl": ctrl, "T": np.full(B, T), "NI": NI, "rtol": 1e-6, "atol": 1e-8, "h0": 1e-3,
+            "max_steps": 20000}
+
+
 def billiard_scene(radius=0.05, mass=0.2, condim=1, mu=0.0, **opt):
     """Two free balls and no gravity, the ball-ball contact only (the billiard
     toy of Sec. 4 and App. C.4 with the table contacts and gravity off)."""
@@ -342,6 +366,6 @@ def chain_goal():
 
 
 SCENES = {"ball": ball_scene, "box": box_scene, "chain_cube": chain_cube_scene, "quadruped": quadruped_scene,
-          "toss": toss_scene, "billiard": billiard_scene, "capsules": capsules_scene}
+          "toss": toss_scene, "billiard": billiard_scene, "capsules": capsules_scene, "arm_tilt": arm_tilt_scene}
 INPUTS = {"ball": ball_inputs, "box": box_push_inputs, "chain_cube": chain_inputs, "quadruped": quadruped_inputs,
-          "toss": toss_inputs, "billiard": billiard_inputs, "capsules": capsules_inputs}
+          "toss": toss_inputs, "billiard": billiard_inputs, "capsules": capsules_inputs, "arm_tilt": arm_tilt_inputs}

@@ -129,6 +129,24 @@ def test_chain_control_gradient_with_boundary_cotangents(dmx, orc_mod, cfd, mode
 
 
 @pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("cfd", [False, True])
+def test_arm_tilt_gradient(dmx, orc_mod, cfd, mode):
+    """Tilted arm (capsule ends pressed into the plane, sliding with
+    friction): gradient w.r.t. x0 and every control, loss on the final state
+    and the interval-boundary states."""
+    sc = W.arm_tilt_scene(**CFD_OPT) if cfd else W.arm_tilt_scene()
+    inp = W.arm_tilt_inputs(8, T=0.24, NI=6)
+    rng = np.random.default_rng(6)
+    xT_bar = rng.normal(size=(8, 27))
+    xb_bar = rng.normal(size=(8, 7, 27))
+    m = dmx.Model(sc)
+    g = gpu_grad(dmx, m, inp, xT_bar, xb_bar=xb_bar, cfd=cfd, K=5, mode=mode)
+    o = oracle_grad(orc_mod, sc, inp, g, xT_bar, xb_bar=xb_bar, cfd=cfd)
+    assert_grad(g, o)
+    assert_grad(g, o, "ctrl_bar")
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_quadruped_gradient(dmx, orc_mod, mode):
     """19 + 18 coordinates and 12 servo targets: 49 input directions (two
     32-lane passes per step for the tangent kernel)."""
@@ -206,21 +224,23 @@ TOL_VJP = 1e-10
 
 
 @pytest.mark.parametrize("cfd", [False, True])
-@pytest.mark.parametrize("name", ["ball", "box", "chain_cube", "quadruped", "billiard", "capsules"])
+@pytest.mark.parametrize("name", ["ball", "box", "chain_cube", "quadruped", "billiard", "capsules", "arm_tilt"])
 def test_rhs_vjp_matches_oracle_jacobian(dmx, orc_mod, name, cfd):
     """Right-hand-side VJP (dmx_eval_rhs_vjp) against the transposed Jacobian
     of the oracle's right-hand side (its derivative scalars) at states near
     contact (angular velocities included), for several lane counts."""
-    from tests.test_gpu_rollout import SEEDS, _random_states, pair_states
+    from tests.test_gpu_rollout import SEEDS, _random_states, arm_tilt_states, pair_states
     sc = W.SCENES[name](**CFD_OPT) if cfd else W.SCENES[name]()
     B = 48
     om = orc_mod.OracleModel(sc)
     if name in ("billiard", "capsules"):          # states near the ball-ball / capsule contacts
         _, q, v = pair_states(orc_mod, name, B, 31)
         u = np.zeros((B, 1))
+    elif name == "arm_tilt":                      # capsule ends pressed into the plane
+        _, q, v, u = arm_tilt_states(orc_mod, B, 37)
     else:
         q, v, u = _random_states(sc, B, SEEDS[name] + 100, om)
-    rng = np.random.default_rng(SEEDS.get(name, 40))
+    rng = np.random.default_rng(SEEDS.get(name, 40))   # (pair and tilted-arm scenes: 40)
     gm = dmx.Model(sc)
     abar = rng.normal(size=(B, gm.nv))
     ref_q, ref_v, ref_u = [], [], []
@@ -228,7 +248,7 @@ def test_rhs_vjp_matches_oracle_jacobian(dmx, orc_mod, name, cfd):
         Jq, Jv, Ju = om.rhs_jacobian(q[e], v[e], u[e], cfd=cfd)
         ref_q.append(Jq.T @ abar[e]); ref_v.append(Jv.T @ abar[e]); ref_u.append(Ju.T @ abar[e])
     ref = [np.concatenate([ref_q[e], ref_v[e], ref_u[e]]) for e in range(B)]
-    for lanes in ((8, 16, 32) if name in ("chain_cube", "quadruped", "capsules") else (2, 8, 32)):   # large workspaces need >= 8 lanes
+    for lanes in ((8, 16, 32) if name in ("chain_cube", "quadruped", "capsules", "arm_tilt") else (2, 8, 32)):   # large workspaces need >= 8 lanes
         qb, vb, ub, st = dmx.eval_rhs_vjp(gm, _dev(q.T), _dev(v.T), _dev(abar.T),
                                           u=_dev(u[:, :gm.nu].T) if gm.nu else None, cfd=cfd, lanes=lanes)
         assert np.all(st.cpu().numpy() == 0)
@@ -417,7 +437,7 @@ def param_inputs(name):
 @pytest.mark.parametrize("name,cfd", [("ball", False), ("ball", True), ("box", False), ("chain_cube", False),
                                       ("quadruped", False)])
 def test_parameter_gradient_matches_oracle(dmx, orc_mod, name, cfd):
-    """p_bar (solref, solimp, friction of every pair) of dmx_rollout_grad_params
+    """p_bar (solref, solimp, friction of every pair, body masses) of dmx_rollout_grad_params
     against the oracle's discrete adjoint along the GPU's steps (1e-6, per
     environment); the state and control gradients of the same call too; the
     in-library sum over environments equals the sum of the per-environment

@@ -322,6 +322,73 @@ def test_quadruped(dmx, orc_mod):
     assert_replay_parity(orc_mod, sc, s, gpu_rollout(dmx, m, s, tape=True))
 
 
+def arm_tilt_states(orc_mod, B, seed):
+    """States of the tilted arm (capsule ends pressed into the plane) along
+    the oracle's trajectories, jittered by 1e-4 (hinges) / 1e-3 (velocities)."""
+    sc = W.arm_tilt_scene()
+    om = orc_mod.OracleModel(sc)
+    inp = W.arm_tilt_inputs(B, seed=seed)
+    g = np.random.default_rng(seed)
+    Q, V, U = [], [], []
+    for e in range(B):
+        r = om.rollout(inp["x0"][e], ctrl=inp["ctrl"][e], T=0.5, NI=inp["NI"])
+        xb = r["xb"][1 + e % inp["NI"]]
+        Q.append(xb[:om.nq] + 1e-4 * g.normal(size=om.nq) * (np.arange(om.nq) < 7))
+        V.append(xb[om.nq:] + 1e-3 * g.normal(size=om.nv))
+        U.append(inp["ctrl"][e][e % inp["NI"]])
+    return sc, np.array(Q), np.array(V), np.array(U)
+
+
+@pytest.mark.parametrize("cfd", [False, True])
+def test_arm_tilt_rhs_matches_oracle(dmx, orc_mod, cfd):
+    """Capsule-plane penetration with friction on hinge chains: the tilted
+    arm's links pressed into the plane at states along its trajectories.
+    The hinges move the pressed capsule ends almost parallel to the plane
+    (the tilt is 0.015 rad), so the normal rows' Jacobians are small against
+    their forces and the right-hand side is ill-conditioned: the oracle's own
+    value moves by ~3e-11 (up to 2e-10) when q and v move by 1e-15 relative.
+    Each state's bar is therefore max(1e-11, 10x that measured floor)."""
+    sc, q, v, u = arm_tilt_states(orc_mod, 48, 31)
+    if cfd:
+        sc = W.arm_tilt_scene(**CFD_OPT)
+    om = orc_mod.OracleModel(sc)
+    plane = np.array([om.contacts(q[e])[-14:, 0].min() for e in range(len(q))])
+    assert (plane < 0).mean() > 0.9                         # capsule ends in the plane
+    ref = np.array([om.rhs(q[e], v[e], u[e], cfd=cfd) for e in range(len(q))])
+    nrows = np.array([om.rhs(q[e], v[e], u[e], cfd=cfd, detail=True)[1]["nr"] for e in range(len(q))])
+    rng = np.random.default_rng(0)
+    floor = np.zeros(len(q))
+    for e in range(len(q)):
+        for _ in range(4):
+            qp = q[e] * (1 + 1e-15 * rng.normal(size=q.shape[1]))
+            vp = v[e] * (1 + 1e-15 * rng.normal(size=v.shape[1]))
+            floor[e] = max(floor[e], rel_err(om.rhs(qp, vp, u[e], cfd=cfd), ref[e]))
+    assert np.median(floor) < 1e-9
+    bar = np.maximum(TOL_RHS, 10 * floor)
+    gm = dmx.Model(sc)
+    for lanes in (8, 16, 32):
+        a, info = dmx.eval_rhs(gm, _dev(q.T), _dev(v.T), _dev(u.T), cfd=cfd, lanes=lanes)
+        a, info = a.cpu().numpy().T, info.cpu().numpy()
+        assert np.all(info[0] == 0)
+        np.testing.assert_array_equal(info[1], nrows)
+        ratio = max(rel_err(a[e], ref[e]) / bar[e] for e in range(len(q)))
+        assert ratio < 1.0, f"lanes {lanes}: {ratio:.3f} of the per-state bar"
+
+
+def test_arm_tilt_trajectories(dmx, orc_mod):
+    """Tilted arm over 0.5 s (10 torque intervals): every step, free running,
+    and the replayed first 50 ms."""
+    sc = W.arm_tilt_scene()
+    inp = W.arm_tilt_inputs(24)
+    m = dmx.Model(sc)
+    g = gpu_rollout(dmx, m, inp, tape=True, K=1, want_xb=True)
+    assert np.all(g["status"] == 0)
+    assert_stepwise_parity(orc_mod, sc, inp, g)
+    assert_free_parity(gpu_rollout(dmx, m, inp), oracle_free(orc_mod, sc, inp))
+    s = dict(inp, T=np.full(24, 0.05), NI=1, ctrl=inp["ctrl"][:, :1])
+    assert_replay_parity(orc_mod, sc, s, gpu_rollout(dmx, m, s, tape=True, want_xb=True))
+
+
 # ---------------------------------------------------------------- GPU invariants and edges
 @pytest.mark.parametrize("form", ["step", "graph"])
 def test_plain_forms_bitwise_equal_persistent(dmx, form):

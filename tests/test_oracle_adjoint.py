@@ -301,21 +301,33 @@ PARAM_NAMES = ["t_c", "phi_d", "d_o", "d_w", "width", "midpoint"]
 
 def _perturbed_scene(make, k, delta):
     """Scene from make() with model parameter k moved by delta (order:
-    t_c, phi_d, d_o, d_w, width, midpoint, then mu of each pair)."""
+    t_c, phi_d, d_o, d_w, width, midpoint, mu of each pair, then the mass of
+    each body with its inertia scaled in proportion)."""
     sc = make()
     o = sc["options"]
+    npair = len(sc["pairs"])
     if k < 2:
         o["solref"][k] += delta
     elif k < 6:
         o["solimp"][k - 2] += delta
-    else:
+    elif k < 6 + npair:
         sc["pairs"][k - 6]["mu"] += delta
+    else:
+        b = sc["bodies"][k - 6 - npair]
+        f = (b["mass"] + delta) / b["mass"]
+        b["mass"] += delta
+        b["inertia"] = [f * x for x in b["inertia"]]
     return sc
 
 
 def _param_value(sc, k):
     o = sc["options"]
-    return o["solref"][k] if k < 2 else o["solimp"][k - 2] if k < 6 else sc["pairs"][k - 6]["mu"]
+    npair = len(sc["pairs"])
+    if k < 2:
+        return o["solref"][k]
+    if k < 6:
+        return o["solimp"][k - 2]
+    return sc["pairs"][k - 6]["mu"] if k < 6 + npair else sc["bodies"][k - 6 - npair]["mass"]
 
 
 def _param_fd(orc, make, x0, hlog, w, T, k, rel=1e-6, ctrl=None, NI=1):
@@ -332,8 +344,9 @@ def _param_fd(orc, make, x0, hlog, w, T, k, rel=1e-6, ctrl=None, NI=1):
 
 @pytest.mark.parametrize("name", ["ball", "box"])
 def test_parameter_gradient_frozen_steps(orc, name):
-    """p_bar of the discrete adjoint (solref, solimp, friction) against central
-    differences of the frozen-step map over models with one parameter moved."""
+    """p_bar of the discrete adjoint (solref, solimp, friction, mass) against
+    central differences of the frozen-step map over models with one parameter
+    moved."""
     make = W.SCENES[name]
     m = orc.OracleModel(make())
     if name == "ball":
@@ -345,7 +358,7 @@ def test_parameter_gradient_frozen_steps(orc, name):
     n = np.array([len(r["hlog"])], dtype=np.int32)
     g = m.batch_replay_grad(x0[None], np.array([T]), r["hlog"][None], n, w[None], params=True)
     pb = g["p_bar"][0]
-    assert len(pb) == m.nparams() == 7
+    assert len(pb) == m.nparams() == 8
     for k in range(m.nparams()):
         if name == "ball" and k == 6:
             assert pb[k] == 0.0                      # frictionless: mu enters no row
@@ -365,10 +378,16 @@ def test_rest_height_parameter_gradient(orc):
     phi_d^2), d the solimp spline): the adjoint's gradient of the final height
     w.r.t. (t_c, phi_d, d_o, d_w, width, midpoint) equals d r_rest / d theta,
     computed here from that scalar equation alone (brentq roots of perturbed
-    equations).  The adaptive steps at rest leave velocities of ~1e-9 m/s, so
-    the comparison holds to 1e-3 relative (a missing term or a sign is O(1))."""
+    equations).  The mass drops out: the contact force m g equals
+    (a_ref + g) / (R + 1/m) with R = A_hat (1 - d) / d, and the ball's A_hat is
+    1/m, so a_ref = g (1 - d) / d whatever m; the mass gradient vanishes only
+    if both the inertia's and A_hat's dependence on the mass are carried
+    (either alone gives a non-zero gradient, the two of opposite sign).  The adaptive
+    steps at rest leave velocities of ~1e-9 m/s, so the comparison holds to
+    1e-3 relative (a missing term or a sign is O(1))."""
     from scipy.optimize import brentq
     sc = W.ball_scene()
+    m0 = sc["bodies"][0]["mass"]
     base = [*sc["options"]["solref"], *sc["options"]["solimp"][:4]]
     pw = sc["options"]["solimp"][4]
 
@@ -388,12 +407,17 @@ def test_rest_height_parameter_gradient(orc):
     w = np.zeros(13); w[2] = 1.0
     n = np.array([len(r["hlog"])], dtype=np.int32)
     pb = m.batch_replay_grad(x0[None], np.array([T]), r["hlog"][None], n, w[None], params=True)["p_bar"][0]
+    # parameter order: the six contact parameters, mu of the pair, the mass
+    assert pb[6] == 0.0                                 # frictionless pair
     for k in range(6):
         eps = 1e-6 * max(abs(base[k]), 1e-3)
         hi, lo = list(base), list(base)
         hi[k] += eps; lo[k] -= eps
         ref = (r_rest(hi) - r_rest(lo)) / (2 * eps)
         assert abs(pb[k] - ref) <= 1e-3 * abs(ref), (PARAM_NAMES[k], pb[k], ref)
+    # relative sensitivities theta dz/dtheta: the mass's vanishes
+    rel = np.abs(pb[:6] * np.array(base))
+    assert abs(pb[7] * m0) <= 1e-3 * rel.max(), (pb[7], rel)
 
 
 def _param_floor(orc, name, inp):
