@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--form", choices=["persistent", "step", "graph"], default="persistent")
     p.add_argument("--lanes", type=int, default=0, help="lanes per environment (0 = autotuned)")
     p.add_argument("--no-extras", action="store_true", help="skip the plain-form and CPU-baseline legs")
+    p.add_argument("--envs", type=int, default=4096,
+                   help="box pushes per GPU (4096: the benchmark; smaller only to profile a small case)")
+    p.add_argument("--horizon", type=float, default=1.0, help="box-push horizon T in s (1: the benchmark)")
     p.add_argument("--serving", action="store_true", help="served-request latency benchmark instead of the rollout bench")
     p.add_argument("--grad-only", action="store_true", help="only the fwd+adjoint leg (one JSON line)")
     p.add_argument("--grad-envs", type=int, default=16384, help="environments of the fwd+adjoint leg")
@@ -279,7 +282,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     dist_init(world, "nccl")
     sc = W.box_scene()
-    inp = W.box_push_inputs(4096, seed=1002 + rank)
+    inp = W.box_push_inputs(args.envs, seed=1002 + rank, T=args.horizon)
     model = dmx.Model(sc)
     x0 = torch.tensor(np.ascontiguousarray(inp["x0"].T), device=dev)
     T = torch.tensor(inp["T"], device=dev)
@@ -357,7 +360,8 @@ def run_ours(args):
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms_max, "ms_p90": ms_p90, "higher_is_better": True,
                   "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded box pushes)",
-                  "config": dict(WORKLOAD, form=args.form, lanes=lanes, parallelism=f"env shards x{world}",
+                  "config": dict(WORKLOAD, B=args.envs, T_s=args.horizon, form=args.form, lanes=lanes,
+                                 parallelism=f"env shards x{world}",
                                  l2="flushed (256 MB write) between timed steps",
                                  env_steps_per_batch=nsteps, autotune_ms=tuned or None),
                   "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline, "clocks": clk.summary()}
@@ -512,7 +516,7 @@ def sysid_leg(dmx, dev, world=1, rank=0, B=4096, parity_envs=(0, 1)):
         scale = np.maximum(np.maximum(np.abs(o["p_bar"]), np.abs(o["p_bar"]).max(axis=1, keepdims=True)), 1e-300)
         parity = {"envs": envs, "p_bar": float(np.max(np.abs(g - o["p_bar"]) / scale)), "bar": 1e-6}
     return {"workload": "cube tosses, final-position loss against a model with mu 0.6 and t_c 4 ms",
-            "envs_per_gpu": B, "params": ["t_c", "phi_d", "d_o", "d_w", "width", "midpoint", "mu"],
+            "envs_per_gpu": B, "params": ["t_c", "phi_d", "d_o", "d_w", "width", "midpoint", "mu", "mass"],
             "grad_rollouts_per_s": B * world / t, "s": t, "env_steps": int(out["nsteps"].sum().item()),
             "p_bar_sum": ps.cpu().numpy().tolist(), "reduction": "in-library row sums, all-reduce over ranks",
             "kernel": "k_adjoint (forward-mode, one direction per lane)", "parity_vs_oracle": parity}
@@ -581,8 +585,8 @@ def _oracle_grad(scene, inp, n, xT_bar):
 
 def run_all(args):
     """Forward and fwd+adjoint rates of the four rollout workloads at their
-    stated batch sizes (the quadruped adjoint on its first 2048 environments),
-    with the CPU oracle timed on bounded samples."""
+    stated batch sizes, billiard shots with the discrete and the continuous
+    adjoint, with the CPU oracle timed on bounded samples."""
     import torch
 
     import paper_2506_14186_gb300 as dmx
@@ -685,11 +689,47 @@ def run_all(args):
         b = torch.zeros_like(out["xT"])
         b[0:3] = 1.0
         return b
-    r = {"forward": forward(m, inp, 8192, reps=1), "fwd_adjoint": gradient(m, inp, 2048, torso_bar)}
+    r = {"forward": forward(m, inp, 8192, reps=1), "fwd_adjoint": gradient(m, inp, 8192, torso_bar)}
     rate, sec = _oracle_fwd(sc, inp, 64)
-    r["cpu_oracle"] = {"env_steps_per_s": rate, "cores": cores, "sample": "forward: first 64 of 8192"}
+    tb = np.zeros((2, 37)); tb[:, 0:3] = 1.0
+    grate, gsec = _oracle_grad(sc, inp, 2, tb)
+    r["cpu_oracle"] = {"env_steps_per_s": rate, "grad_rollouts_per_s": grate, "cores": cores,
+                       "sample": "forward: first 64 of 8192; gradient: first 2"}
     res["quadruped_B8192"] = r
+    res["billiard_B4096"] = _billiard_leg(dmx, W, d, cores)
     return {"metric": METRIC, "impl": "ours", "dtype": "f64", "data": "synthetic (seeded)", "all": res}
+
+
+def _billiard_leg(dmx, W, d, cores, B=4096):
+    """Billiard shots (Sec. 4, App. C.4; B = 4096, T = 0.5 s): forward with a
+    tape, the discrete adjoint (DTO) and the continuous adjoint by backsolve
+    (OTD) of the target ball's final x, plain and straight-through with
+    contacts from distance; the CPU oracle's OTD on a sample."""
+    import torch
+    import oracle
+    inp = W.billiard_inputs(B)
+    out = {}
+    for label, sc, cfd in (("plain", W.billiard_scene(), False), ("cfd", W.billiard_scene(**W.CFD_OPTIONS), True)):
+        m = dmx.Model(sc)
+        x0, T = d(inp["x0"].T), d(inp["T"])
+        w = torch.zeros((26, B), dtype=torch.float64, device=x0.device)
+        w[7] = 1.0
+        kw = dict(rtol=inp["rtol"], atol=inp["atol"], h0=inp["h0"], max_steps=inp["max_steps"])
+        _events_time(lambda: dmx.rollout(m, x0, T, tape=True, **kw))          # warm-up
+        f, tf = _events_time(lambda: dmx.rollout(m, x0, T, tape=True, **kw))
+        _, tdto = _events_time(lambda: dmx.rollout_grad(f["tape"], w, cfd=cfd))
+        (gx, _, steps, st), totd = _events_time(lambda: dmx.rollout_grad_otd(m, f["xT"], T, w, cfd=cfd, **kw))
+        om = oracle.OracleModel(sc)
+        n = 64
+        t0 = time.perf_counter()
+        om.batch_grad_otd(inp["x0"][:n], inp["T"][:n], w[:, :n].T.cpu().numpy(), cfd=cfd, **kw)
+        cpu = n / (time.perf_counter() - t0)
+        out[label] = {"forward_s": tf, "dto_s": tdto, "otd_s": totd,
+                      "forward_env_steps": int(f["nsteps"].sum().item()),
+                      "otd_backward_steps": int(steps.sum().item()), "otd_status_ok": bool((st == 0).all().item()),
+                      "otd_grad_rollouts_per_s": B / (tf + totd), "dto_grad_rollouts_per_s": B / (tf + tdto),
+                      "cpu_oracle_otd_grad_rollouts_per_s": cpu, "cpu_cores": cores, "cpu_sample": f"first {n} of {B}"}
+    return out
 
 
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
