@@ -516,7 +516,7 @@ def sysid_leg(dmx, dev, world=1, rank=0, B=4096, parity_envs=(0, 1)):
         scale = np.maximum(np.maximum(np.abs(o["p_bar"]), np.abs(o["p_bar"]).max(axis=1, keepdims=True)), 1e-300)
         parity = {"envs": envs, "p_bar": float(np.max(np.abs(g - o["p_bar"]) / scale)), "bar": 1e-6}
     return {"workload": "cube tosses, final-position loss against a model with mu 0.6 and t_c 4 ms",
-            "envs_per_gpu": B, "params": ["t_c", "phi_d", "d_o", "d_w", "width", "midpoint", "mu", "mass"],
+            "envs_per_gpu": B, "params": ["t_c", "phi_d", "d_o", "d_w", "width", "midpoint", "mu", "mass", "side"],
             "grad_rollouts_per_s": B * world / t, "s": t, "env_steps": int(out["nsteps"].sum().item()),
             "p_bar_sum": ps.cpu().numpy().tolist(), "reduction": "in-library row sums, all-reduce over ranks",
             "kernel": "k_adjoint (forward-mode, one direction per lane)", "parity_vs_oracle": parity}

@@ -182,17 +182,19 @@ dmx_status dmx_rollout(dmx_model* m, const dmx_rollout_args* a, void* stream);
 dmx_status dmx_rollout_grad(dmx_model* m, dmx_tape* tape, int32_t cfd, const double* xT_bar,
                             const double* xb_bar, double* x0_bar, double* ctrl_bar, void* stream);
 /* Model parameters of the gradient below (the parameters tuned by the
- * system identification of Sec. 5.1 / App. E.2): np = 6 + npair + nbody,
- * values (host, may be NULL) = t_c, phi_d (solref), d_o, d_w, width,
- * midpoint (solimp), the friction coefficient mu of every pair, then the mass
- * of every body (its rotational inertia scaled in proportion: equal
- * density, fixed shape). */
+ * system identification of Sec. 5.1 / App. E.2): np = 6 + npair + nbody +
+ * nbox, values (host, may be NULL) = t_c, phi_d (solref), d_o, d_w, width,
+ * midpoint (solimp), the friction coefficient mu of every pair, the mass of
+ * every body (its rotational inertia scaled in proportion: equal density,
+ * fixed shape), then the side length of every box geom in geom order (2 x
+ * its x half size; the half sizes scale together, and the inertia of a body
+ * whose only geom is the box scales with the square, mass fixed). */
 dmx_status dmx_model_params(const dmx_model* m, int32_t* np, double* values);
 /* dmx_rollout_grad plus the gradient of the same loss with respect to the
  * model parameters (p of the problem statement in Sec. 2, differentiated
  * through the discrete adjoint with the accepted step sizes held constant;
  * A_hat, the model constant computed at qpos0 at creation, carries its
- * derivative with respect to the masses).  p_bar [np][B] receives
+ * derivative with respect to the masses and box sides).  p_bar [np][B] receives
  * it per environment; p_bar_sum [np] (may be NULL) the sum over the
  * environments (a fixed-order reduction: the batch's gradient when every
  * environment shares the model).  Computed by the forward-mode adjoint kernel

@@ -324,8 +324,9 @@ class OracleModel:
                 "back_status": st[:, 4].copy(), "back_steps": st[:, 5].copy(), "back_rej": st[:, 6].copy()}
 
     def nparams(self):
-        """Model parameters of the adjoint: t_c, phi_d, d_o, d_w, width, midpoint, then mu of each pair,
-        then the mass of each body (its rotational inertia scaled in proportion)."""
+        """Model parameters of the adjoint: t_c, phi_d, d_o, d_w, width, midpoint, mu of each pair,
+        the mass of each body (its rotational inertia scaled in proportion), then the side length of
+        each box geom (half sizes scaled together; the inertia of a body that is the box by the square)."""
         return int(lib().orc_nparams(self.h))
 
     def batch_grad(self, x0, T, xT_bar, ctrl=None, NI=1, rtol=1e-6, atol=1e-8, h0=1e-3, max_steps=20000, cfd=False,

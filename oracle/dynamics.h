@@ -90,19 +90,36 @@ template <class S> struct Kin {
 // Model parameters that the adjoint differentiates (the parameters of the
 // system identification of Sec. 5.1 and App. E.2): solref (t_c, phi_d),
 // solimp (d_o, d_w, width, midpoint), the friction coefficient of every pair,
-// then the mass of every body (its rotational inertia scaled in proportion:
-// equal density, fixed shape).  par<S>(k, v) is the value v of parameter k;
-// in the derivative scalar it carries a unit tangent when k is the direction
-// being differentiated (g_pdir), else none.
+// the mass of every body (its rotational inertia scaled in proportion: equal
+// density, fixed shape), then the side length of every box geom (its edge
+// along the geom's x axis; the half sizes scale together, and the inertia of
+// a body whose only geom is the box scales with the square, mass fixed).
+// par<S>(k, v) is the value v of parameter k; in the derivative scalar it
+// carries a unit tangent when k is the direction being differentiated
+// (g_pdir), else none.
 enum { PAR_TC = 0, PAR_DAMP = 1, PAR_DO = 2, PAR_DW = 3, PAR_WIDTH = 4, PAR_MID = 5, PAR_MU0 = 6 };
 extern thread_local int g_pdir;
 template <class S> inline S par(int, double v) { return S(v); }
 template <> inline Dual<double> par<Dual<double>>(int k, double v) { return Dual<double>(v, g_pdir == k ? 1.0 : 0.0); }
 inline int par_mass(const Model& m, int b) { return PAR_MU0 + (int)m.pair.size() + b; }
-inline int n_params(const Model& m) { return par_mass(m, (int)m.body.size()); }
+inline int par_side(const Model& m, int j) { return par_mass(m, (int)m.body.size()) + j; }
+inline int n_params(const Model& m) { return par_side(m, (int)m.box_geom.size()); }
 // Whether S carries the tangent of body b's mass in this evaluation.
 template <class S> inline bool mass_direction(const Model&, int) { return false; }
 template <> inline bool mass_direction<Dual<double>>(const Model& m, int b) { return g_pdir == par_mass(m, b); }
+// Whether S carries the tangent of the side of the box body b consists of.
+template <class S> inline bool side_direction(const Model&, int) { return false; }
+template <> inline bool side_direction<Dual<double>>(const Model& m, int b) {
+  return m.body[b].sole_box >= 0 && g_pdir == par_side(m, m.body[b].sole_box);
+}
+// Half size i of geom g; for a box in the derivative scalar with g_pdir on
+// its side length l = 2 h_0, the tangent dh_i/dl = h_i / (2 h_0).
+template <class S> inline S half_size(const Model& m, int g, int i) { return S(m.geom[g].size[i]); }
+template <> inline Dual<double> half_size<Dual<double>>(const Model& m, int g, int i) {
+  const Geom& G = m.geom[g];
+  const bool dir = G.box >= 0 && g_pdir == par_side(m, G.box);
+  return Dual<double>(G.size[i], dir ? G.size[i] / (2.0 * G.size[0]) : 0.0);
+}
 
 // A_hat of pair P (the sum of its bodies' inverse weights); the derivative
 // scalar carries its derivative with respect to the body mass g_pdir points at.
@@ -137,6 +154,12 @@ template <class S> void kinematics(const Model& m, const S* q, Kin<S>& k) {
     if (mass_direction<S>(m, b)) {                      // inertia proportional to the mass
       const S scale = par<S>(par_mass(m, b), B.mass) / B.mass;
       for (int i = 0; i < 9; ++i) RI[i] = RI[i] * scale;
+    }
+    if (side_direction<S>(m, b)) {                      // inertia proportional to the side squared
+      const Geom& G = m.geom[m.box_geom[B.sole_box]];
+      const double l0 = 2.0 * G.size[0];
+      const S lam = par<S>(par_side(m, B.sole_box), l0) / l0;
+      for (int i = 0; i < 9; ++i) RI[i] = RI[i] * (lam * lam);
     }
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j)
@@ -294,7 +317,7 @@ template <class S> struct Contact {
 
 // Box signed distance in box coordinates and its gradient (a subgradient
 // inside); exact Euclidean distance outside.
-template <class S> S box_sdf(const V3<S>& y, const double* h, V3<S>& grad, bool& outside) {
+template <class S, class H> S box_sdf(const V3<S>& y, const H* h, V3<S>& grad, bool& outside) {
   S qd[3];
   outside = false;
   for (int i = 0; i < 3; ++i) {
@@ -336,6 +359,7 @@ void capsule_box(const Model& m, const Kin<S>& k, const Pair& P, Contact<S>& ct)
   const Geom& Bx = m.geom[P.g2];
   const double rc = C.size[0], L = C.size[1];
   const double* h = Bx.size;
+  const S hS[3] = {half_size<S>(m, P.g2, 0), half_size<S>(m, P.g2, 1), half_size<S>(m, P.g2, 2)};
   V3<S> u = {k.gR[P.g1][0], k.gR[P.g1][3], k.gR[P.g1][6]};     // capsule axis = geom x
   // segment in box coordinates: y(s) = y0 + s w, s in [-L, L]
   V3<S> y0 = mtvec(k.gR[P.g2], vsub(k.gp[P.g1], k.gp[P.g2]));
@@ -377,7 +401,7 @@ void capsule_box(const Model& m, const Kin<S>& k, const Pair& P, Contact<S>& ct)
       if (phi2 > 1e-12) {
         V3<S> yS = vadd(y0, vscl(w, S(s_star)));
         V3<S> gS; bool o2;
-        box_sdf<S>(yS, h, gS, o2);
+        box_sdf<S>(yS, hS, gS, o2);
         S dS = vdot(gS, w);
         s = S(s_star) - dS / phi2;
       }
@@ -385,7 +409,7 @@ void capsule_box(const Model& m, const Kin<S>& k, const Pair& P, Contact<S>& ct)
   }
   V3<S> y = vadd(y0, vscl(w, s));
   V3<S> g; bool out;
-  S dist = box_sdf<S>(y, h, g, out);
+  S dist = box_sdf<S>(y, hS, g, out);
   V3<S> nw = mvec(k.gR[P.g2], g);
   V3<S> x = vadd(k.gp[P.g1], vscl(u, s));
   ct.r = dist - rc;
@@ -488,8 +512,8 @@ template <class S> void contacts(const Model& m, const Kin<S>& k, std::vector<Co
         cpt = vadd(k.gp[P.g1], mvec(k.gR[P.g1], e));
         rad = G.size[0];
       } else {
-        V3<S> e = {S((j & 1) ? G.size[0] : -G.size[0]), S((j & 2) ? G.size[1] : -G.size[1]),
-                   S((j & 4) ? G.size[2] : -G.size[2])};
+        const S h0 = half_size<S>(m, P.g1, 0), h1 = half_size<S>(m, P.g1, 1), h2 = half_size<S>(m, P.g1, 2);
+        V3<S> e = {(j & 1) ? h0 : -h0, (j & 2) ? h1 : -h1, (j & 4) ? h2 : -h2};
         cpt = vadd(k.gp[P.g1], mvec(k.gR[P.g1], e));
       }
       ct.r = cpt[2] - rad;

@@ -53,7 +53,14 @@ std::string build_model(Model& m, const double* body, int nbody, const double* g
     for (int i = 0; i < 4; ++i) G.quat[i] = r[5 + i];
     if (G.body < 0 || G.body >= nbody) return "geom body out of range";
     normalize4(G.quat);
+    if (G.type == GEOM_BOX) { G.box = (int)m.box_geom.size(); m.box_geom.push_back(g); }
     m.geom.push_back(G);
+  }
+  for (int b = 0; b < nbody; ++b) {
+    int n = 0, last = -1;
+    for (int g = 0; g < ngeom; ++g)
+      if (m.geom[g].body == b) { ++n; last = g; }
+    if (n == 1 && m.geom[last].type == GEOM_BOX) m.body[b].sole_box = m.geom[last].box;
   }
   int row = 0;
   for (int p = 0; p < npair; ++p) {
@@ -100,9 +107,10 @@ std::string build_model(Model& m, const double* body, int nbody, const double* g
   // translational inverse weight of each body at qpos0: trace(Jc M^-1 Jc^T) / 3,
   // and its derivative with respect to every body mass (one derivative pass each)
   if (!body_inverse_weights(m, m.body_invw)) return "mass matrix at qpos0 is not positive definite";
-  std::vector<std::vector<double>> dinv(nbody, std::vector<double>(nbody, 0.0));
-  for (int c = 0; c < nbody; ++c) {
-    g_pdir = par_mass(m, c);
+  const int nmc = nbody + (int)m.box_geom.size();    // parameters M(q0) depends on: masses, box sides
+  std::vector<std::vector<double>> dinv(nmc, std::vector<double>(nbody, 0.0));
+  for (int c = 0; c < nmc; ++c) {
+    g_pdir = par_mass(m, 0) + c;
     std::vector<Dual<double>> w;
     body_inverse_weights(m, w);
     for (int b = 0; b < nbody; ++b) dinv[c][b] = w[b].d;
@@ -112,8 +120,8 @@ std::string build_model(Model& m, const double* body, int nbody, const double* g
     const int bA = m.geom[P.g1].body;
     const int bB = P.g2 >= 0 ? m.geom[P.g2].body : -1;
     P.invw = m.body_invw[bA] + (bB >= 0 ? m.body_invw[bB] : 0.0);
-    P.dinvw.assign(nbody, 0.0);
-    for (int c = 0; c < nbody; ++c) P.dinvw[c] = dinv[c][bA] + (bB >= 0 ? dinv[c][bB] : 0.0);
+    P.dinvw.assign(nmc, 0.0);
+    for (int c = 0; c < nmc; ++c) P.dinvw[c] = dinv[c][bA] + (bB >= 0 ? dinv[c][bB] : 0.0);
   }
   return "";
 }

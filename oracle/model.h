@@ -29,9 +29,11 @@ struct Body {
   int parent, jtype;
   double pos[3], quat[4], axis[3], mass, com[3], inertia[3], damping;
   int qadr, vadr, nq, nv;
+  int sole_box = -1;        // the body's only geom is box geom number sole_box (its inertia follows the size)
 };
 struct Geom {
   int type, body;
+  int box = -1;             // index among the model's box geoms (side-length parameter), else -1
   double pos[3], quat[4], size[3];
 };
 struct Pair {
@@ -39,7 +41,7 @@ struct Pair {
   double mu;
   int nslot, slot0, row0;   // contact slots and first constraint row of this pair
   double invw;              // approximate diag(J M^-1 J^T) for the normal row
-  std::vector<double> dinvw; // its derivative with respect to the mass of each body
+  std::vector<double> dinvw; // its derivative w.r.t. the mass of each body, then the side of each box
 };
 struct Act {
   int type, body;
@@ -62,6 +64,7 @@ struct Model {
   std::vector<std::vector<char>> anc;   // anc[b][j]: body j is b or an ancestor of b
   std::vector<int> dof_body;            // body owning each dof
   std::vector<double> body_invw;        // translational inverse weight at qpos0
+  std::vector<int> box_geom;            // geom index of every box geom
 };
 
 // Builds the model; returns "" on success or an error message.

@@ -202,7 +202,8 @@ class Model:
 
     def params(self):
         """Model parameters of rollout_grad_params: numpy array of t_c, phi_d,
-        d_o, d_w, width, midpoint, mu of every pair, then the mass of every body."""
+        d_o, d_w, width, midpoint, mu of every pair, the mass of every body, then the side
+        length of every box geom."""
         n = c_i32()
         _check(lib().dmx_model_params(self.h, ctypes.byref(n), None))
         vals = (c_f64 * n.value)()

@@ -216,6 +216,10 @@ struct WsT {
 // Parameter order: PAR_TC .. PAR_MID, mu of every pair, then the mass of
 // every body (rotational inertia scaled in proportion).
 __device__ __forceinline__ int par_mass(const DevModel& m, int b) { return PAR_MU0 + m.npair + b; }
+// then the side length of every box geom (its edge along the geom's x axis;
+// the half sizes scale together; the inertia of a body whose only geom is the
+// box scales with the square)
+__device__ __forceinline__ int par_side(const DevModel& m, int j) { return PAR_MU0 + m.npair + m.nbody + j; }
 template <class T>
 struct Par {
   static __device__ __forceinline__ double get(int, int, double v) { return v; }
@@ -224,6 +228,8 @@ struct Par {
   static __device__ __forceinline__ double ahat(const DevModel& m, int, int p) { return m.p_ahat[p]; }
   static __device__ __forceinline__ double ahat_edge(const DevModel& m, int, int p) { return m.p_ahat_edge[p]; }
   static __device__ __forceinline__ bool mass_dir(const DevModel&, int, int) { return false; }
+  static __device__ __forceinline__ bool side_dir(const DevModel&, int, int) { return false; }
+  static __device__ __forceinline__ double half(const DevModel& m, int, int g, int i) { return m.g_size[g][i]; }
 };
 template <>
 struct Par<Dual> {
@@ -240,10 +246,10 @@ struct Par<Dual> {
                  : pdir == PAR_DAMP ? -2.0 * k / m.solref[1]
                  : pdir == PAR_DW ? -2.0 * k / m.solimp[1] : 0.0);
   }
-  // d A_hat / d theta: non-zero for the body masses only
+  // d A_hat / d theta: non-zero for the body masses and box sides only
   static __device__ __forceinline__ double dahat(const DevModel& m, int pdir, int p) {
     const int b = pdir - par_mass(m, 0);
-    return (b >= 0 && b < m.nbody) ? m.p_dahat[p][b] : 0.0;
+    return (b >= 0 && b < m.nbody + m.nbox) ? m.p_dahat[p][b] : 0.0;
   }
   static __device__ __forceinline__ Dual ahat(const DevModel& m, int pdir, int p) {
     return Dual(m.p_ahat[p], dahat(m, pdir, p));
@@ -255,6 +261,14 @@ struct Par<Dual> {
                                       dahat(m, pdir, p) * (1.0 + mu * mu));
   }
   static __device__ __forceinline__ bool mass_dir(const DevModel& m, int pdir, int b) { return pdir == par_mass(m, b); }
+  static __device__ __forceinline__ bool side_dir(const DevModel& m, int pdir, int b) {
+    return m.b_solebox[b] >= 0 && pdir == par_side(m, m.g_box[m.b_solebox[b]]);
+  }
+  // half size i of geom g: a box's carries dh_i/dl = h_i / (2 h_0) along its side l
+  static __device__ __forceinline__ Dual half(const DevModel& m, int pdir, int g, int i) {
+    const double h = m.g_size[g][i];
+    return Dual(h, (m.g_box[g] >= 0 && pdir == par_side(m, m.g_box[g])) ? h / (2.0 * m.g_size[g][0]) : 0.0);
+  }
 };
 using Ws = WsT<double>;
 
@@ -413,6 +427,12 @@ __device__ void kinematics(const Grp<G>& g, const DevModel& m, const WsT<T>& w, 
       const double* In = m.b_inertia[b];
       v = Rb[3 * i] * Rb[3 * j] * In[0] + Rb[3 * i + 1] * Rb[3 * j + 1] * In[1] + Rb[3 * i + 2] * Rb[3 * j + 2] * In[2];
       if (Par<T>::mass_dir(m, w.pdir, b)) v = v * (ms / m.b_mass[b]);   // inertia proportional to the mass
+      if (Par<T>::side_dir(m, w.pdir, b)) {                             // ... and to the side squared
+        const int gs = m.b_solebox[b];
+        const double l0 = 2.0 * m.g_size[gs][0];
+        const auto lam = Par<T>::get(w.pdir, par_side(m, m.g_box[gs]), l0) / l0;
+        v = v * (lam * lam);
+      }
       const T cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
       v += ms * ((i == j ? cc : T(0.0)) - c[i] * c[j]);
     }
@@ -545,8 +565,8 @@ __device__ void rne_and_forces(const Grp<G>& g, const DevModel& m, const WsT<T>&
 
 // ------------------------------------------------------------------ collision
 // contact record (16 scalars): r, pos[3], n[3], t1[3], t2[3], d, pterm, D
-template <class T>
-__device__ __forceinline__ T box_sdf(const T* y, const double* h, T* grad) {
+template <class T, class H>
+__device__ __forceinline__ T box_sdf(const T* y, const H* h, T* grad) {
   T qd[3];
   bool out = false;
   for (int i = 0; i < 3; ++i) { qd[i] = fabs(y[i]) - h[i]; out = out || value(qd[i]) > 0; }
@@ -625,9 +645,12 @@ __device__ __forceinline__ double capsule_box_curv(const double* y0v, const doub
 // outside field: ds = -d(slope) / (d slope / ds)); elsewhere s is constant.
 template <class T>
 __device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1, int g2, double thr, T* ct,
-                            T* s_out) {
+                            T* s_out, int pdir = -1) {
   const double rc = m.g_size[g1][0], Lh = m.g_size[g1][1];
   const double* h = m.g_size[g2];
+  // the box half sizes as the evaluation's scalars (a side-length tangent in derivative scalars)
+  using H = decltype(Par<T>::half(m, pdir, g2, 0));
+  const H hT[3] = {Par<T>::half(m, pdir, g2, 0), Par<T>::half(m, pdir, g2, 1), Par<T>::half(m, pdir, g2, 2)};
   const T* R1 = gR + 9 * g1; const T* R2 = gR + 9 * g2;
   const T* c1 = gp + 3 * g1; const T* c2 = gp + 3 * g2;
   T dc[3] = {c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2]};
@@ -646,13 +669,13 @@ __device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1,
     const double phi2 = capsule_box_curv(y0v, wvv, sv, Lh, h);
     if (phi2 > 0) {
       T yT[3] = {y0[0] + sv * wv[0], y0[1] + sv * wv[1], y0[2] + sv * wv[2]}, gT[3];
-      box_sdf(yT, h, gT);
+      box_sdf(yT, hT, gT);
       const T slope = gT[0] * wv[0] + gT[1] * wv[1] + gT[2] * wv[2];
       s = T(sv, -slope.d / phi2);
     }
   }
   T y[3] = {y0[0] + s * wv[0], y0[1] + s * wv[1], y0[2] + s * wv[2]}, gr[3], n[3];
-  const T dist = box_sdf(y, h, gr);
+  const T dist = box_sdf(y, hT, gr);
   matvec3(R2, gr, n);
   const T r = dist - rc;
   ct[0] = r;
@@ -809,7 +832,7 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, boo
     T* ct = CT + 16 * s;
     const int p = m.s_pair[s], j = m.s_idx[s], g1 = m.p_g1[p];
     if (m.p_g2[p] >= 0) {
-      if (m.g_type[m.p_g2[p]] == GEOM_BOX) capsule_box(m, gR, gp, g1, m.p_g2[p], thr, ct, w.at(L.csv) + 2 * s);
+      if (m.g_type[m.p_g2[p]] == GEOM_BOX) capsule_box(m, gR, gp, g1, m.p_g2[p], thr, ct, w.at(L.csv) + 2 * s, w.pdir);
       else seg_seg(m, gR, gp, g1, m.p_g2[p], thr, ct, w.at(L.csv) + 2 * s);
     } else {
       const T* Rg = gR + 9 * g1; const T* cg = gp + 3 * g1;
@@ -822,8 +845,10 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, boo
         pt[0] = cg[0] + e * Rg[0]; pt[1] = cg[1] + e * Rg[3]; pt[2] = cg[2] + e * Rg[6];
         rad = m.g_size[g1][0];
       } else {
-        const double ex[3] = {(j & 1) ? m.g_size[g1][0] : -m.g_size[g1][0], (j & 2) ? m.g_size[g1][1] : -m.g_size[g1][1],
-                              (j & 4) ? m.g_size[g1][2] : -m.g_size[g1][2]};
+        const auto h0 = Par<T>::half(m, w.pdir, g1, 0), h1 = Par<T>::half(m, w.pdir, g1, 1);
+        const auto h2 = Par<T>::half(m, w.pdir, g1, 2);
+        using H = decltype(h0);
+        const H ex[3] = {(j & 1) ? h0 : H(-h0), (j & 2) ? h1 : H(-h1), (j & 4) ? h2 : H(-h2)};
         T t[3];
         matvec3(Rg, ex, t);
         pt[0] = cg[0] + t[0]; pt[1] = cg[1] + t[1]; pt[2] = cg[2] + t[2];

@@ -16,6 +16,7 @@ constexpr int MAXB = 16;      // bodies
 constexpr int MAXV = 24;      // dofs
 constexpr int MAXQ = 32;      // position coordinates
 constexpr int MAXG = 24;      // geoms
+constexpr int MAXBOX = 4;     // box geoms (side-length parameters)
 constexpr int MAXP = 24;      // contact pairs
 constexpr int MAXS = 32;      // contact slots
 constexpr int MAXU = 16;      // actuators
@@ -60,11 +61,14 @@ struct DevModel {
   int g_type[MAXG], g_body[MAXG];
   double g_pos[MAXG][3], g_Roff[MAXG][9], g_size[MAXG][3];
   double g_bound[MAXG];              // bounding-sphere radius about the geom centre
+  int g_box[MAXG];                   // index among the box geoms (side-length parameter), else -1
+  int nbox;
+  int b_solebox[MAXB];               // geom index of the body's only geom when it is a box (its inertia follows the side), else -1
   int g_ident[MAXG], g_zpos[MAXG];   // 1: g_Roff is exactly the identity / g_pos is exactly zero
   // pairs and slots
   int p_g1[MAXP], p_g2[MAXP], p_condim[MAXP], p_slot0[MAXP], p_nslot[MAXP], p_row0[MAXP];
   double p_mu[MAXP], p_ahat[MAXP], p_ahat_edge[MAXP];
-  double p_dahat[MAXP][MAXB];        // d A_hat / d (mass of body b), the model constant's mass derivative
+  double p_dahat[MAXP][MAXB + MAXBOX];   // d A_hat / d (mass of each body, then side of each box)
   int s_pair[MAXS], s_idx[MAXS];
   int s_barofs[MAXS], nslotbar;      // adjoint: offset / total of the per-slot pose cotangents
                                      // (12 doubles for a plane slot, 24 for a geom pair)

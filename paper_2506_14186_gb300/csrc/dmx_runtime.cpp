@@ -129,9 +129,20 @@ static std::string compile_model(const dmx_model_desc* d, DevModel& m) {
     quat_mat(G.quat, m.g_Roff[g]);
     m.g_ident[g] = is_identity(m.g_Roff[g]);
     m.g_zpos[g] = G.pos[0] == 0.0 && G.pos[1] == 0.0 && G.pos[2] == 0.0;
+    m.g_box[g] = -1;
+    if (G.type == DMX_GEOM_BOX) {
+      if (m.nbox >= MAXBOX) return "too many box geoms for the compiled limits";
+      m.g_box[g] = m.nbox++;
+    }
     if (G.type == DMX_GEOM_SPHERE) m.g_bound[g] = G.size[0];
     else if (G.type == DMX_GEOM_CAPSULE) m.g_bound[g] = G.size[0] + G.size[1];
     else m.g_bound[g] = std::sqrt(G.size[0] * G.size[0] + G.size[1] * G.size[1] + G.size[2] * G.size[2]);
+  }
+  for (int b = 0; b < m.nbody; ++b) {
+    int n = 0, last = -1;
+    for (int g = 0; g < m.ngeom; ++g)
+      if (m.g_body[g] == b) { ++n; last = g; }
+    m.b_solebox[b] = (n == 1 && m.g_type[last] == DMX_GEOM_BOX) ? last : -1;
   }
   int row = 0;
   for (int p = 0; p < m.npair; ++p) {
@@ -220,13 +231,15 @@ extern "C" dmx_status dmx_create_model(const dmx_model_desc* desc, dmx_model** o
   CK(cudaMemcpy(invw, dinv, sizeof(double) * m->host.nbody, cudaMemcpyDeviceToHost));
   // derivative of the inverse weights with respect to every body mass (the
   // model-parameter gradient carries A_hat's dependence on the masses)
-  double dinvw[MAXB][MAXB] = {};
+  // (and every box side, through the inertia of a body that is that box)
+  const int nmc = m->host.nbody + m->host.nbox;
+  double dinvw[MAXB + MAXBOX][MAXB] = {};
   {
     void *ws = nullptr, *tscr = nullptr;
     const size_t wsb = (size_t)m->L.nd * 16 + (size_t)m->L.ni * 4 + 16;
     CK(cudaMalloc(&ws, wsb));
     CK(cudaMalloc(&tscr, 16 * (size_t)(m->host.nq + 2 * m->host.nv)));
-    for (int c = 0; c < m->host.nbody; ++c) {
+    for (int c = 0; c < nmc; ++c) {
       CK(launch_body_invweight_tangent(m->dev, dq0, m->rcap, dmx::PAR_MU0 + m->host.npair + c, ws, tscr, dinv, 0));
       CK(cudaMemcpy(dinvw[c], dinv, sizeof(double) * m->host.nbody, cudaMemcpyDeviceToHost));
     }
@@ -240,7 +253,7 @@ extern "C" dmx_status dmx_create_model(const dmx_model_desc* desc, dmx_model** o
     if (!(ah > 0) || !std::isfinite(ah)) { cudaFree(m->dev); delete m; return dmx_fail(DMX_ERR_INVALID, "mass matrix at qpos0 is singular"); }
     m->host.p_ahat[p] = ah;
     m->host.p_ahat_edge[p] = ah * (1.0 + m->host.p_mu[p] * m->host.p_mu[p]);
-    for (int c = 0; c < m->host.nbody; ++c) m->host.p_dahat[p][c] = dinvw[c][bA] + (bB >= 0 ? dinvw[c][bB] : 0.0);
+    for (int c = 0; c < nmc; ++c) m->host.p_dahat[p][c] = dinvw[c][bA] + (bB >= 0 ? dinvw[c][bB] : 0.0);
   }
   for (int b = 0; b < m->host.nbody; ++b) m->invw[b] = invw[b];
   CK(cudaMemcpy(m->dev, &m->host, sizeof(DevModel), cudaMemcpyHostToDevice));
@@ -598,7 +611,9 @@ static dmx_status run_tangent_adjoint(dmx_model* m, dmx_tape* t, dmx::AdjParams&
   return DMX_OK;
 }
 
-static int model_nparams(const dmx_model* m) { return dmx::PAR_MU0 + m->host.npair + m->host.nbody; }
+static int model_nparams(const dmx_model* m) {
+  return dmx::PAR_MU0 + m->host.npair + m->host.nbody + m->host.nbox;
+}
 
 extern "C" dmx_status dmx_model_params(const dmx_model* m, int32_t* np, double* values) {
   if (!m) return dmx_fail(DMX_ERR_INVALID, "null model");
@@ -611,6 +626,8 @@ extern "C" dmx_status dmx_model_params(const dmx_model* m, int32_t* np, double* 
     values[dmx::PAR_WIDTH] = d.solimp[2]; values[dmx::PAR_MID] = d.solimp[3];
     for (int p = 0; p < d.npair; ++p) values[dmx::PAR_MU0 + p] = d.p_mu[p];
     for (int b = 0; b < d.nbody; ++b) values[dmx::PAR_MU0 + d.npair + b] = d.b_mass[b];
+    for (int g = 0; g < d.ngeom; ++g)
+      if (d.g_box[g] >= 0) values[dmx::PAR_MU0 + d.npair + d.nbody + d.g_box[g]] = 2.0 * d.g_size[g][0];
   }
   return DMX_OK;
 }

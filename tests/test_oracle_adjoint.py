@@ -299,35 +299,53 @@ def test_other_schemes_gradient_frozen_steps(orc, method):
 PARAM_NAMES = ["t_c", "phi_d", "d_o", "d_w", "width", "midpoint"]
 
 
+def _boxes(sc):
+    return [g for g, gm in enumerate(sc["geoms"]) if gm["type"] == "box"]
+
+
 def _perturbed_scene(make, k, delta):
     """Scene from make() with model parameter k moved by delta (order:
-    t_c, phi_d, d_o, d_w, width, midpoint, mu of each pair, then the mass of
-    each body with its inertia scaled in proportion)."""
+    t_c, phi_d, d_o, d_w, width, midpoint, mu of each pair, the mass of each
+    body with its inertia scaled in proportion, then the side length (2 x the
+    x half size) of each box geom: half sizes scaled together, and the
+    inertia of a body whose only geom is the box by the square)."""
     sc = make()
     o = sc["options"]
-    npair = len(sc["pairs"])
+    npair, nbody = len(sc["pairs"]), len(sc["bodies"])
     if k < 2:
         o["solref"][k] += delta
     elif k < 6:
         o["solimp"][k - 2] += delta
     elif k < 6 + npair:
         sc["pairs"][k - 6]["mu"] += delta
-    else:
+    elif k < 6 + npair + nbody:
         b = sc["bodies"][k - 6 - npair]
         f = (b["mass"] + delta) / b["mass"]
         b["mass"] += delta
         b["inertia"] = [f * x for x in b["inertia"]]
+    else:
+        g = _boxes(sc)[k - 6 - npair - nbody]
+        gm = sc["geoms"][g]
+        lam = (2 * gm["size"][0] + delta) / (2 * gm["size"][0])
+        gm["size"] = [lam * x for x in gm["size"]]
+        if sum(1 for q in sc["geoms"] if q["body"] == gm["body"]) == 1:
+            b = sc["bodies"][gm["body"]]
+            b["inertia"] = [lam * lam * x for x in b["inertia"]]
     return sc
 
 
 def _param_value(sc, k):
     o = sc["options"]
-    npair = len(sc["pairs"])
+    npair, nbody = len(sc["pairs"]), len(sc["bodies"])
     if k < 2:
         return o["solref"][k]
     if k < 6:
         return o["solimp"][k - 2]
-    return sc["pairs"][k - 6]["mu"] if k < 6 + npair else sc["bodies"][k - 6 - npair]["mass"]
+    if k < 6 + npair:
+        return sc["pairs"][k - 6]["mu"]
+    if k < 6 + npair + nbody:
+        return sc["bodies"][k - 6 - npair]["mass"]
+    return 2 * sc["geoms"][_boxes(sc)[k - 6 - npair - nbody]]["size"][0]
 
 
 def _param_fd(orc, make, x0, hlog, w, T, k, rel=1e-6, ctrl=None, NI=1):
@@ -344,9 +362,9 @@ def _param_fd(orc, make, x0, hlog, w, T, k, rel=1e-6, ctrl=None, NI=1):
 
 @pytest.mark.parametrize("name", ["ball", "box"])
 def test_parameter_gradient_frozen_steps(orc, name):
-    """p_bar of the discrete adjoint (solref, solimp, friction, mass) against
-    central differences of the frozen-step map over models with one parameter
-    moved."""
+    """p_bar of the discrete adjoint (solref, solimp, friction, mass, box side)
+    against central differences of the frozen-step map over models with one
+    parameter moved."""
     make = W.SCENES[name]
     m = orc.OracleModel(make())
     if name == "ball":
@@ -358,7 +376,7 @@ def test_parameter_gradient_frozen_steps(orc, name):
     n = np.array([len(r["hlog"])], dtype=np.int32)
     g = m.batch_replay_grad(x0[None], np.array([T]), r["hlog"][None], n, w[None], params=True)
     pb = g["p_bar"][0]
-    assert len(pb) == m.nparams() == 8
+    assert len(pb) == m.nparams() == 8 + (name == "box")
     for k in range(m.nparams()):
         if name == "ball" and k == 6:
             assert pb[k] == 0.0                      # frictionless: mu enters no row
@@ -366,7 +384,7 @@ def test_parameter_gradient_frozen_steps(orc, name):
         # stiff contact curves the frozen-step map: best of a small eps sweep
         # (truncation vs round-off), as for the state gradients
         errs = []
-        for rel in (1e-4, 1e-5, 1e-6, 1e-7):
+        for rel in (1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9):
             fd = _param_fd(orc, make, x0, r["hlog"], w, T, k, rel=rel)
             errs.append(abs(pb[k] - fd) / max(abs(fd), np.abs(pb).max() * 1e-2))
         assert min(errs) < 2e-5, (k, pb[k], errs)
@@ -418,6 +436,55 @@ def test_rest_height_parameter_gradient(orc):
     # relative sensitivities theta dz/dtheta: the mass's vanishes
     rel = np.abs(pb[:6] * np.array(base))
     assert abs(pb[7] * m0) <= 1e-3 * rel.max(), (pb[7], rel)
+
+
+def test_cube_rest_height_side_gradient(orc):
+    """A cube settled flat on the plane rests at z = l/2 + r_rest: the
+    penetration r_rest solves the same per-vertex equilibrium whatever the
+    side l (the vertices move horizontally with it, and the inverse weight of
+    the free body is 1/m, independent of its inertia), so dz/dl = 1/2; and,
+    as for the ball, the mass leaves z unchanged.  Pins the side length's
+    path through the vertex positions and the inertia scaling."""
+    sc = W.box_scene()
+    m = orc.OracleModel(sc)
+    x0 = np.array([0, 0, 0.06, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0.0])
+    T = 1.0
+    r = m.rollout(x0, T=T)
+    w = np.zeros(13); w[2] = 1.0
+    n = np.array([len(r["hlog"])], dtype=np.int32)
+    pb = m.batch_replay_grad(x0[None], np.array([T]), r["hlog"][None], n, w[None], params=True)["p_bar"][0]
+    assert len(pb) == 9                                  # 6 contact, mu, mass, side
+    assert abs(pb[8] - 0.5) < 1e-9, pb[8]
+    assert abs(pb[7] * sc["bodies"][0]["mass"]) < 1e-12, pb[7]
+
+
+def test_capsule_box_side_gradient(orc):
+    """The side length through the capsule-box distance: the arm's last link
+    pressed 0.5 mm into a vertical edge of the yawed cube (zero gravity, so
+    that contact alone acts), loss on the whole state after 10 ms; p_bar of
+    the side against central differences of the frozen-step map over models
+    with the box scaled (the implicit-function derivative of the minimiser
+    along the link and the distance field both carry the box size)."""
+    make = lambda: W.chain_cube_scene(gravity=(0.0, 0.0, 0.0))
+    m = orc.OracleModel(make())
+    k = m.nparams() - 1                                   # the cube's side
+    yaw = 0.4
+    x0 = np.zeros(27)
+    x0[7:10] = [1.95, 0.09, 0.06]
+    x0[10:14] = [np.cos(yaw / 2), 0, 0, np.sin(yaw / 2)]
+    assert -1e-3 < m.contacts(x0[:14])[14, 0] < 0            # the last link's capsule-box slot
+    ctrl = np.zeros((1, 7))
+    T = 0.01
+    r = m.rollout(x0, ctrl=ctrl, T=T, NI=1)
+    w = np.random.default_rng(3).normal(size=27)
+    n = np.array([r["nsteps"]], dtype=np.int32)
+    pb = m.batch_replay_grad(x0[None], np.array([T]), r["hlog"][None], n, w[None], ctrl=ctrl[None], NI=1,
+                             params=True)["p_bar"][0]
+    errs = []
+    for rel in (1e-6, 1e-7, 1e-8):
+        fd = _param_fd(orc, make, x0, r["hlog"][:r["nsteps"]], w, T, k, rel=rel, ctrl=ctrl, NI=1)
+        errs.append(abs(pb[k] - fd) / abs(fd))
+    assert min(errs) < 1e-7, (pb[k], errs)
 
 
 def _param_floor(orc, name, inp):
