@@ -649,8 +649,12 @@ __device__ void capsule_box(const DevModel& m, const T* gR, const T* gp, int g1,
   const double rc = m.g_size[g1][0], Lh = m.g_size[g1][1];
   const double* h = m.g_size[g2];
   // the box half sizes as the evaluation's scalars (a side-length tangent in derivative scalars)
-  using H = decltype(Par<T>::half(m, pdir, g2, 0));
-  const H hT[3] = {Par<T>::half(m, pdir, g2, 0), Par<T>::half(m, pdir, g2, 1), Par<T>::half(m, pdir, g2, 2)};
+  T hd[3];
+  if constexpr (!std::is_same<T, double>::value)
+    for (int i = 0; i < 3; ++i) hd[i] = Par<T>::half(m, pdir, g2, i);
+  const auto* hT = [&]() {
+    if constexpr (std::is_same<T, double>::value) return h; else return static_cast<const T*>(hd);
+  }();
   const T* R1 = gR + 9 * g1; const T* R2 = gR + 9 * g2;
   const T* c1 = gp + 3 * g1; const T* c2 = gp + 3 * g2;
   T dc[3] = {c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2]};
@@ -845,12 +849,18 @@ __device__ void collide(const Grp<G>& g, const DevModel& m, const WsT<T>& w, boo
         pt[0] = cg[0] + e * Rg[0]; pt[1] = cg[1] + e * Rg[3]; pt[2] = cg[2] + e * Rg[6];
         rad = m.g_size[g1][0];
       } else {
-        const auto h0 = Par<T>::half(m, w.pdir, g1, 0), h1 = Par<T>::half(m, w.pdir, g1, 1);
-        const auto h2 = Par<T>::half(m, w.pdir, g1, 2);
-        using H = decltype(h0);
-        const H ex[3] = {(j & 1) ? h0 : H(-h0), (j & 2) ? h1 : H(-h1), (j & 4) ? h2 : H(-h2)};
         T t[3];
-        matvec3(Rg, ex, t);
+        if constexpr (std::is_same<T, double>::value) {
+          const double ex[3] = {(j & 1) ? m.g_size[g1][0] : -m.g_size[g1][0],
+                                (j & 2) ? m.g_size[g1][1] : -m.g_size[g1][1],
+                                (j & 4) ? m.g_size[g1][2] : -m.g_size[g1][2]};
+          matvec3(Rg, ex, t);
+        } else {   // derivative scalars: the half sizes carry a side-length tangent
+          const T h0 = Par<T>::half(m, w.pdir, g1, 0), h1 = Par<T>::half(m, w.pdir, g1, 1);
+          const T h2 = Par<T>::half(m, w.pdir, g1, 2);
+          const T ex[3] = {(j & 1) ? h0 : -h0, (j & 2) ? h1 : -h1, (j & 4) ? h2 : -h2};
+          matvec3(Rg, ex, t);
+        }
         pt[0] = cg[0] + t[0]; pt[1] = cg[1] + t[1]; pt[2] = cg[2] + t[2];
       }
       const T r = pt[2] - rad;
