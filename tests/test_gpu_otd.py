@@ -147,3 +147,38 @@ def test_arm_controls_parity(dmx, orc_mod):
     g, o = _both(dmx, orc_mod, sc, inp["x0"], inp["T"], w, wb=wb, **kw)
     keys = ("x0_bar", "ctrl_bar")
     _assert_within_spread(g, o, _spread(orc_mod, sc, inp["x0"], inp["T"], w, o, keys, xb_bar=wb, **kw), keys)
+
+
+def test_semi_implicit_euler_parity(dmx, orc_mod):
+    """The fixed-step scheme backward (h = h0 every step, clamped at the
+    horizon): the same step count as the forward and the oracle's gradient to
+    rounding on the damped hinge and the top."""
+    sc = _hinge_scene()
+    x0 = np.array([[0.2, 2.0], [-0.1, 0.5]])
+    w = np.array([[0.3, 1.0], [1.0, -0.2]])
+    g, o = _both(dmx, orc_mod, sc, x0, 0.5, w, method="euler")
+    _assert_parity(g, o)
+    assert np.all(g["steps"] == int(round(0.5 / 1e-3)))
+    g_ = np.random.default_rng(9)
+    x0 = np.zeros((4, 13)); x0[:, 2] = 1.0; x0[:, 3] = 1.0
+    x0[:, 7:13] = g_.normal(0.0, 1.0, (4, 6))
+    g, o = _both(dmx, orc_mod, _top_scene(), x0, 0.3, g_.normal(size=(4, 13)), method="euler")
+    _assert_parity(g, o)
+
+
+def test_step_budget_status(dmx):
+    """A backward solve that runs out of attempts reports MAX_STEPS per
+    environment (and leaves the others untouched)."""
+    import torch
+    sc = _top_scene()
+    m = dmx.Model(sc)
+    B = 4
+    xT = np.zeros((B, 13)); xT[:, 2] = 1.0; xT[:, 3] = 1.0; xT[:, 12] = 4.0
+    T = np.array([1.0, 1.0, 1e-4, 1e-4])
+    w = np.ones((B, 13))
+    gx, _, steps, status = dmx.rollout_grad_otd(m, _dev(xT.T), _dev(T), _dev(w.T), rtol=1e-10, atol=1e-12,
+                                                max_steps=5)
+    status = status.cpu().numpy()
+    assert list(status[:2]) == [1, 1]                   # DMX_ENV_MAX_STEPS
+    assert list(status[2:]) == [0, 0]
+    assert torch.isfinite(gx).all()
