@@ -188,7 +188,7 @@ __device__ Ws group_workspace(const RolloutParams& P, const Layout* L) {
 
 // Persistent form: loop { take next env; integrate it to T }.
 template <int G>
-__global__ void __launch_bounds__(32) k_rollout_persistent(RolloutParams P) {
+__global__ void __launch_bounds__(32, 1) k_rollout_persistent(RolloutParams P) {
   __shared__ Layout sL;
   if (threadIdx.x == 0) sL = P.L;
   __syncthreads();
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(32) k_rollout_persistent(RolloutParams P) {
 
 // Plain form, initialisation launch: state of every environment into HBM.
 template <int G>
-__global__ void __launch_bounds__(32) k_step_init(RolloutParams P, StepState S) {
+__global__ void __launch_bounds__(32, 1) k_step_init(RolloutParams P, StepState S) {
   __shared__ Layout sL;
   if (threadIdx.x == 0) sL = P.L;
   __syncthreads();
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(32) k_step_init(RolloutParams P, StepState S) 
 
 // Plain form, one attempt of every unfinished environment.
 template <int G>
-__global__ void __launch_bounds__(32) k_step(RolloutParams P, StepState S) {
+__global__ void __launch_bounds__(32, 1) k_step(RolloutParams P, StepState S) {
   __shared__ Layout sL;
   if (threadIdx.x == 0) sL = P.L;
   __syncthreads();
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(32) k_step(RolloutParams P, StepState S) {
 // Right-hand side of a batch of states (q [nq][B], v [nv][B], u [nu][B]) into
 // a [nv][B]; info [4][B]: status, rows, active rows, Newton solves.
 template <int G>
-__global__ void __launch_bounds__(32) k_eval_rhs(RolloutParams P, const double* q, const double* v, const double* u,
+__global__ void __launch_bounds__(32, 1) k_eval_rhs(RolloutParams P, const double* q, const double* v, const double* u,
                                                   int cfd, double* a, int* info) {
   __shared__ Layout sL;
   if (threadIdx.x == 0) sL = P.L;
