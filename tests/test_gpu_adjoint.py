@@ -452,6 +452,10 @@ def test_parameter_gradient_matches_oracle(dmx, orc_mod, name, cfd):
     assert np.all(g["status"] == 0)
     om = orc_mod.OracleModel(sc)
     assert m.params().shape == (om.nparams(),)
+    o_ = sc["options"]
+    expect = (list(o_["solref"]) + list(o_["solimp"][:4]) + [p["mu"] for p in sc["pairs"]]
+              + [b["mass"] for b in sc["bodies"]] + [2 * g["size"][0] for g in sc["geoms"] if g["type"] == "box"])
+    np.testing.assert_array_equal(m.params(), expect)
     o = om.batch_replay_grad(inp["x0"], inp["T"], g["hlog"], g["n"], xT_bar, ctrl=inp["ctrl"], NI=inp["NI"], cfd=cfd,
                              params=True)
     assert_grad(g, o, "p_bar")
